@@ -1,0 +1,522 @@
+"""Pins of the FP64 oracle against what the mathematics fixes independently of
+the oracle's own code: closed forms, invariants, brute force and central finite
+differences.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2401_05345_gb300 import scenes as S
+
+
+def _scene(mean, scale, quat, opacity, feat, sh_degree=-1):
+    f32 = lambda a: np.asarray(a, np.float32)
+    return S.Scene(f32(mean), f32(scale), f32(quat), f32(opacity), sh_degree, f32(feat))
+
+
+def _cam(W=33, H=33, dist=4.0, fov=60.0):
+    return S.front_camera(W, H, dist, fov)
+
+
+# ----------------------------------------------------------------------------
+# spherical harmonics
+# ----------------------------------------------------------------------------
+
+def test_sh_basis_orthonormal(orc):
+    """Real SH basis of degree <= 3 is orthonormal on the unit sphere
+    (Gauss-Legendre in cos(theta) x uniform phi, exact for degree <= 6)."""
+    xg, wg = np.polynomial.legendre.leggauss(8)
+    nphi = 16
+    gram = np.zeros((16, 16))
+    for ct, w in zip(xg, wg):
+        st = math.sqrt(1 - ct * ct)
+        for k in range(nphi):
+            ph = 2 * math.pi * k / nphi
+            d = np.array([st * math.cos(ph), st * math.sin(ph), ct])
+            y = orc.sh_basis(3, d)
+            gram += w * (2 * math.pi / nphi) * np.outer(y, y)
+    np.testing.assert_allclose(gram, np.eye(16), atol=1e-12)
+
+
+def test_sh_basis_low_orders_closed_form(orc):
+    d = np.array([0.36, -0.48, 0.8])
+    y = orc.sh_basis(1, d)
+    c0 = 0.5 / math.sqrt(math.pi)
+    c1 = math.sqrt(3 / (4 * math.pi))
+    np.testing.assert_allclose(y, [c0, -c1 * d[1], c1 * d[2], -c1 * d[0]], rtol=1e-14)
+
+
+def test_sh_basis_gradient_fd(orc):
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        d = rng.normal(size=3)
+        g = orc.sh_basis_grad(3, d)
+        h = 1e-6
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            fd = (orc.sh_basis(3, d + e) - orc.sh_basis(3, d - e)) / (2 * h)
+            np.testing.assert_allclose(g[:, a], fd, rtol=1e-7, atol=1e-8)
+
+
+# ----------------------------------------------------------------------------
+# projection / covariance closed forms
+# ----------------------------------------------------------------------------
+
+def test_point_projection_closed_form(orc):
+    cam = _cam(65, 49)
+    means = np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.5], [-0.7, 0.4, -1.0]])
+    sc = _scene(means, np.full((3, 3), 0.01), np.tile([1, 0, 0, 0], (3, 1)), [0.5] * 3,
+                np.full((3, 3), 0.5))
+    pp = orc.preprocess(sc, cam)
+    m = sc.mean.astype(np.float64)
+    z = m[:, 2] + 4.0
+    u = cam.fx * m[:, 0] / z + cam.cx
+    v = cam.fy * m[:, 1] / z + cam.cy
+    np.testing.assert_allclose(pp["uv"][:, 0], u, rtol=1e-13)
+    np.testing.assert_allclose(pp["uv"][:, 1], v, rtol=1e-13)
+    np.testing.assert_allclose(pp["depth"], z, rtol=1e-13)
+
+
+@pytest.mark.parametrize("s", [0.01, 0.05, 0.2])
+def test_isotropic_conic_on_axis(orc, s):
+    """Isotropic Gaussian on the optical axis: Sigma2 = (s f / z)^2 I + 0.3 I."""
+    cam = _cam(33, 33)
+    sc = _scene([[0, 0, 0]], [[s, s, s]], [[0.3, 0.1, -0.5, 0.7]], [0.5], [[0.2, 0.4, 0.6]])
+    pp = orc.preprocess(sc, cam)
+    z = 4.0
+    var = (np.float64(np.float32(s)) * cam.fx / z) ** 2 + float(np.float32(0.3))
+    np.testing.assert_allclose(pp["conic"][0], [1 / var, 0.0, 1 / var], rtol=1e-12, atol=1e-14)
+    assert pp["radius"][0] == math.ceil(3 * math.sqrt(var + math.sqrt(float(np.float32(0.1)))))
+
+
+def test_rotated_anisotropic_conic_on_axis(orc):
+    """Rotation by theta about the optical axis, q = (cos t/2, 0, 0, sin t/2):
+    Sigma2 = k^2 [[a c^2 + b s^2, (a-b) c s], [(a-b) c s, a s^2 + b c^2]] + 0.3 I."""
+    cam = _cam(33, 33)
+    th = 0.7
+    sx, sy, sz = 0.08, 0.02, 0.05
+    q = [math.cos(th / 2), 0, 0, math.sin(th / 2)]
+    sc = _scene([[0, 0, 0]], [[sx, sy, sz]], [q], [0.5], [[0.2, 0.4, 0.6]])
+    pp = orc.preprocess(sc, cam)
+    sx, sy = float(np.float32(sx)), float(np.float32(sy))
+    qq = np.asarray(np.float32(q), np.float64)
+    qq /= np.linalg.norm(qq)
+    th = 2 * math.atan2(qq[3], qq[0])
+    c, s_ = math.cos(th), math.sin(th)
+    k = cam.fx / 4.0
+    dil = float(np.float32(0.3))
+    S2 = k * k * np.array([[sx**2 * c * c + sy**2 * s_ * s_, (sx**2 - sy**2) * c * s_],
+                           [(sx**2 - sy**2) * c * s_, sx**2 * s_ * s_ + sy**2 * c * c]]) + dil * np.eye(2)
+    inv = np.linalg.inv(S2)
+    np.testing.assert_allclose(pp["conic"][0], [inv[0, 0], inv[0, 1], inv[1, 1]], rtol=1e-10)
+
+
+def test_identity_quaternion_covariance_is_diag_scale(orc):
+    """Identity rotation: Sigma3 = diag(s^2); on the axis Sigma2 = diag((f/z)^2 sx^2, (f/z)^2 sy^2) + 0.3."""
+    cam = _cam(33, 33)
+    sx, sy, sz = 0.03, 0.07, 0.11
+    sc = _scene([[0, 0, 0]], [[sx, sy, sz]], [[2.0, 0, 0, 0]], [0.5], [[0.2, 0.4, 0.6]])
+    pp = orc.preprocess(sc, cam)
+    k = cam.fx / 4.0
+    dil = float(np.float32(0.3))
+    a = k * k * float(np.float32(sx)) ** 2 + dil
+    b = k * k * float(np.float32(sy)) ** 2 + dil
+    np.testing.assert_allclose(pp["conic"][0], [1 / a, 0, 1 / b], rtol=1e-12, atol=1e-15)
+
+
+def test_ewa_jacobian_matches_numeric_projection_derivative(orc):
+    """Off-axis Gaussian: Sigma2 = J W Sigma3 W^T J^T + 0.3 I with J the
+    derivative of the pixel position w.r.t. the camera-space mean.  J is taken
+    here by central differences of the oracle's own (u, v) output."""
+    cam = S.look_at_camera((1.0, -0.5, -3.5), (0.2, 0.1, 0.3), 64, 48)
+    rng = np.random.default_rng(11)
+    m0 = np.array([0.3, -0.2, 0.4])
+    sc = _scene([m0], [[0.05, 0.02, 0.08]], [rng.normal(size=4)], [0.5], [[0.2, 0.4, 0.6]])
+    pp = orc.preprocess(sc, cam)
+    # numeric d(u,v)/d(mean) (world) from shifted means
+    h = 1e-6
+    Jw = np.zeros((2, 3))
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        up = orc.preprocess(_scene([m0 + e], sc.scale, sc.quat, sc.opacity, sc.feat), cam)["uv"][0]
+        dn = orc.preprocess(_scene([m0 - e], sc.scale, sc.quat, sc.opacity, sc.feat), cam)["uv"][0]
+        # float32 rounding of the shifted means: use the stored values for the step
+        mp = np.float64(np.float32(m0 + e))[a]
+        mm = np.float64(np.float32(m0 - e))[a]
+        Jw[:, a] = (up - dn) / (mp - mm)
+    q = sc.quat[0].astype(np.float64)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    # R must be a proper rotation
+    np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-12)
+    Sg = R @ np.diag(sc.scale[0].astype(np.float64) ** 2) @ R.T
+    S2 = Jw @ Sg @ Jw.T + float(np.float32(0.3)) * np.eye(2)
+    inv = np.linalg.inv(S2)
+    np.testing.assert_allclose(pp["conic"][0], [inv[0, 0], inv[0, 1], inv[1, 1]], rtol=2e-6)
+
+
+def test_near_plane_cull(orc):
+    cam = _cam(33, 33)
+    sc = _scene([[0, 0, -3.85], [0, 0, -3.75]], np.full((2, 3), 0.05), [[1, 0, 0, 0]] * 2,
+                [0.5, 0.5], np.full((2, 3), 0.5))
+    pp = orc.preprocess(sc, cam)
+    assert pp["radius"][0] == 0 and pp["radius"][1] > 0
+
+
+# ----------------------------------------------------------------------------
+# compositing closed forms and invariants
+# ----------------------------------------------------------------------------
+
+def _render_2d(orc, W, H, uv, conic, opac, rgb, bg, g=None, tile=(16, 16), radius=None, depth=None):
+    uv = np.asarray(uv, np.float64)
+    n = len(uv)
+    if radius is None:
+        radius = np.full(n, 40, np.int32)
+    if depth is None:
+        depth = np.arange(1, n + 1, dtype=np.float64)
+    keys, pl, ranges = orc.bin_sort(uv, depth, radius, W, H, tile)
+    return orc.render(W, H, ranges, pl, uv, conic, opac, rgb, bg, g, tile)
+
+
+def test_single_isotropic_splat_pixel_values(orc):
+    """One isotropic splat on a pixel centre: out = o c + (1 - o) bg there, and
+    alpha = o exp(-|d|^2 / (2 var)) at offset d."""
+    W = H = 32
+    var = 6.0
+    o, c, bg = 0.7, np.array([0.2, 0.5, 0.9]), np.array([0.1, 0.3, 0.05])
+    out = _render_2d(orc, W, H, [[12.0, 17.0]], [[1 / var, 0, 1 / var]], [o], [c], bg)
+    img = out["image"]
+    np.testing.assert_allclose(img[:, 17, 12], o * c + (1 - o) * bg, rtol=1e-14)
+    for (dx, dy) in [(1, 0), (2, 3), (-4, 1), (0, -5)]:
+        a = o * math.exp(-(dx * dx + dy * dy) / (2 * var))
+        exp_val = (a * c + (1 - a) * bg) if a >= 1 / 255 else bg
+        np.testing.assert_allclose(img[:, 17 + dy, 12 + dx], exp_val, rtol=1e-13)
+
+
+def test_alpha_cap(orc):
+    out = _render_2d(orc, 16, 16, [[5.0, 5.0]], [[0.5, 0, 0.5]], [0.9999], [[1.0, 1.0, 1.0]], [0, 0, 0])
+    assert abs(out["image"][0, 5, 5] - float(np.float32(0.99))) < 1e-15
+
+
+def test_transmittance_telescopes(orc):
+    """Sum_j alpha_j T_j + T_final = 1: white splats over a white background
+    render exactly 1, and over black render 1 - T_final."""
+    rng = np.random.default_rng(5)
+    n, W, H = 60, 40, 36
+    uv = rng.uniform(0, [W, H], size=(n, 2))
+    L = rng.normal(size=(n, 2, 2)) * 0.6
+    cov = L @ L.transpose(0, 2, 1) + 2.0 * np.eye(2)
+    inv = np.linalg.inv(cov)
+    conic = np.stack([inv[:, 0, 0], inv[:, 0, 1], inv[:, 1, 1]], 1)
+    opac = rng.uniform(0.3, 0.99, size=n)
+    ones = np.ones((n, 3))
+    out1 = _render_2d(orc, W, H, uv, conic, opac, ones, [1, 1, 1], radius=np.full(n, 12, np.int32))
+    np.testing.assert_allclose(out1["image"], 1.0, atol=1e-13)
+    out0 = _render_2d(orc, W, H, uv, conic, opac, ones, [0, 0, 0], radius=np.full(n, 12, np.int32))
+    np.testing.assert_allclose(out0["image"][0], 1.0 - out0["final_T"], atol=1e-13)
+    assert (out0["final_T"] < 1).any() and (out0["final_T"] > 1e-4 * 0.5).all()
+
+
+def test_single_splat_gradient_closed_form(orc):
+    """out = c a + (1 - a) bg: dL/dc = a g, dL/do = G (c - bg).g, and the
+    position gradient points along the conic-weighted offset."""
+    W = H = 16
+    var, o = 5.0, 0.6
+    c, bg = np.array([0.3, 0.8, 0.4]), np.array([0.2, 0.1, 0.7])
+    g = np.zeros((3, H, W), np.float32)
+    g[:, 7, 9] = [1.0, -1.0, 1.0]
+    u, v = 8.25, 6.5
+    out = _render_2d(orc, W, H, [[u, v]], [[1 / var, 0, 1 / var]], [o], [c], bg, g)
+    dx, dy = u - 9, v - 7
+    G = math.exp(-(dx * dx + dy * dy) / (2 * var))
+    a = o * G
+    gv = g[:, 7, 9].astype(np.float64)
+    gr = out["grad2d"][0]
+    np.testing.assert_allclose(gr[6:9], a * gv, rtol=1e-13)
+    dalpha = float(np.dot(c - bg, gv))
+    np.testing.assert_allclose(gr[5], G * dalpha, rtol=1e-12)
+    dsig = -o * G * dalpha
+    np.testing.assert_allclose(gr[0:2], [dx / var * dsig, dy / var * dsig], rtol=1e-12)
+    np.testing.assert_allclose(gr[2:5], [0.5 * dx * dx * dsig, dx * dy * dsig, 0.5 * dy * dy * dsig],
+                               rtol=1e-12)
+
+
+def test_two_stacked_splats_closed_form(orc):
+    """out = c1 a1 + c2 a2 (1-a1) + bg (1-a1)(1-a2):
+    dL/da1 = (c1 - c2 a2 - bg (1 - a2)).g, dL/da2 = (1-a1)(c2 - bg).g."""
+    W = H = 16
+    c1, c2, bg = np.array([0.9, 0.1, 0.3]), np.array([0.2, 0.6, 0.5]), np.array([0.05, 0.2, 0.9])
+    o1, o2 = 0.55, 0.8
+    g = np.zeros((3, H, W), np.float32)
+    g[:, 4, 4] = [1.0, 1.0, -1.0]
+    out = _render_2d(orc, W, H, [[4.0, 4.0], [4.0, 4.0]], [[0.2, 0, 0.2]] * 2, [o1, o2], [c1, c2], bg,
+                     g, depth=np.array([1.0, 2.0]))
+    gv = g[:, 4, 4].astype(np.float64)
+    np.testing.assert_allclose(out["image"][:, 4, 4],
+                               c1 * o1 + c2 * o2 * (1 - o1) + bg * (1 - o1) * (1 - o2), rtol=1e-14)
+    gr = out["grad2d"]
+    np.testing.assert_allclose(gr[0, 5], np.dot(c1 - c2 * o2 - bg * (1 - o2), gv), rtol=1e-12)
+    np.testing.assert_allclose(gr[1, 5], (1 - o1) * np.dot(c2 - bg, gv), rtol=1e-12)
+    np.testing.assert_allclose(gr[1, 6:9], o2 * (1 - o1) * gv, rtol=1e-13)
+
+
+def test_occluded_splat_has_zero_gradient(orc):
+    """Splats behind an opaque pair (T (1 - alpha) < 1e-4) get exactly zero."""
+    W = H = 16
+    n = 5
+    uv = np.full((n, 2), 8.0)
+    conic = np.tile([0.02, 0.0, 0.02], (n, 1))
+    opac = np.array([1.0, 1.0, 0.5, 0.7, 0.9])
+    rng = np.random.default_rng(2)
+    rgb = rng.uniform(size=(n, 3))
+    g = np.zeros((3, H, W), np.float32)
+    g[:, 8, 8] = 1.0   # only the pixel where the front pair is opaque
+    out = _render_2d(orc, W, H, uv, conic, opac, rgb, [0.3, 0.3, 0.3], g,
+                     depth=np.arange(1.0, n + 1))
+    gr = out["grad2d"]
+    assert np.all(gr[1:] == 0.0)
+    assert np.any(gr[0] != 0.0)
+    assert out["n_contrib"][8, 8] == 1
+
+
+def test_ambiguous_alpha_floor_gets_allowance(orc):
+    """alpha within FP32 rounding of 1/255: the oracle flags the decision and
+    the image allowance equals the contribution of either outcome."""
+    W = H = 16
+    amin = float(np.float32(1.0) / np.float32(255.0))
+    o = amin * (1 + 1e-9)
+    out = _render_2d(orc, W, H, [[8.0, 8.0]], [[0.5, 0, 0.5]], [o], [[1.0, 0.5, 0.25]], [0, 0, 0],
+                     np.ones((3, H, W), np.float32))
+    assert out["pix_ambig"][8, 8] >= 1
+    np.testing.assert_allclose(out["iallow"][:, 8, 8], o * np.array([1.0, 0.5, 0.25]), rtol=1e-12)
+    assert out["gallow"][0, 6] > 0
+
+
+# ----------------------------------------------------------------------------
+# binning: brute force
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 16)])
+def test_binning_matches_brute_force(orc, tile):
+    """Tile t = (tx, ty) holds Gaussian i iff floor(u)-r <= tw*tx + tw-1 and
+    floor(u)+r >= tw*tx + 1 (same in y): the 3DGS bounding-box rule stated as
+    interval overlap; lists ordered by (tile, depth, id)."""
+    rng = np.random.default_rng(7)
+    W, H, n = 77, 53, 300
+    uv = np.asarray(rng.uniform(-20, [W + 20, H + 20], size=(n, 2)), np.float32).astype(np.float64)
+    radius = rng.integers(0, 25, size=n).astype(np.int32)
+    depth = rng.uniform(0.5, 5, size=n).astype(np.float32).astype(np.float64)
+    depth[::7] = depth[3]  # equal depths: ties broken by id
+    keys, pl, ranges = orc.bin_sort(uv, depth, radius, W, H, tile)
+    tw, th = tile
+    gx, gy = -(-W // tw), -(-H // th)
+    entries = []
+    for i in range(n):
+        if radius[i] <= 0:
+            continue
+        fu, fv = math.floor(uv[i, 0]), math.floor(uv[i, 1])
+        r = int(radius[i])
+        for ty in range(gy):
+            if not (fv - r <= th * ty + th - 1 and fv + r >= th * ty + 1):
+                continue
+            for tx in range(gx):
+                if fu - r <= tw * tx + tw - 1 and fu + r >= tw * tx + 1:
+                    entries.append((ty * gx + tx, float(np.float32(depth[i])), i))
+    entries.sort()
+    assert len(entries) == len(pl)
+    assert [e[2] for e in entries] == [int(x) for x in pl]
+    exp_ranges = np.zeros((gx * gy, 2), np.int64)
+    for k, e in enumerate(entries):
+        t = e[0]
+        if k == 0 or entries[k - 1][0] != t:
+            exp_ranges[t, 0] = k
+        exp_ranges[t, 1] = k + 1
+    np.testing.assert_array_equal(ranges, exp_ranges)
+    tiles = (keys >> np.uint64(32)).astype(np.int64)
+    np.testing.assert_array_equal(tiles, [e[0] for e in entries])
+
+
+# ----------------------------------------------------------------------------
+# finite differences
+# ----------------------------------------------------------------------------
+
+def _random_2d(rng, n, W, H):
+    uv = rng.uniform(2, [W - 2, H - 2], size=(n, 2))
+    L = rng.normal(size=(n, 2, 2)) * 0.8
+    cov = L @ L.transpose(0, 2, 1) + 1.5 * np.eye(2)
+    inv = np.linalg.inv(cov)
+    conic = np.stack([inv[:, 0, 0], inv[:, 0, 1], inv[:, 1, 1]], 1)
+    opac = rng.uniform(0.2, 0.95, size=n)
+    rgb = rng.uniform(size=(n, 3))
+    return uv, conic, opac, rgb
+
+
+def test_render_gradient_matches_central_differences(orc):
+    """grad2d of L = sum(g * image) against central differences of the FP64
+    forward for every 2D parameter of every splat."""
+    rng = np.random.default_rng(21)
+    W, H, n = 24, 20, 14
+    uv, conic, opac, rgb = _random_2d(rng, n, W, H)
+    bg = np.array([0.2, 0.4, 0.1])
+    g = rng.normal(size=(3, H, W)).astype(np.float32)
+    radius = np.full(n, 12, np.int32)
+    depth = rng.uniform(1, 3, size=n)
+    base = _render_2d(orc, W, H, uv, conic, opac, rgb, bg, g, radius=radius, depth=depth)
+    gr = base["grad2d"]
+    gd = g.astype(np.float64)
+
+    def L(uv_, conic_, opac_, rgb_):
+        o = _render_2d(orc, W, H, uv_, conic_, opac_, rgb_, bg, None, radius=radius, depth=depth)
+        return float(np.sum(gd * o["image"]))
+
+    h = 1e-6
+    for i in range(n):
+        for p in range(9):
+            args = [uv.copy(), conic.copy(), opac.copy(), rgb.copy()]
+            if p < 2:
+                arr, idx = 0, (i, p)
+            elif p < 5:
+                arr, idx = 1, (i, p - 2)
+            elif p == 5:
+                arr, idx = 2, (i,)
+            else:
+                arr, idx = 3, (i, p - 6)
+            args[arr][idx] += h
+            lp = L(*args)
+            args[arr][idx] -= 2 * h
+            lm = L(*args)
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gr[i, p]) <= 1e-6 * (abs(gr[i, p]) + 1e-3), (i, p, fd, gr[i, p])
+
+
+def _fd_backproject_check(orc, sc, cam, rng, n_check=None):
+    pp0 = orc.preprocess(sc, cam)
+    vis = pp0["radius"] > 0
+    lam = rng.normal(size=(sc.n, 9))
+
+    def L(scene):
+        pp = orc.preprocess(scene, cam)
+        v = np.concatenate([pp["uv"], pp["conic"], pp["opacity"][:, None], pp["rgb"]], 1)
+        return float(np.sum(lam[vis] * v[vis]))
+
+    bp = orc.backproject(sc, cam, lam)
+    fields = [("mean", "dmean"), ("scale", "dscale"), ("quat", "dquat"), ("opacity", "dopacity"),
+              ("feat", "dfeat")]
+    checked = 0
+    for i in np.nonzero(vis)[0][:n_check]:
+        for fname, gname in fields:
+            arr = getattr(sc, fname)
+            flat_idx = list(np.ndindex(arr[i].shape)) if arr[i].shape else [()]
+            for j in flat_idx:
+                x0 = float(arr[(i,) + j])
+                h = 1e-3 * max(abs(x0), 1e-2)
+                # the parameters are float32: step between representable values
+                xp, xm = np.float32(x0 + h), np.float32(x0 - h)
+                arr[(i,) + j] = xp
+                lp = L(sc)
+                arr[(i,) + j] = xm
+                lm = L(sc)
+                arr[(i,) + j] = x0
+                fd = (lp - lm) / (float(xp) - float(xm))
+                an = bp[gname][(i,) + j]
+                tol = 2e-5 * (abs(an) + np.abs(bp[gname][i]).max() + 1e-6)
+                assert abs(fd - an) <= tol, (i, fname, j, fd, an)
+                checked += 1
+    return checked
+
+
+@pytest.mark.parametrize("sh_degree", [-1, 0, 1, 3])
+def test_backproject_matches_central_differences(orc, sh_degree):
+    """Backward projection of an arbitrary linear functional of the 2D outputs
+    (u, v, A, B, C, o, rgb) against central differences of the FP64 preprocess
+    w.r.t. mean, scale, unnormalised quaternion, opacity and SH/colour."""
+    rng = np.random.default_rng(100 + sh_degree)
+    n = 6
+    cam = S.look_at_camera((0.6, -0.4, -3.6), (0.0, 0.1, 0.2), 96, 72)
+    mean = rng.uniform(-0.6, 0.6, size=(n, 3))
+    scale = np.exp(rng.normal(-2.5, 0.4, size=(n, 3)))
+    quat = rng.normal(size=(n, 4))
+    opac = rng.uniform(0.2, 0.9, size=n)
+    if sh_degree < 0:
+        feat = rng.uniform(size=(n, 3))
+    else:
+        k = (sh_degree + 1) ** 2
+        feat = rng.normal(0, 0.3, size=(n, k, 3))
+        feat[:, 0] = rng.uniform(0.5, 1.5, size=(n, 3))
+    sc = _scene(mean, scale, quat, opac, feat, sh_degree)
+    assert _fd_backproject_check(orc, sc, cam, rng) > 0
+
+
+def test_backproject_frustum_clamp_branch(orc):
+    """Gaussian beyond 1.3 tan(fov/2) in x (clamped Jacobian) but large enough
+    to reach the screen: the exact derivative of the clamped projection."""
+    rng = np.random.default_rng(9)
+    cam = S.front_camera(64, 64)
+    sc = _scene([[3.4, 0.1, 0.0]], [[0.9, 0.5, 0.6]], [rng.normal(size=4)], [0.6],
+                [[0.3, 0.5, 0.7]], -1)
+    pp = orc.preprocess(sc, cam)
+    assert pp["radius"][0] > 0
+    assert abs(3.4 / 4.0) > 1.3 * cam.tan_fovx
+    assert _fd_backproject_check(orc, sc, cam, rng) > 0
+
+
+def test_end_to_end_gradient_matches_central_differences(orc):
+    """Full FP64 pipeline (preprocess -> bin -> render): d sum(g*image) / d theta
+    by the oracle's backward (render then backproject) against central
+    differences of the forward, on a tiny SH-degree-1 scene."""
+    rng = np.random.default_rng(4)
+    n, W, H = 8, 40, 32
+    cam = S.front_camera(W, H)
+    mean = rng.uniform(-0.5, 0.5, size=(n, 3))
+    scale = np.exp(rng.normal(-2.2, 0.3, size=(n, 3)))
+    feat = rng.normal(0, 0.2, size=(n, 4, 3))
+    feat[:, 0] = rng.uniform(0.5, 1.5, size=(n, 3))
+    sc = _scene(mean, scale, rng.normal(size=(n, 4)), rng.uniform(0.3, 0.9, size=n), feat, 1)
+    g = rng.normal(size=(3, H, W)).astype(np.float32)
+    gd = g.astype(np.float64)
+    bg = (0.1, 0.2, 0.3)
+    out = orc.render_scene(sc, cam, bg, g)
+    bp = orc.backproject(sc, cam, out["grad2d"])
+
+    def L():
+        return float(np.sum(gd * orc.render_scene(sc, cam, bg)["image"]))
+
+    for i in range(n):
+        for fname, gname in [("mean", "dmean"), ("scale", "dscale"), ("quat", "dquat"),
+                             ("opacity", "dopacity"), ("feat", "dfeat")]:
+            arr = getattr(sc, fname)
+            for j in (list(np.ndindex(arr[i].shape)) if arr[i].shape else [()])[:6]:
+                x0 = float(arr[(i,) + j])
+                h = 1e-3 * max(abs(x0), 1e-2)
+                xp, xm = np.float32(x0 + h), np.float32(x0 - h)
+                arr[(i,) + j] = xp
+                lp = L()
+                arr[(i,) + j] = xm
+                lm = L()
+                arr[(i,) + j] = x0
+                fd = (lp - lm) / (float(xp) - float(xm))
+                an = bp[gname][(i,) + j]
+                assert abs(fd - an) <= 1e-4 * (abs(an) + np.abs(bp[gname][i]).max() + 1e-4), \
+                    (i, fname, j, fd, an)
+
+
+# ----------------------------------------------------------------------------
+# Adam
+# ----------------------------------------------------------------------------
+
+def test_adam_first_steps_closed_form(orc):
+    """From zero moments with a constant gradient, every bias-corrected Adam
+    step moves each parameter by -lr g / (|g| + eps)."""
+    rng = np.random.default_rng(0)
+    p0 = rng.normal(size=50)
+    gr = rng.normal(size=50)
+    p, m, v = p0.copy(), np.zeros(50), np.zeros(50)
+    lr, eps = 1e-2, 1e-8
+    for step in (1, 2, 3):
+        orc.adam(p, gr.copy(), m, v, lr, 0.9, 0.999, eps, step)
+        np.testing.assert_allclose(p, p0 - step * lr * gr / (np.abs(gr) + eps), rtol=1e-9, atol=1e-12)
