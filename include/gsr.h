@@ -1,0 +1,242 @@
+/*
+ * gsr.h -- C ABI of the GB300 (sm_103a) Gaussian-splat rasterizer library
+ * (libgsr.so): projection, tile binning, forward blend, and the backward blend
+ * whose per-splat gradient accumulation is the bottleneck studied by DISTWAR
+ * (arXiv 2401.05345).
+ *
+ * Conventions shared by every entry point
+ *  - All pointers are DEVICE pointers unless the argument says "host".  The
+ *    caller owns every buffer; the library never allocates device memory.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = legacy default stream) unless stated otherwise.
+ *  - Return value: GSR_OK (0) or a negative status; gsr_status_string() names
+ *    it.  Argument errors are detected before anything is launched.  A CUDA
+ *    launch or runtime error returns GSR_ECUDA (the CUDA error string is kept
+ *    for gsr_last_cuda_error()).  No exception crosses the ABI.
+ *  - Gradient outputs ACCUMULATE (+=): the caller zeroes them first
+ *    (gsr_preprocess can do that for grad2d in the same pass).
+ *  - Images are planar float32 [3][H][W]; per-pixel maps float32/int32 [H][W].
+ *  - Tiles: tile_w x tile_h pixels (each a power of two in [8,32], product
+ *    <= 512); the grid has gx = ceil(W/tile_w) by gy = ceil(H/tile_h) tiles,
+ *    tile id = ty*gx + tx.
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSR_OK          0
+#define GSR_EINVAL     (-1)  /* bad argument (null pointer, size, option)   */
+#define GSR_ECAPACITY  (-2)  /* duplicated keys exceed key_capacity          */
+#define GSR_ECUDA      (-3)  /* CUDA runtime / launch error                  */
+#define GSR_ETIMEOUT   (-4)  /* a bounded device wait gave up                */
+#define GSR_ESCRATCH   (-5)  /* scratch buffer smaller than required         */
+
+typedef void* gsr_stream_t;
+
+/* Pinhole camera.  view: row-major 3x4 [R | t] mapping world to camera
+ * coordinates (camera looks down +z, image y down).  A camera-space point
+ * (x, y, z) projects to pixel (fx x/z + cx, fy y/z + cy), pixel centres at
+ * integer coordinates.  tan_fov*: tangent of the half field of view (the
+ * EWA Jacobian clamps x/z to +-1.3 tan_fovx).  campos: world position of the
+ * camera, origin of the SH viewing direction.  znear: near-plane cull. */
+typedef struct gsr_camera {
+    int32_t width, height;
+    float view[12];
+    float fx, fy, cx, cy;
+    float tan_fovx, tan_fovy;
+    float campos[3];
+    float znear;
+} gsr_camera;
+
+/* 2D splat record written by gsr_preprocess, 12 floats (48 bytes) per
+ * Gaussian: [0] u [1] v (pixel position), [2] A [3] B [4] C (conic: inverse
+ * screen covariance [[A,B],[B,C]]), [5] opacity, [6..8] RGB, [9] depth
+ * (camera z), [10..11] zero.  grad2d uses the same stride: [0] dL/du ...
+ * [8] dL/db, [9..11] unused (left as the caller initialised them). */
+#define GSR_REC 12
+
+/* Reduction tiers of the backward gradient accumulation.
+ *  PLAIN   every active pixel-thread issues one atomic add per parameter
+ *          (9 per pair) -- the baseline kernel of Sec. III-A, Fig. "Outline
+ *          of the gradient computation step".
+ *  WARP    every warp that holds at least one active lane reduces the 9
+ *          parameters across its 32 lanes in registers (inactive lanes add
+ *          zero, Sec. V-A2 / Fig. "modified gradient computation kernel") and
+ *          issues one 9-lane red instruction to L2.
+ *  HYBRID  balancing threshold (Sec. IV-B, Sec. V-A3): warps with
+ *          popc(active) >= threshold reduce at the SM as WARP, the others send
+ *          per-lane atomics to the L2 atomic units as PLAIN.
+ *  BLOCK   warp partials (or, below the threshold, per-lane values) are
+ *          added into the CTA's shared memory; one global red per
+ *          (tile, splat, parameter) when the staged batch is retired.
+ * threshold: 0 = every warp reduces, 33 = none does. */
+enum {
+    GSR_REDUCE_PLAIN = 0,
+    GSR_REDUCE_WARP = 1,
+    GSR_REDUCE_HYBRID = 2,
+    GSR_REDUCE_BLOCK = 3
+};
+
+/* lane_layout: which pixels of a 16x16 tile share a warp.
+ *   0: 16 x 2 rows,  1: 8 x 4 block. */
+typedef struct gsr_backward_opts {
+    int32_t reduce_mode;   /* GSR_REDUCE_* */
+    int32_t threshold;     /* 0..33, see above */
+    int32_t lane_layout;   /* 0 or 1 */
+    int32_t store_T;       /* 1: read final_T / n_contrib written by
+                              gsr_forward; 0: recompute them in the kernel
+                              (final_T / n_contrib may be NULL) */
+    int32_t reserved[4];   /* must be zero */
+} gsr_backward_opts;
+
+const char* gsr_status_string(int status);
+/* Text of the last CUDA error seen by the library in this thread. */
+const char* gsr_last_cuda_error(void);
+/* Library ABI version (major*100 + minor). */
+int gsr_version(void);
+
+/*
+ * Projection ("preprocess") of n 3D Gaussians.  Per Gaussian: camera-space
+ * mean, near-plane cull (z <= znear), 3D covariance R(q/|q|) diag(s)^2 R^T,
+ * EWA screen covariance J W Sigma W^T J^T + 0.3 I, conic, 3-sigma radius of
+ * the larger eigenvalue (eigenvalue discriminant floored at 0.1), tile
+ * rectangle (culled when empty), colour max(0, SH(dir) + 0.5) or the given
+ * colour.  The paper relies on the 3DGS rasterizer for this step (Sec. VI,
+ * "Workloads"; Sec. II-C).
+ *   mean [n,3], scale [n,3] (activated, > 0), quat [n,4] (w,x,y,z, any
+ *   non-zero norm), opacity [n] (activated, in (0,1)), feat: sh_degree 0..3 ->
+ *   SH coefficients [n,(deg+1)^2,3]; sh_degree -1 -> RGB colours [n,3].
+ *   cam: host pointer.  Outputs: splat2d [n,GSR_REC] (zeros and radius 0 for
+ *   culled Gaussians), radius [n] (int32, 0 = culled).
+ *   grad2d_to_zero: optional [n,GSR_REC] buffer zeroed in the same pass.
+ */
+int gsr_preprocess(int32_t n, int32_t sh_degree, const float* mean, const float* scale,
+                   const float* quat, const float* opacity, const float* feat,
+                   const gsr_camera* cam, int32_t tile_w, int32_t tile_h, float* splat2d,
+                   int32_t* radius, float* grad2d_to_zero, gsr_stream_t stream);
+
+/*
+ * Scratch bytes gsr_bin_sort needs for n Gaussians, a W x H image and at
+ * most key_capacity duplicated keys (host output *bytes).
+ */
+int gsr_bin_scratch_bytes(int32_t n, int32_t width, int32_t height, int32_t tile_w,
+                          int32_t tile_h, int64_t key_capacity, size_t* bytes);
+
+/*
+ * Tile binning: one key (tile_id << 32 | FP32 bits of depth) per (tile,
+ * Gaussian) pair in each visible Gaussian's tile rectangle, emitted in
+ * Gaussian order; stable LSD radix sort; per-tile [start, end) ranges.  This
+ * builds the "per-pixel list of primitives" that the gradient computation
+ * iterates (Sec. III-A): all pixels of a tile share one depth-sorted list.
+ *   splat2d, radius: from gsr_preprocess.  scratch: scratch_bytes >=
+ *   gsr_bin_scratch_bytes().  Outputs: point_list [key_capacity] (Gaussian
+ *   ids, first *n_keys valid), tile_ranges [gx*gy*2] (uint32 start, end;
+ *   0,0 for empty tiles), keys_out [key_capacity] (optional: sorted keys).
+ *   n_keys: HOST pointer, receives the key count.
+ * Synchronises `stream` once to read the key count.  Returns GSR_ECAPACITY
+ * (with *n_keys set, nothing else written) when the count exceeds
+ * key_capacity: the caller grows the buffers and calls again.
+ */
+int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                 const float* splat2d, const int32_t* radius, int64_t key_capacity,
+                 void* scratch, size_t scratch_bytes, uint32_t* point_list,
+                 uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,
+                 gsr_stream_t stream);
+
+/*
+ * Forward blend: for each pixel, front to back over its tile's list:
+ * sigma = A dx^2/2 + B dx dy + C dy^2/2 with (dx,dy) = (u,v) - pixel, skip if
+ * sigma < 0; alpha = min(0.99, o exp(-sigma)), skip if alpha < 1/255; stop
+ * (excluding this splat) once T (1 - alpha) < 1e-4; C += rgb alpha T;
+ * T *= 1 - alpha.  image = C + T bg (Sec. II-C, the forward pass whose
+ * per-pixel lists the gradient step walks).
+ *   bg: HOST pointer to 3 floats.  Outputs: image [3,H,W]; final_T [H,W]
+ *   and n_contrib [H,W] (1-based list position of the last contributor, 0 if
+ *   none), both optional (NULL).
+ */
+int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
+                const float* bg, float* image, float* final_T, int32_t* n_contrib,
+                gsr_stream_t stream);
+
+/*
+ * Backward blend + per-splat gradient accumulation: the gradient computation
+ * step of Sec. III-A.  One thread per pixel walks its tile's list back to
+ * front from the pixel's last contributor, recovers T_j = T_{j+1}/(1-alpha_j),
+ * and computes for every contributor
+ *   dL/drgb = alpha T g,
+ *   dL/dalpha = T (rgb.g) - [sum_{k>j} (rgb_k.g) alpha_k T_k + T_final (bg.g)] / (1-alpha),
+ *   dL/do = G dL/dalpha, dL/dsigma = -o G dL/dalpha (0 where alpha is capped),
+ *   dL/d(A,B,C) = (dx^2/2, dx dy, dy^2/2) dL/dsigma,
+ *   dL/d(u,v) = (A dx + B dy, B dx + C dy) dL/dsigma,
+ * with g = dL_dimage at the pixel; the 9 values are accumulated into
+ * grad2d[id*GSR_REC + 0..8] by the tier in opts (see GSR_REDUCE_*).  Every
+ * tier forms the same sum; only the float summation order differs.
+ *   final_T, n_contrib: from gsr_forward (ignored when opts->store_T == 0).
+ *   bg: HOST pointer.  opts: HOST pointer (NULL = WARP, threshold 0, 16x2,
+ *   store_T 1).
+ */
+int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                 const uint32_t* tile_ranges, const uint32_t* point_list,
+                 const float* splat2d, const float* bg, const float* final_T,
+                 const int32_t* n_contrib, const float* dL_dimage, float* grad2d,
+                 const gsr_backward_opts* opts, gsr_stream_t stream);
+
+/*
+ * Backward projection: chain rule from grad2d to the 3D parameters through
+ * the conic inverse, the EWA Jacobian (exact derivative, zero through an
+ * active frustum clamp), the covariance R S S^T R^T, the quaternion
+ * normalisation and the SH basis (zero on channels clamped at 0).  The paper
+ * only states that gradients of all parameters are computed (Sec. II-C).
+ * Inputs as gsr_preprocess plus radius and grad2d [n,GSR_REC].  Outputs
+ * ACCUMULATE: dmean [n,3], dscale [n,3], dquat [n,4], dopacity [n], dfeat
+ * (layout of feat).  Gaussians with radius 0 are left untouched.
+ */
+int gsr_backward_project(int32_t n, int32_t sh_degree, const float* mean, const float* scale,
+                         const float* quat, const float* opacity, const float* feat,
+                         const gsr_camera* cam, const int32_t* radius, const float* grad2d,
+                         float* dmean, float* dscale, float* dquat, float* dopacity,
+                         float* dfeat, gsr_stream_t stream);
+
+/*
+ * L1 photometric loss of Sec. II-B (difference to the reference image):
+ * dL_dimage[i] = sign(image[i] - target[i]) (0 where equal) and, if loss_sum
+ * is not NULL, loss_sum[0] += sum |image - target| (device float).
+ */
+int gsr_l1_loss(int64_t count, const float* image, const float* target, float* dL_dimage,
+                float* loss_sum, gsr_stream_t stream);
+
+/*
+ * Adam (Kingma & Ba) on a flat float array of n parameters, step >= 1:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
+ * The optimizer step of the training loop (Sec. II-B, Fig. 2).
+ */
+int gsr_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr,
+                  float beta1, float beta2, float eps, int32_t step, gsr_stream_t stream);
+
+/*
+ * Microbenchmark of the L2 atomic (red) path, the roofline of the PLAIN tier
+ * (Sec. II-A: atomics are processed by the ROP units at the L2 slices).
+ *   pattern 0: every lane adds to its own address (coalesced, distinct);
+ *   pattern 1: all 32 lanes of a warp add to one address (contended);
+ *   pattern 2: 9 lanes of a warp add to 9 consecutive floats of a 48-byte
+ *              record (the reduced tiers' access);
+ *   pattern 3: as 1 but 9 adds per lane to 9 consecutive floats (PLAIN).
+ * Issues `iters` rounds over a grid of `blocks` x 256 threads; buffer holds
+ * buffer_floats floats (device, accumulated into).  Adds performed are
+ * reported in *adds (host).
+ */
+int gsr_bench_red(int32_t pattern, int32_t blocks, int32_t iters, float* buffer,
+                  int64_t buffer_floats, int64_t* adds, gsr_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSR_H */

@@ -568,14 +568,19 @@ static void pixel_grads(const scene2d_t* S, const contrib_t* cs, int nc, double 
  * gallow [N,9], iallow [3,H,W], tallow [H*W]: allowance from decisions that
  *   FP32 may take the other way (difference between both outcomes);
  * nc_alt [H*W]: n_contrib under the flipped decision (-1 if none);
- * pix_ambig [H*W]: count of such decisions in the pixel.
+ * pix_ambig [H*W]: count of such decisions in the pixel;
+ * pix_widen [H*W]: the pixel's widening factor max(1, 8 b / 1e-5);
+ * terr [H*W]: first-order FP32 relative error bound of final_T.
+ * tile_mask [tiles] (may be NULL = all): only tiles with a non-zero entry are
+ * evaluated (sampled comparisons); other pixels' outputs are left untouched.
  * Any output pointer may be NULL.  Returns 0, or -1 on allocation failure.
  */
 int orc_render(int W, int H, int tw, int th, const uint32_t* ranges, const uint32_t* point_list, int N,
                const double* uv, const double* conic, const double* opacity, const double* rgb,
-               const double* bg, const float* dL_dimage, double* image, double* final_T, int* n_contrib,
-               double* grad2d, double* gscale, double* glit, double* gallow, double* iallow,
-               double* tallow, int* nc_alt, int* pix_ambig) {
+               const double* bg, const float* dL_dimage, const uint8_t* tile_mask, double* image,
+               double* final_T, int* n_contrib, double* grad2d, double* gscale, double* glit,
+               double* gallow, double* iallow, double* tallow, int* nc_alt, int* pix_ambig,
+               double* pix_widen, double* terr) {
     scene2d_t S = {W, H, uv, conic, opacity, rgb, bg};
     long long gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
     int maxlen = 1;
@@ -601,6 +606,7 @@ int orc_render(int W, int H, int tw, int th, const uint32_t* ranges, const uint3
     for (long long ty = 0; ty < gy; ++ty)
         for (long long tx = 0; tx < gx; ++tx) {
             long long t = ty * gx + tx;
+            if (tile_mask && !tile_mask[t]) continue;
             const uint32_t* list = point_list + ranges[2 * t];
             int n = (int)(ranges[2 * t + 1] - ranges[2 * t]);
             for (int yy = 0; yy < th; ++yy)
@@ -629,6 +635,8 @@ int orc_render(int W, int H, int tw, int th, const uint32_t* ranges, const uint3
                     }
                     double widen = AMBIG_SAFETY * bpix / 1e-5;
                     if (widen < 1.0) widen = 1.0;
+                    if (pix_widen) pix_widen[pix] = widen;
+                    if (terr) terr[pix] = eTf;
                     if (dL_dimage) {
                         pixel_grads(&S, cs, nc, Tf, g, gr, mg);
                         for (int j = 0; j < nc; ++j)

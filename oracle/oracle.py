@@ -53,7 +53,8 @@ def _load():
     lib.orc_bin.argtypes = [c_int, D, D, I, c_int, c_int, c_int, c_int, POINTER(c_uint64), U32, U32]
     lib.orc_bin.restype = c_int
     lib.orc_render.argtypes = [c_int, c_int, c_int, c_int, U32, U32, c_int, D, D, D, D, D,
-                               POINTER(c_float), D, D, I, D, D, D, D, D, D, I, I]
+                               POINTER(c_float), POINTER(ctypes.c_uint8), D, D, I, D, D, D, D, D, D,
+                               I, I, D, D]
     lib.orc_render.restype = c_int
     lib.orc_backproject.argtypes = [c_int, c_int, D, D, D, D, D, POINTER(OrcCamera), c_int, c_int,
                                     D, D, D, D, D, D, D, D, D, D]
@@ -130,8 +131,9 @@ def bin_sort(uv, depth, radius, W, H, tile=(16, 16)):
 
 
 def render(W, H, ranges, point_list, uv, conic, opacity, rgb, bg, dL_dimage=None, tile=(16, 16),
-           extras=True):
-    """Forward image and (if dL_dimage is given) exact FP64 grad2d [N,9]."""
+           extras=True, tile_mask=None):
+    """Forward image and (if dL_dimage is given) exact FP64 grad2d [N,9].
+    ``tile_mask`` (bool per tile) restricts the evaluation to those tiles."""
     lib = _load()
     n = len(opacity)
     uv, conic, opacity, rgb, bg = _d(uv), _d(conic), _d(opacity), _d(rgb), _d(bg)
@@ -155,13 +157,19 @@ def render(W, H, ranges, point_list, uv, conic, opacity, rgb, bg, dL_dimage=None
         out["tallow"] = np.zeros((H, W))
         out["nc_alt"] = np.zeros((H, W), np.int32)
         out["pix_ambig"] = np.zeros((H, W), np.int32)
+        out["pix_widen"] = np.ones((H, W))
+        out["terr"] = np.zeros((H, W))
+    tm = None
+    if tile_mask is not None:
+        tm = np.ascontiguousarray(tile_mask, np.uint8)
     gp = lambda k, t=c_double: _p(out[k], t) if k in out else None
     rc = lib.orc_render(W, H, tile[0], tile[1], _p(ranges, c_uint32), _p(pl, c_uint32), n,
                         _p(uv), _p(conic), _p(opacity), _p(rgb), _p(bg),
                         _p(g, c_float) if g is not None else None,
+                        _p(tm, ctypes.c_uint8) if tm is not None else None,
                         gp("image"), gp("final_T"), gp("n_contrib", c_int), gp("grad2d"),
                         gp("gscale"), gp("glit"), gp("gallow"), gp("iallow"), gp("tallow"),
-                        gp("nc_alt", c_int), gp("pix_ambig", c_int))
+                        gp("nc_alt", c_int), gp("pix_ambig", c_int), gp("pix_widen"), gp("terr"))
     if rc != 0:
         raise MemoryError("oracle render")
     return out

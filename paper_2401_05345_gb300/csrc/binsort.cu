@@ -1,0 +1,175 @@
+// Tile binning: duplicated (tile, depth) keys, stable radix sort, ranges.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+namespace {
+
+struct BinGeom {
+    int W, H, tw, th, gx, gy, twl, thl, tiles, end_bit;
+};
+
+int ilog2(int x) { int l = 0; while ((1 << l) < x) ++l; return l; }
+
+bool make_geom(int W, int H, int tw, int th, BinGeom& g) {
+    if (W <= 0 || H <= 0) return false;
+    if (!pow2_in(tw, 8, 32) || !pow2_in(th, 8, 32) || tw * th > 512) return false;
+    g.W = W; g.H = H; g.tw = tw; g.th = th;
+    g.gx = (W + tw - 1) / tw;
+    g.gy = (H + th - 1) / th;
+    g.twl = ilog2(tw); g.thl = ilog2(th);
+    g.tiles = g.gx * g.gy;
+    int bits = 0;
+    while ((1ll << bits) < (long long)g.tiles) ++bits;
+    g.end_bit = 32 + (bits > 0 ? bits : 1);
+    return true;
+}
+
+// Scratch layout (each region 256-byte aligned).
+struct Scratch {
+    uint32_t* counts;      // n + 1: tiles touched, then exclusive offsets
+    uint64_t* keys_in;     // capacity
+    uint32_t* vals_in;     // capacity
+    uint64_t* keys_out;    // capacity
+    void* cub_tmp;
+    size_t cub_bytes;
+    size_t total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int layout(int n, long long cap, char* base, Scratch& s) {
+    size_t scan_bytes = 0, sort_bytes = 0;
+    cudaError_t e = cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, (uint32_t*)nullptr,
+                                                  (uint32_t*)nullptr, n + 1);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, (uint64_t*)nullptr, (uint64_t*)nullptr,
+                                        (uint32_t*)nullptr, (uint32_t*)nullptr, (int)(cap > 0 ? cap : 1),
+                                        0, 64);
+    if (e != cudaSuccess) return cuda_fail(e);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return base ? base + o : nullptr; };
+    s.counts = (uint32_t*)take(sizeof(uint32_t) * ((size_t)n + 1));
+    s.keys_in = (uint64_t*)take(sizeof(uint64_t) * (size_t)(cap > 0 ? cap : 1));
+    s.vals_in = (uint32_t*)take(sizeof(uint32_t) * (size_t)(cap > 0 ? cap : 1));
+    s.keys_out = (uint64_t*)take(sizeof(uint64_t) * (size_t)(cap > 0 ? cap : 1));
+    s.cub_bytes = scan_bytes > sort_bytes ? scan_bytes : sort_bytes;
+    s.cub_tmp = take(s.cub_bytes);
+    s.total = off;
+    return GSR_OK;
+}
+
+__global__ void count_kernel(int n, const float* __restrict__ splat2d, const int* __restrict__ radius,
+                             BinGeom g, uint32_t* __restrict__ counts) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    uint32_t c = 0;
+    if (i < n) {
+        int r = radius[i];
+        if (r > 0) {
+            float2 uv = *reinterpret_cast<const float2*>(splat2d + (size_t)i * GSR_REC);
+            int x0, x1, y0, y1;
+            tile_rect(uv.x, uv.y, r, g.gx, g.gy, g.twl, g.thl, x0, x1, y0, y1);
+            int nt = (x1 - x0) * (y1 - y0);
+            c = nt > 0 ? (uint32_t)nt : 0u;
+        }
+    }
+    counts[i] = c;  // counts[n] = 0 so the exclusive scan ends with the total
+}
+
+__global__ void duplicate_kernel(int n, const float* __restrict__ splat2d, const int* __restrict__ radius,
+                                 BinGeom g, const uint32_t* __restrict__ offsets,
+                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = radius[i];
+    if (r <= 0) return;
+    const float* rec = splat2d + (size_t)i * GSR_REC;
+    int x0, x1, y0, y1;
+    tile_rect(rec[0], rec[1], r, g.gx, g.gy, g.twl, g.thl, x0, x1, y0, y1);
+    uint32_t o = offsets[i];
+    uint64_t dbits = (uint64_t)__float_as_uint(rec[9]);
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) {
+            keys[o] = ((uint64_t)(uint32_t)(y * g.gx + x) << 32) | dbits;
+            vals[o] = (uint32_t)i;
+            ++o;
+        }
+}
+
+__global__ void ranges_kernel(long long nkeys, const uint64_t* __restrict__ keys, uint32_t* __restrict__ ranges) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkeys) return;
+    uint32_t t = (uint32_t)(keys[k] >> 32);
+    if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != t) ranges[2 * (size_t)t] = (uint32_t)k;
+    if (k == nkeys - 1 || (uint32_t)(keys[k + 1] >> 32) != t) ranges[2 * (size_t)t + 1] = (uint32_t)(k + 1);
+}
+
+}  // namespace
+}  // namespace gsr
+
+using namespace gsr;
+
+extern "C" int gsr_bin_scratch_bytes(int32_t n, int32_t width, int32_t height, int32_t tile_w,
+                                     int32_t tile_h, int64_t key_capacity, size_t* bytes) {
+    BinGeom g;
+    if (n < 0 || key_capacity < 0 || key_capacity >= 0xffffffffll || !bytes ||
+        !make_geom(width, height, tile_w, tile_h, g))
+        return GSR_EINVAL;
+    Scratch s;
+    int rc = layout(n, key_capacity, nullptr, s);
+    if (rc != GSR_OK) return rc;
+    *bytes = s.total;
+    return GSR_OK;
+}
+
+extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                            const float* splat2d, const int32_t* radius, int64_t key_capacity,
+                            void* scratch, size_t scratch_bytes, uint32_t* point_list,
+                            uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,
+                            gsr_stream_t stream_) {
+    BinGeom g;
+    if (n < 0 || key_capacity < 0 || key_capacity >= 0xffffffffll || !n_keys ||
+        !make_geom(width, height, tile_w, tile_h, g))
+        return GSR_EINVAL;
+    if (!tile_ranges || !scratch || (n > 0 && (!splat2d || !radius)) || (key_capacity > 0 && !point_list))
+        return GSR_EINVAL;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    Scratch s;
+    int rc = layout(n, key_capacity, (char*)scratch, s);
+    if (rc != GSR_OK) return rc;
+    if (scratch_bytes < s.total) return GSR_ESCRATCH;
+    cudaError_t e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)g.tiles, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *n_keys = 0;
+    if (n == 0) return GSR_OK;
+    count_kernel<<<(n + 1 + 255) / 256, 256, 0, stream>>>(n, splat2d, radius, g, s.counts);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    size_t tb = s.cub_bytes;
+    e = cub::DeviceScan::ExclusiveSum(s.cub_tmp, tb, s.counts, s.counts, n + 1, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    uint32_t total = 0;
+    e = cudaMemcpyAsync(&total, s.counts + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *n_keys = (int64_t)total;
+    if ((long long)total > key_capacity) return GSR_ECAPACITY;
+    if (total == 0) return GSR_OK;
+    duplicate_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, splat2d, radius, g, s.counts, s.keys_in, s.vals_in);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    uint64_t* sorted_keys = keys_out ? keys_out : s.keys_out;
+    tb = 0;
+    e = cub::DeviceRadixSort::SortPairs(nullptr, tb, s.keys_in, sorted_keys, s.vals_in, point_list,
+                                        (int)total, 0, g.end_bit, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (tb > s.cub_bytes) return GSR_ESCRATCH;
+    tb = s.cub_bytes;
+    e = cub::DeviceRadixSort::SortPairs(s.cub_tmp, tb, s.keys_in, sorted_keys, s.vals_in, point_list,
+                                        (int)total, 0, g.end_bit, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    ranges_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>((long long)total, sorted_keys, tile_ranges);
+    return check_launch();
+}

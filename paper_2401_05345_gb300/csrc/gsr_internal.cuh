@@ -1,0 +1,103 @@
+// Internal device/host helpers of libgsr (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gsr.h"
+
+namespace gsr {
+
+constexpr float kDilation = 0.3f;       // screen-space covariance dilation
+constexpr float kAlphaMax = 0.99f;      // alpha cap
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 0.0001f;        // transmittance stop
+constexpr float kFrustum = 1.3f;        // clamp of x/z in the EWA Jacobian
+constexpr float kLambdaFloor = 0.1f;    // floor of the eigenvalue discriminant
+constexpr unsigned kFull = 0xffffffffu;
+
+// Records the CUDA error text for gsr_last_cuda_error().
+int cuda_fail(cudaError_t e);
+// Checks the last launch; returns GSR_OK or GSR_ECUDA.
+int check_launch();
+
+inline bool pow2_in(int x, int lo, int hi) { return x >= lo && x <= hi && (x & (x - 1)) == 0; }
+
+// Tile rectangle of a splat: the 3DGS bounding-box rule written with
+// floor(u) so it is exact integer arithmetic ([x0,x1) x [y0,y1)).
+__device__ __forceinline__ void tile_rect(float u, float v, int r, int gx, int gy, int tw_log2,
+                                          int th_log2, int& x0, int& x1, int& y0, int& y1) {
+    int fu = (int)floorf(u), fv = (int)floorf(v);
+    int tw = 1 << tw_log2, th = 1 << th_log2;
+    x0 = min(max((fu - r) >> tw_log2, 0), gx);
+    x1 = min(max((fu + r + tw - 1) >> tw_log2, 0), gx);
+    y0 = min(max((fv - r) >> th_log2, 0), gy);
+    y1 = min(max((fv + r + th - 1) >> th_log2, 0), gy);
+}
+
+// Evaluation of one splat at one pixel with a fixed sequence of IEEE
+// operations, so that the forward and the backward kernels take bit-identical
+// skip decisions:  sigma = (A dx^2 + C dy^2)/2 + B dx dy, G = exp(-sigma),
+// alpha = min(0.99, o G).  Returns false when the splat is skipped
+// (sigma < 0 or alpha < 1/255).
+struct SplatEval {
+    float dx, dy, sigma, G, alpha;
+    bool capped;
+};
+
+__device__ __forceinline__ bool eval_splat(float u, float v, float A, float B, float C, float o,
+                                           float px, float py, SplatEval& e) {
+    e.dx = __fsub_rn(u, px);
+    e.dy = __fsub_rn(v, py);
+    float q = __fmaf_rn(C, __fmul_rn(e.dy, e.dy), __fmul_rn(A, __fmul_rn(e.dx, e.dx)));
+    e.sigma = __fmaf_rn(0.5f, q, __fmul_rn(B, __fmul_rn(e.dx, e.dy)));
+    if (e.sigma < 0.0f) return false;
+    e.G = __expf(-e.sigma);
+    float oG = __fmul_rn(o, e.G);
+    e.capped = oG > kAlphaMax;
+    e.alpha = e.capped ? kAlphaMax : oG;
+    return e.alpha >= kAlphaMin;
+}
+
+// pair step of the transposing reduce-scatter: lanes with bit b set keep y
+// and send x, the others keep x and send y; the kept value gains the
+// partner's copy of it.
+__device__ __forceinline__ float pair_step(float x, float y, bool b, int off) {
+    float send = b ? x : y;
+    float keep = b ? y : x;
+    return keep + __shfl_xor_sync(kFull, send, off);
+}
+
+// Sums 9 per-lane values over the full warp in 12 shuffles (instead of the
+// 45 of nine butterflies): every halving step exchanges half of the values
+// still held, so lanes end up owning different parameters.  On return, lane
+// L holds the warp total of parameter reduce9_param(L) when that is <= 8.
+__device__ __forceinline__ float reduce9(const float v[9], int lane) {
+    bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float w0 = pair_step(v[0], v[1], b4, 16);
+    float w1 = pair_step(v[2], v[3], b4, 16);
+    float w2 = pair_step(v[4], v[5], b4, 16);
+    float w3 = pair_step(v[6], v[7], b4, 16);
+    float w4 = pair_step(v[8], 0.0f, b4, 16);
+    float x0 = pair_step(w0, w1, b3, 8);
+    float x1 = pair_step(w2, w3, b3, 8);
+    float x2 = pair_step(w4, 0.0f, b3, 8);
+    float y0 = pair_step(x0, x1, b2, 4);
+    float y1 = pair_step(x2, 0.0f, b2, 4);
+    float z = pair_step(y0, y1, b1, 2);
+    return z + __shfl_xor_sync(kFull, z, 1);
+}
+
+// Parameter index owned by lane L after reduce9 (>= 9: padding / duplicate).
+__device__ __forceinline__ int reduce9_param(int lane) {
+    int b1 = (lane >> 1) & 1, b2 = (lane >> 2) & 1, b3 = (lane >> 3) & 1, b4 = (lane >> 4) & 1;
+    if (lane & 1) return 16;  // odd lanes hold a copy of the even lane's sum
+    if (b1) return (b2 | b3 | b4) ? 16 : 8;
+    return 4 * b2 + 2 * b3 + b4;
+}
+
+__device__ __forceinline__ void red_add(float* addr, float v) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(v) : "memory");
+}
+
+}  // namespace gsr

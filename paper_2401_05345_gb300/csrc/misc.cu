@@ -1,0 +1,139 @@
+// Status strings, loss, optimizer, and the L2 red microbenchmark.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+static thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e) {
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return GSR_ECUDA;
+}
+
+int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GSR_OK : cuda_fail(e);
+}
+
+namespace {
+
+__global__ void l1_kernel(long long count, const float* __restrict__ img, const float* __restrict__ tgt,
+                          float* __restrict__ grad, float* __restrict__ loss) {
+    float acc = 0.0f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        float d = img[i] - tgt[i];
+        grad[i] = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
+        acc += fabsf(d);
+    }
+    if (!loss) return;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    __shared__ float s[32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (threadIdx.x == 0) atomicAdd(loss, acc);
+    }
+}
+
+__global__ void adam_kernel(long long n, float* __restrict__ p, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
+                            float eps, float bc1, float bc2) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float gi = g[i];
+        float mi = b1 * m[i] + (1.0f - b1) * gi;
+        float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+// pattern 0: own address per lane; 1: one address per warp; 2: 9 lanes to a
+// 48-byte record; 3: 9 adds per lane into one record per warp.
+__global__ void __launch_bounds__(256) red_bench_kernel(int pattern, int iters, float* __restrict__ buf,
+                                                        long long nfloats) {
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gwarp = gtid >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long nrec = nfloats / GSR_REC;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (int it = 0; it < iters; ++it) {
+        const long long w = (gwarp + (long long)it * nwarps) % nrec;  // record touched by this warp
+        float* rec = buf + w * GSR_REC;
+        if (pattern == 0) {
+            long long a = (gtid + (long long)it * gridDim.x * blockDim.x) % nfloats;
+            red_add(buf + a, 1.0f);
+        } else if (pattern == 1) {
+            red_add(rec, 1.0f);
+        } else if (pattern == 2) {
+            if (lane < 9) red_add(rec + lane, 1.0f);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) red_add(rec + q, 1.0f);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace gsr
+
+using namespace gsr;
+
+extern "C" const char* gsr_status_string(int status) {
+    switch (status) {
+        case GSR_OK: return "ok";
+        case GSR_EINVAL: return "invalid argument";
+        case GSR_ECAPACITY: return "duplicated keys exceed key_capacity";
+        case GSR_ECUDA: return "CUDA error";
+        case GSR_ETIMEOUT: return "bounded device wait timed out";
+        case GSR_ESCRATCH: return "scratch buffer too small";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* gsr_last_cuda_error(void) { return g_cuda_err; }
+
+extern "C" int gsr_version(void) { return 100; }
+
+extern "C" int gsr_l1_loss(int64_t count, const float* image, const float* target, float* dL_dimage,
+                           float* loss_sum, gsr_stream_t stream) {
+    if (count < 0 || (count > 0 && (!image || !target || !dL_dimage))) return GSR_EINVAL;
+    if (count == 0) return GSR_OK;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    l1_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(count, image, target, dL_dimage, loss_sum);
+    return check_launch();
+}
+
+extern "C" int gsr_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr,
+                             float beta1, float beta2, float eps, int32_t step, gsr_stream_t stream) {
+    if (n < 0 || step < 1 || (n > 0 && (!param || !grad || !m || !v))) return GSR_EINVAL;
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f)) return GSR_EINVAL;
+    if (n == 0) return GSR_OK;
+    float bc1 = (float)(1.0 - pow((double)beta1, (double)step));
+    float bc2 = (float)(1.0 - pow((double)beta2, (double)step));
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    adam_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(n, param, grad, m, v, lr, beta1, beta2, eps,
+                                                                bc1, bc2);
+    return check_launch();
+}
+
+extern "C" int gsr_bench_red(int32_t pattern, int32_t blocks, int32_t iters, float* buffer,
+                             int64_t buffer_floats, int64_t* adds, gsr_stream_t stream) {
+    if (pattern < 0 || pattern > 3 || blocks <= 0 || iters <= 0 || !buffer || buffer_floats < 32 * GSR_REC || !adds)
+        return GSR_EINVAL;
+    long long threads = (long long)blocks * 256, warps = threads / 32;
+    long long per_iter = pattern == 0 ? threads : pattern == 1 ? threads : pattern == 2 ? warps * 9 : threads * 9;
+    *adds = per_iter * iters;
+    red_bench_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(pattern, iters, buffer, buffer_floats);
+    return check_launch();
+}

@@ -1,0 +1,324 @@
+// Forward blend and backward blend + per-splat gradient accumulation.
+//
+// One CTA per screen tile, one thread per pixel.  The tile's depth-sorted
+// splat list is staged through shared memory in batches of one entry per
+// thread (coalesced id load, three 16-byte record loads per entry); every
+// thread then walks the whole batch, so all 32 lanes of a warp evaluate the
+// same splat at the same time -- the property that makes the warp-level
+// reduction of the backward legal without a match (Sec. V-A2 requires all
+// lanes to update the same primitive; here it holds by construction).
+#include "gsr_internal.cuh"
+
+namespace gsr {
+namespace {
+
+struct RasterGeom {
+    int W, H, gx, gy;
+};
+
+// Front-to-back walk of one pixel over its tile list (shared by the forward
+// kernel and the recompute mode of the backward, so both produce the same
+// final transmittance and last contributor bit for bit).  All threads of the
+// CTA must call it.
+template <int B, bool COLOR>
+__device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict__ point_list,
+                                           const float* __restrict__ splat2d, float px, float py,
+                                           bool inside, float4* s_a, float4* s_b, float* s_c,
+                                           float& T, int& last, float& C0, float& C1, float& C2) {
+    const int n = (int)(rg.y - rg.x);
+    bool done = !inside;
+    T = 1.0f;
+    last = 0;
+    C0 = C1 = C2 = 0.0f;
+    for (int base = 0; base < n; base += B) {
+        if (__syncthreads_count(done) == B) break;
+        int idx = base + (int)threadIdx.x;
+        if (idx < n) {
+            uint32_t id = point_list[rg.x + idx];
+            const float4* rec = reinterpret_cast<const float4*>(splat2d + (size_t)id * GSR_REC);
+            s_a[threadIdx.x] = rec[0];
+            s_b[threadIdx.x] = rec[1];
+            if (COLOR) s_c[threadIdx.x] = rec[2].x;
+        }
+        __syncthreads();
+        const int cnt = min(B, n - base);
+        for (int k = 0; k < cnt && !done; ++k) {
+            float4 a = s_a[k], b = s_b[k];
+            SplatEval e;
+            if (!eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, px, py, e)) continue;
+            float testT = __fmul_rn(T, __fsub_rn(1.0f, e.alpha));
+            if (testT < kTMin) {
+                done = true;
+                break;
+            }
+            if (COLOR) {
+                float w = __fmul_rn(e.alpha, T);
+                C0 = __fmaf_rn(b.z, w, C0);
+                C1 = __fmaf_rn(b.w, w, C1);
+                C2 = __fmaf_rn(s_c[k], w, C2);
+            }
+            T = testT;
+            last = base + k + 1;
+        }
+    }
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW* TH)
+forward_kernel(RasterGeom g, const uint2* __restrict__ ranges, const uint32_t* __restrict__ point_list,
+               const float* __restrict__ splat2d, float bg0, float bg1, float bg2,
+               float* __restrict__ image, float* __restrict__ final_T, int* __restrict__ n_contrib) {
+    constexpr int B = TW * TH;
+    __shared__ float4 s_a[B];
+    __shared__ float4 s_b[B];
+    __shared__ float s_c[B];
+    const int tile = blockIdx.x;
+    const int tx = tile % g.gx, ty = tile / g.gx;
+    const int px = tx * TW + (int)threadIdx.x % TW, py = ty * TH + (int)threadIdx.x / TW;
+    const bool inside = px < g.W && py < g.H;
+    float T, C0, C1, C2;
+    int last;
+    walk_front<B, true>(ranges[tile], point_list, splat2d, (float)px, (float)py, inside, s_a, s_b, s_c,
+                        T, last, C0, C1, C2);
+    if (inside) {
+        const size_t HW = (size_t)g.W * g.H, pix = (size_t)py * g.W + px;
+        image[pix] = __fmaf_rn(T, bg0, C0);
+        image[HW + pix] = __fmaf_rn(T, bg1, C1);
+        image[2 * HW + pix] = __fmaf_rn(T, bg2, C2);
+        if (final_T) final_T[pix] = T;
+        if (n_contrib) n_contrib[pix] = last;
+    }
+}
+
+struct BwdArgs {
+    RasterGeom g;
+    const uint2* ranges;
+    const uint32_t* point_list;
+    const float* splat2d;
+    float bg0, bg1, bg2;
+    const float* final_T;
+    const int* n_contrib;
+    const float* dL_dimage;
+    float* grad2d;
+    int threshold;
+};
+
+// Pixel of thread (warp w, lane l) inside a TW x TH tile.
+template <int TW, int LAYOUT>
+__device__ __forceinline__ void lane_pixel(int tid, int& lx, int& ly) {
+    if (LAYOUT == 0) {  // row-major: a warp covers 32 consecutive pixels
+        lx = tid % TW;
+        ly = tid / TW;
+    } else {            // 8 x 4 pixel blocks per warp
+        const int w = tid >> 5, l = tid & 31;
+        constexpr int WX = TW / 8;
+        lx = (w % WX) * 8 + (l & 7);
+        ly = (w / WX) * 4 + (l >> 3);
+    }
+}
+
+template <int TW, int TH, int MODE, int LAYOUT, bool STORE_T>
+__global__ void __launch_bounds__(TW* TH)
+backward_kernel(BwdArgs p) {
+    constexpr int B = TW * TH;
+    __shared__ float4 s_a[B];
+    __shared__ float4 s_b[B];
+    __shared__ float s_c[B];
+    __shared__ uint32_t s_id[B];
+    __shared__ float s_acc[MODE == GSR_REDUCE_BLOCK ? B * 9 : 1];
+    __shared__ int s_maxlast;
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int tile = blockIdx.x;
+    const int tx = tile % p.g.gx, ty = tile / p.g.gx;
+    int lx, ly;
+    lane_pixel<TW, LAYOUT>(tid, lx, ly);
+    const int px = tx * TW + lx, py = ty * TH + ly;
+    const bool inside = px < p.g.W && py < p.g.H;
+    const float fpx = (float)px, fpy = (float)py;
+    const uint2 rg = p.ranges[tile];
+    const size_t HW = (size_t)p.g.W * p.g.H, pix = (size_t)py * p.g.W + px;
+
+    float Tf;
+    int last;
+    const int nlist = (int)(rg.y - rg.x);
+    if (STORE_T) {
+        Tf = inside ? p.final_T[pix] : 0.0f;
+        last = inside ? min(max(p.n_contrib[pix], 0), nlist) : 0;  // never walk past the list
+    } else {
+        float c0, c1, c2;
+        walk_front<B, false>(rg, p.point_list, p.splat2d, fpx, fpy, inside, s_a, s_b, s_c, Tf, last, c0, c1, c2);
+        if (!inside) { Tf = 0.0f; last = 0; }
+    }
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (inside) {
+        g0 = p.dL_dimage[pix];
+        g1 = p.dL_dimage[HW + pix];
+        g2 = p.dL_dimage[2 * HW + pix];
+    }
+    if (tid == 0) s_maxlast = 0;
+    if (MODE == GSR_REDUCE_BLOCK)
+        for (int i = tid; i < B * 9; i += B) s_acc[i] = 0.0f;
+    __syncthreads();
+    const int wlast = __reduce_max_sync(kFull, last);
+    if (lane == 0) atomicMax(&s_maxlast, wlast);
+    __syncthreads();
+    const int maxlast = s_maxlast;
+
+    float T = Tf;
+    float S = Tf * (p.bg0 * g0 + p.bg1 * g1 + p.bg2 * g2);
+    const int rparam = reduce9_param(lane);
+    float* __restrict__ grad = p.grad2d;
+
+    for (int top = maxlast; top > 0; top -= B) {
+        const int cnt = min(B, top);
+        __syncthreads();
+        if (tid < cnt) {
+            uint32_t id = p.point_list[rg.x + (uint32_t)(top - 1 - tid)];
+            const float4* rec = reinterpret_cast<const float4*>(p.splat2d + (size_t)id * GSR_REC);
+            s_id[tid] = id;
+            s_a[tid] = rec[0];
+            s_b[tid] = rec[1];
+            s_c[tid] = rec[2].x;
+        }
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) {
+            const int pos = top - 1 - k;
+            if (pos >= wlast) continue;  // warp-uniform: no lane of this warp reaches pos
+            const float4 a = s_a[k], b = s_b[k];
+            SplatEval e;
+            const bool active = (pos < last) && eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, fpx, fpy, e);
+            float v[9];
+            if (active) {
+                const float inv = __frcp_rn(1.0f - e.alpha);
+                const float Tj = T * inv;
+                const float cb = s_c[k];
+                const float cg = b.z * g0 + b.w * g1 + cb * g2;
+                const float dal = Tj * cg - S * inv;
+                const float w = e.alpha * Tj;
+                S = fmaf(cg, w, S);
+                T = Tj;
+                v[6] = w * g0;
+                v[7] = w * g1;
+                v[8] = w * g2;
+                const float dsig = e.capped ? 0.0f : -b.y * e.G * dal;
+                v[5] = e.capped ? 0.0f : e.G * dal;
+                v[0] = (a.z * e.dx + a.w * e.dy) * dsig;
+                v[1] = (a.w * e.dx + b.x * e.dy) * dsig;
+                v[2] = 0.5f * e.dx * e.dx * dsig;
+                v[3] = e.dx * e.dy * dsig;
+                v[4] = 0.5f * e.dy * e.dy * dsig;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) v[q] = 0.0f;
+            }
+            float* rec = grad + (size_t)s_id[k] * GSR_REC;
+            if (MODE == GSR_REDUCE_PLAIN) {
+                if (active) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) atomicAdd(rec + q, v[q]);
+                }
+            } else {
+                const unsigned m = __ballot_sync(kFull, active);
+                if (m == 0u) continue;
+                const bool dense = (MODE == GSR_REDUCE_WARP) || (__popc(m) >= p.threshold);
+                if (dense) {
+                    const float z = reduce9(v, lane);
+                    if (rparam < 9) {
+                        if (MODE == GSR_REDUCE_BLOCK) atomicAdd(&s_acc[k * 9 + rparam], z);
+                        else red_add(rec + rparam, z);
+                    }
+                } else if (active) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        if (MODE == GSR_REDUCE_BLOCK) atomicAdd(&s_acc[k * 9 + q], v[q]);
+                        else atomicAdd(rec + q, v[q]);
+                    }
+                }
+            }
+        }
+        if (MODE == GSR_REDUCE_BLOCK) {
+            __syncthreads();
+            for (int i = tid; i < cnt * 9; i += B) {
+                const float val = s_acc[i];
+                if (val != 0.0f) {
+                    const int k = i / 9;
+                    red_add(grad + (size_t)s_id[k] * GSR_REC + (i - 9 * k), val);
+                    s_acc[i] = 0.0f;
+                }
+            }
+        }
+    }
+}
+
+template <int MODE, int LAYOUT, bool STORE_T>
+void launch_bwd(int tiles, const BwdArgs& a, cudaStream_t s) {
+    backward_kernel<16, 16, MODE, LAYOUT, STORE_T><<<tiles, 256, 0, s>>>(a);
+}
+
+template <int MODE>
+void launch_bwd_mode(int layout, bool store, int tiles, const BwdArgs& a, cudaStream_t s) {
+    if (layout == 0) {
+        if (store) launch_bwd<MODE, 0, true>(tiles, a, s);
+        else launch_bwd<MODE, 0, false>(tiles, a, s);
+    } else {
+        if (store) launch_bwd<MODE, 1, true>(tiles, a, s);
+        else launch_bwd<MODE, 1, false>(tiles, a, s);
+    }
+}
+
+}  // namespace
+}  // namespace gsr
+
+using namespace gsr;
+
+extern "C" int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                           const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
+                           const float* bg, float* image, float* final_T, int32_t* n_contrib,
+                           gsr_stream_t stream) {
+    if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !bg || !image) return GSR_EINVAL;
+    if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
+    RasterGeom g{width, height, (width + 15) / 16, (height + 15) / 16};
+    int tiles = g.gx * g.gy;
+    forward_kernel<16, 16><<<tiles, 256, 0, (cudaStream_t)stream>>>(
+        g, reinterpret_cast<const uint2*>(tile_ranges), point_list, splat2d, bg[0], bg[1], bg[2], image,
+        final_T, n_contrib);
+    return check_launch();
+}
+
+extern "C" int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                            const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
+                            const float* bg, const float* final_T, const int32_t* n_contrib,
+                            const float* dL_dimage, float* grad2d, const gsr_backward_opts* opts,
+                            gsr_stream_t stream_) {
+    gsr_backward_opts o = {GSR_REDUCE_WARP, 0, 0, 1, {0, 0, 0, 0}};
+    if (opts) o = *opts;
+    if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !bg || !dL_dimage || !grad2d) return GSR_EINVAL;
+    if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
+    if (o.reduce_mode < GSR_REDUCE_PLAIN || o.reduce_mode > GSR_REDUCE_BLOCK) return GSR_EINVAL;
+    if (o.threshold < 0 || o.threshold > 33 || (o.lane_layout != 0 && o.lane_layout != 1)) return GSR_EINVAL;
+    if (o.store_T != 0 && o.store_T != 1) return GSR_EINVAL;
+    for (int i = 0; i < 4; ++i) if (o.reserved[i] != 0) return GSR_EINVAL;
+    if (o.store_T && (!final_T || !n_contrib)) return GSR_EINVAL;
+    BwdArgs a;
+    a.g = RasterGeom{width, height, (width + 15) / 16, (height + 15) / 16};
+    a.ranges = reinterpret_cast<const uint2*>(tile_ranges);
+    a.point_list = point_list;
+    a.splat2d = splat2d;
+    a.bg0 = bg[0]; a.bg1 = bg[1]; a.bg2 = bg[2];
+    a.final_T = final_T;
+    a.n_contrib = n_contrib;
+    a.dL_dimage = dL_dimage;
+    a.grad2d = grad2d;
+    a.threshold = o.threshold;
+    const int tiles = a.g.gx * a.g.gy;
+    cudaStream_t s = (cudaStream_t)stream_;
+    const bool st = o.store_T != 0;
+    switch (o.reduce_mode) {
+        case GSR_REDUCE_PLAIN: launch_bwd_mode<GSR_REDUCE_PLAIN>(o.lane_layout, st, tiles, a, s); break;
+        case GSR_REDUCE_WARP: launch_bwd_mode<GSR_REDUCE_WARP>(o.lane_layout, st, tiles, a, s); break;
+        case GSR_REDUCE_HYBRID: launch_bwd_mode<GSR_REDUCE_HYBRID>(o.lane_layout, st, tiles, a, s); break;
+        default: launch_bwd_mode<GSR_REDUCE_BLOCK>(o.lane_layout, st, tiles, a, s); break;
+    }
+    return check_launch();
+}

@@ -1,0 +1,115 @@
+"""Per-view device buffers and the render / backward sequence over libgsr.
+
+``SceneTensors`` holds one scene's parameters on the device; ``ViewBuffers``
+holds everything one rendered view needs (2D splat records, bins, images) and
+grows its key capacity when binning reports GSR_ECAPACITY.  All arithmetic
+runs in libgsr kernels; this module only allocates and sequences calls.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import gsr
+
+TILE = (16, 16)
+
+
+@dataclasses.dataclass
+class SceneTensors:
+    mean: torch.Tensor
+    scale: torch.Tensor
+    quat: torch.Tensor
+    opacity: torch.Tensor
+    feat: torch.Tensor
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.mean.shape[0])
+
+    @staticmethod
+    def from_scene(scene, device="cuda") -> "SceneTensors":
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
+        return SceneTensors(t(scene.mean), t(scene.scale), t(scene.quat), t(scene.opacity),
+                            t(scene.feat), int(scene.sh_degree))
+
+    def zeros_like_params(self):
+        z = torch.zeros_like
+        return SceneTensors(z(self.mean), z(self.scale), z(self.quat), z(self.opacity), z(self.feat),
+                            self.sh_degree)
+
+    def tensors(self):
+        return [self.mean, self.scale, self.quat, self.opacity, self.feat]
+
+    def nbytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in self.tensors())
+
+
+class ViewBuffers:
+    """Buffers of one (scene, camera) view."""
+
+    def __init__(self, n, cam, device="cuda", key_capacity=None, store_T=True):
+        self.n = int(n)
+        self.cam = cam
+        self.c_cam = gsr.camera(cam)
+        self.W, self.H = int(cam.width), int(cam.height)
+        self.tw, self.th = TILE
+        self.gx = (self.W + self.tw - 1) // self.tw
+        self.gy = (self.H + self.th - 1) // self.th
+        self.device = device
+        f32 = dict(dtype=torch.float32, device=device)
+        self.splat2d = torch.zeros((max(self.n, 1), gsr.GSR_REC), **f32)
+        self.radius = torch.zeros(max(self.n, 1), dtype=torch.int32, device=device)
+        self.grad2d = torch.zeros((max(self.n, 1), gsr.GSR_REC), **f32)
+        self.tile_ranges = torch.zeros((self.gx * self.gy, 2), dtype=torch.int32, device=device)
+        self.image = torch.zeros((3, self.H, self.W), **f32)
+        self.final_T = torch.zeros((self.H, self.W), **f32) if store_T else None
+        self.n_contrib = torch.zeros((self.H, self.W), dtype=torch.int32, device=device) if store_T else None
+        self.n_keys = 0
+        self._alloc_keys(key_capacity if key_capacity is not None else max(1024, 8 * self.n))
+
+    def _alloc_keys(self, cap):
+        self.key_capacity = int(cap)
+        self.point_list = torch.zeros(max(self.key_capacity, 1), dtype=torch.int32, device=self.device)
+        sb = gsr.gsr_bin_scratch_bytes(self.n, self.W, self.H, self.tw, self.th, self.key_capacity)
+        self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
+
+    def device_bytes(self) -> int:
+        ts = [self.splat2d, self.radius, self.grad2d, self.tile_ranges, self.image, self.point_list,
+              self.scratch]
+        ts += [t for t in (self.final_T, self.n_contrib) if t is not None]
+        return sum(t.numel() * t.element_size() for t in ts)
+
+    # -- stages ------------------------------------------------------------
+    def preprocess(self, sc: SceneTensors, zero_grad=True, stream=None):
+        gsr.gsr_preprocess(self.n, sc.sh_degree, sc.mean, sc.scale, sc.quat, sc.opacity, sc.feat,
+                           self.c_cam, self.tw, self.th, self.splat2d, self.radius,
+                           self.grad2d if zero_grad else None, stream)
+
+    def bin(self, stream=None, keys_out=None):
+        while True:
+            st, nk = gsr.gsr_bin_sort(self.n, self.W, self.H, self.tw, self.th, self.splat2d, self.radius,
+                                      self.key_capacity, self.scratch, self.point_list, self.tile_ranges,
+                                      keys_out, stream)
+            self.n_keys = nk
+            if st == gsr.GSR_OK:
+                return nk
+            if keys_out is not None:
+                raise RuntimeError("keys_out smaller than the key count %d" % nk)
+            self._alloc_keys(int(nk * 1.25) + 1024)
+
+    def forward(self, bg, stream=None):
+        gsr.gsr_forward(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
+                        bg, self.image, self.final_T, self.n_contrib, stream)
+
+    def backward(self, bg, dL_dimage, opts=None, stream=None):
+        gsr.gsr_backward(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
+                         bg, self.final_T, self.n_contrib, dL_dimage, self.grad2d, opts, stream)
+
+    def backward_project(self, sc: SceneTensors, grads: SceneTensors, stream=None):
+        gsr.gsr_backward_project(self.n, sc.sh_degree, sc.mean, sc.scale, sc.quat, sc.opacity, sc.feat,
+                                 self.c_cam, self.radius, self.grad2d, grads.mean, grads.scale, grads.quat,
+                                 grads.opacity, grads.feat, stream)

@@ -1,0 +1,348 @@
+"""CUDA path against the FP64 oracle, stage by stage, element by element.
+
+Each stage of the CUDA library is fed the oracle's own stage inputs (the
+oracle's projection rounded to the FP32 record format), so a mismatch points
+at exactly one kernel.  Integer and index outputs must agree bit for bit,
+except where the oracle shows that FP32 may legitimately decide a comparison
+the other way (then the result must be one of the two valid outcomes).
+Floating-point outputs: |gpu - oracle| <= 1e-5 * scale + 1e-7 + allowance,
+scale = sum of the absolute values of the terms summed (widened where FP32
+evaluation of alpha near 1 is ill-conditioned), allowance = difference
+between the two valid outcomes of an FP32-ambiguous decision.
+"""
+import numpy as np
+import pytest
+import torch
+
+from _helpers import check_scaled, pack_records, records_f64
+from paper_2401_05345_gb300 import gsr
+from paper_2401_05345_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_05345_gb300 import build
+    build.build()
+    gsr.lib()
+    return torch.device("cuda")
+
+
+def T(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def N(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+# ----------------------------------------------------------------------------
+# workloads (seeded, small enough for the full oracle, several tiles and a
+# ragged tail; "dense" has lists longer than one 256-entry batch)
+# ----------------------------------------------------------------------------
+
+def workload(name, seed=0):
+    if name == "tiny":
+        return S.tiny_workload(seed)
+    if name == "ragged_sh3":
+        return S.gmm_scene(seed, 3000, 16, (-3.5, 0.5), 3), S.front_camera(77, 53)
+    if name == "dense_sh1":
+        return S.gmm_scene(seed, 20000, 32, (-3.2, 0.4), 1), S.front_camera(200, 150)
+    if name == "offaxis_sh2":
+        cam = S.look_at_camera((1.5, -1.0, -3.2), (0.1, 0.0, 0.2), 143, 97)
+        return S.gmm_scene(seed, 8000, 24, (-3.4, 0.5), 2), cam
+    raise KeyError(name)
+
+
+WORKLOADS = ["tiny", "ragged_sh3", "dense_sh1", "offaxis_sh2"]
+_cache = {}
+
+
+def oracle_stage(orc, name, bg=(0.0, 0.0, 0.0)):
+    key = (name, tuple(bg))
+    if key in _cache:
+        return _cache[key]
+    scene, cam = workload(name)
+    pp = orc.preprocess(scene, cam)
+    rec, radius = pack_records(pp)
+    r64 = records_f64(rec)
+    keys, pl, ranges = orc.bin_sort(r64["uv"], r64["depth"], radius, cam.width, cam.height)
+    g = S.upstream_grad(7, cam.width, cam.height)
+    out = orc.render(cam.width, cam.height, ranges, pl, r64["uv"], r64["conic"], r64["opacity"], r64["rgb"],
+                     np.asarray(bg, np.float64), g)
+    res = dict(scene=scene, cam=cam, pp=pp, rec=rec, radius=radius, keys=keys, pl=pl, ranges=ranges, g=g,
+               out=out, bg=np.asarray(bg, np.float32))
+    _cache[key] = res
+    return res
+
+
+# ----------------------------------------------------------------------------
+# a1: projection
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_preprocess_matches_oracle(dev, orc, name):
+    scene, cam = workload(name)
+    pp = orc.preprocess(scene, cam)
+    n = scene.n
+    splat = torch.zeros((n, 12), device=dev)
+    radius = torch.zeros(n, dtype=torch.int32, device=dev)
+    gz = torch.full((n, 12), 7.0, device=dev)
+    feat = T(scene.feat.reshape(n, -1))
+    gsr.gsr_preprocess(n, scene.sh_degree, T(scene.mean), T(scene.scale), T(scene.quat), T(scene.opacity),
+                       feat, cam, 16, 16, splat, radius, gz)
+    rec, rad = N(splat), N(radius)
+    assert np.all(N(gz) == 0.0)
+    amb = pp["pp_ambig"] != 0
+    exact = ~amb
+    np.testing.assert_array_equal(rad[exact], pp["radius"][exact])
+    # ambiguous ones: either the same, a neighbouring ceiling, or the cull flipped
+    d = np.abs(rad[amb].astype(np.int64) - pp["radius"][amb])
+    assert np.all((d <= 1) | (rad[amb] == 0) | (pp["radius"][amb] == 0))
+    vis = (rad > 0) & (pp["radius"] > 0)
+    assert vis.sum() > 0.5 * n or name == "offaxis_sh2"
+    # u, v: scale = |fx x / z| + |cx|
+    for c, cc in ((0, cam.cx), (1, cam.cy)):
+        ref = pp["uv"][:, c]
+        check_scaled(f"{name} uv{c}", rec[vis, c], ref[vis], np.abs(ref[vis] - cc) + abs(cc))
+    # conic: relative to |A|+|B|+|C| times the conditioning of the 2x2 inverse
+    A, B, C = pp["conic"][:, 0], pp["conic"][:, 1], pp["conic"][:, 2]
+    kap = (np.abs(A * C) + B * B) / (A * C - B * B + 1e-300)
+    sc = (np.abs(A) + np.abs(B) + np.abs(C)) * np.maximum(kap, 1.0)
+    for j in range(3):
+        check_scaled(f"{name} conic{j}", rec[vis, 2 + j], pp["conic"][vis, j], sc[vis])
+    np.testing.assert_array_equal(rec[vis, 5], scene.opacity[vis])
+    # colour: scale = sum of |SH coefficients| + 0.5 (|Y_lm| <= 1 for degree <= 3)
+    f = np.abs(scene.feat.astype(np.float64)).reshape(n, -1, 3).sum(1) + 0.5
+    check_scaled(f"{name} rgb", rec[vis, 6:9], pp["rgb"][vis], f[vis])
+    # depth: scale = sum |R_z . mean| + |t_z|
+    V = cam.view.astype(np.float64)
+    zs = np.abs(scene.mean.astype(np.float64)) @ np.abs(V[2, :3]) + abs(V[2, 3])
+    check_scaled(f"{name} depth", rec[vis, 9], pp["depth"][vis], zs[vis])
+    culled = rad == 0
+    assert np.all(rec[culled] == 0.0)
+
+
+# ----------------------------------------------------------------------------
+# a2: binning -- bit-exact
+# ----------------------------------------------------------------------------
+
+def gpu_bin(dev, rec, radius, W, H, cap):
+    n = len(rec)
+    splat, rad = T(rec), T(radius)
+    sb = gsr.gsr_bin_scratch_bytes(n, W, H, 16, 16, cap)
+    scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
+    pl = torch.zeros(max(cap, 1), dtype=torch.int32, device=dev)
+    gx, gy = (W + 15) // 16, (H + 15) // 16
+    ranges = torch.full((gx * gy, 2), -1, dtype=torch.int32, device=dev)
+    keys = torch.zeros(max(cap, 1), dtype=torch.int64, device=dev)
+    st, nk = gsr.gsr_bin_sort(n, W, H, 16, 16, splat, rad, cap, scratch, pl, ranges, keys)
+    return st, nk, pl, ranges, keys
+
+
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_bin_sort_bit_exact(dev, orc, name):
+    st_ = oracle_stage(orc, name)
+    cam = st_["cam"]
+    nref = len(st_["pl"])
+    st, nk, pl, ranges, keys = gpu_bin(dev, st_["rec"], st_["radius"], cam.width, cam.height, nref + 100)
+    assert st == gsr.GSR_OK and nk == nref
+    np.testing.assert_array_equal(N(keys)[:nk].view(np.uint64), st_["keys"])
+    np.testing.assert_array_equal(N(pl)[:nk].view(np.uint32), st_["pl"])
+    np.testing.assert_array_equal(N(ranges).view(np.uint32), st_["ranges"])
+
+
+def test_bin_sort_capacity_overflow_then_regrow(dev, orc):
+    st_ = oracle_stage(orc, "tiny")
+    cam = st_["cam"]
+    nref = len(st_["pl"])
+    st, nk, pl, ranges, keys = gpu_bin(dev, st_["rec"], st_["radius"], cam.width, cam.height, nref - 1)
+    assert st == gsr.GSR_ECAPACITY and nk == nref
+    st, nk, pl, ranges, keys = gpu_bin(dev, st_["rec"], st_["radius"], cam.width, cam.height, nref)
+    assert st == gsr.GSR_OK
+    np.testing.assert_array_equal(N(pl)[:nk].view(np.uint32), st_["pl"])
+
+
+# ----------------------------------------------------------------------------
+# a3: forward blend
+# ----------------------------------------------------------------------------
+
+def gpu_forward(dev, st_):
+    cam = st_["cam"]
+    W, H = cam.width, cam.height
+    image = torch.zeros((3, H, W), device=dev)
+    fT = torch.zeros((H, W), device=dev)
+    nc = torch.zeros((H, W), dtype=torch.int32, device=dev)
+    ranges = T(st_["ranges"].view(np.int32))
+    pl = T(np.concatenate([st_["pl"], [0]]).astype(np.uint32).view(np.int32))
+    splat = T(st_["rec"])
+    gsr.gsr_forward(W, H, 16, 16, ranges, pl, splat, st_["bg"], image, fT, nc)
+    return dict(image=image, final_T=fT, n_contrib=nc, ranges=ranges, pl=pl, splat=splat)
+
+
+def check_forward(name, got, out):
+    check_scaled(f"{name} image", got["image"], out["image"], np.abs(out["image"]) * out["pix_widen"][None],
+                 out["iallow"])
+    check_scaled(f"{name} final_T", got["final_T"], out["final_T"],
+                 out["final_T"] * np.maximum(1.0, 8 * out["terr"] / 1e-5), out["tallow"])
+    nc = got["n_contrib"]
+    ok = (nc == out["n_contrib"]) | ((out["pix_ambig"] > 0) & (nc == out["nc_alt"]))
+    assert ok.all(), f"{name} n_contrib: {(~ok).sum()} pixels differ"
+
+
+@pytest.mark.parametrize("bg", [(0.0, 0.0, 0.0), (0.3, 0.7, 0.1)])
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_forward_matches_oracle(dev, orc, name, bg):
+    st_ = oracle_stage(orc, name, bg)
+    r = gpu_forward(dev, st_)
+    got = {k: N(r[k]) for k in ("image", "final_T", "n_contrib")}
+    check_forward(name, got, st_["out"])
+
+
+# ----------------------------------------------------------------------------
+# a4-a6: backward blend + gradient accumulation, every tier
+# ----------------------------------------------------------------------------
+
+TIERS = [("plain", 0, 0), ("warp", 0, 0), ("warp", 0, 1), ("hybrid", 8, 0), ("hybrid", 16, 1),
+         ("hybrid", 33, 0), ("block", 0, 0), ("block", 12, 1)]
+
+
+@pytest.mark.parametrize("store_T", [True, False])
+@pytest.mark.parametrize("tier", TIERS, ids=lambda t: f"{t[0]}-thr{t[1]}-lay{t[2]}")
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_backward_matches_oracle(dev, orc, name, tier, store_T):
+    st_ = oracle_stage(orc, name, (0.3, 0.7, 0.1))
+    cam = st_["cam"]
+    W, H = cam.width, cam.height
+    f = gpu_forward(dev, st_)
+    n = len(st_["rec"])
+    grad = torch.zeros((n, 12), device=dev)
+    opts = gsr.backward_opts(tier[0], tier[1], tier[2], store_T)
+    gsr.gsr_backward(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], st_["bg"],
+                     f["final_T"] if store_T else None, f["n_contrib"] if store_T else None,
+                     T(st_["g"]), grad, opts)
+    got = N(grad)
+    out = st_["out"]
+    worst = check_scaled(f"{name} {tier} grad2d", got[:, :9], out["grad2d"], out["gscale"], out["gallow"])
+    assert np.all(got[:, 9:] == 0.0)
+    # the literal tolerance (no widening, no allowance) holds for almost all
+    lit = np.abs(got[:, :9] - out["grad2d"]) <= 1e-5 * out["glit"] + 1e-7
+    assert lit.mean() > 0.995, lit.mean()
+    print(f"{name} {tier} store_T={store_T}: worst/bound {worst:.3f}, literal-pass {lit.mean():.5f}")
+
+
+def test_backward_accumulates_into_existing_values(dev, orc):
+    st_ = oracle_stage(orc, "tiny", (0.3, 0.7, 0.1))
+    cam = st_["cam"]
+    f = gpu_forward(dev, st_)
+    n = len(st_["rec"])
+    base = torch.randn((n, 12), device=dev)
+    grad = base.clone()
+    gsr.gsr_backward(cam.width, cam.height, 16, 16, f["ranges"], f["pl"], f["splat"], st_["bg"],
+                     f["final_T"], f["n_contrib"], T(st_["g"]), grad, gsr.backward_opts("block", 0))
+    out = st_["out"]
+    check_scaled("accumulate", N(grad)[:, :9] - N(base)[:, :9], out["grad2d"], out["gscale"] + 10 * np.abs(N(base)[:, :9]),
+                 out["gallow"])
+    np.testing.assert_array_equal(N(grad)[:, 9:], N(base)[:, 9:])
+
+
+# ----------------------------------------------------------------------------
+# a8: backward projection
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_backward_project_matches_oracle(dev, orc, name):
+    st_ = oracle_stage(orc, name, (0.3, 0.7, 0.1))
+    scene, cam, pp = st_["scene"], st_["cam"], st_["pp"]
+    n = scene.n
+    g9 = st_["out"]["grad2d"].astype(np.float32)
+    g12 = np.zeros((n, 12), np.float32)
+    g12[:, :9] = g9
+    ref = orc.backproject(scene, cam, g9.astype(np.float64))
+    k = scene.feat.reshape(n, -1).shape[1]
+    dm, ds, dq = (torch.zeros((n, c), device=dev) for c in (3, 3, 4))
+    do = torch.zeros(n, device=dev)
+    df = torch.zeros((n, k), device=dev)
+    gsr.gsr_backward_project(n, scene.sh_degree, T(scene.mean), T(scene.scale), T(scene.quat),
+                             T(scene.opacity), T(scene.feat.reshape(n, -1)), cam, T(st_["radius"]), T(g12),
+                             dm, ds, dq, do, df)
+    ok = (pp["bp_ambig"] == 0) & (pp["pp_ambig"] == 0)
+    vis = (st_["radius"] > 0) & ok
+    for key, got, mag in (("dmean", dm, "dmean_mag"), ("dscale", ds, "dscale_mag"), ("dquat", dq, "dquat_mag"),
+                          ("dfeat", df, "dfeat_mag")):
+        r = ref[key].reshape(n, -1)
+        m = ref[mag].reshape(n, -1)
+        check_scaled(f"{name} {key}", N(got)[vis], r[vis], m[vis])
+    np.testing.assert_allclose(N(do)[vis], g9[vis, 5], rtol=0, atol=0)
+    assert np.all(N(dm)[st_["radius"] == 0] == 0)
+
+
+# ----------------------------------------------------------------------------
+# edge cases
+# ----------------------------------------------------------------------------
+
+def _run_all(dev, scene, cam, bg=(0.2, 0.4, 0.6)):
+    from paper_2401_05345_gb300 import pipeline
+    sc = pipeline.SceneTensors.from_scene(scene, dev)
+    vb = pipeline.ViewBuffers(scene.n, cam, dev, key_capacity=16)
+    vb.preprocess(sc)
+    vb.bin()
+    vb.forward(bg)
+    g = T(S.upstream_grad(1, cam.width, cam.height))
+    vb.backward(bg, g, gsr.backward_opts("hybrid", 8))
+    grads = sc.zeros_like_params()
+    vb.backward_project(sc, grads)
+    torch.cuda.synchronize()
+    return vb, grads
+
+
+def test_empty_scene_renders_background(dev):
+    cam = S.front_camera(40, 24)
+    scene = S.uniform_scene(0, 1).subset(slice(0, 0))
+    vb, grads = _run_all(dev, scene, cam)
+    assert vb.n_keys == 0
+    img = N(vb.image)
+    np.testing.assert_array_equal(img, np.broadcast_to(np.float32([0.2, 0.4, 0.6])[:, None, None], img.shape))
+    assert np.all(N(vb.final_T) == 1.0) and np.all(N(vb.n_contrib) == 0)
+
+
+def test_everything_behind_the_camera(dev):
+    cam = S.front_camera(48, 48)
+    scene = S.uniform_scene(1, 200)
+    scene.mean[:, 2] = -6.0  # z_cam = -2
+    vb, grads = _run_all(dev, scene, cam)
+    assert vb.n_keys == 0 and np.all(N(vb.radius) == 0)
+    assert np.all(N(vb.grad2d)[:, :9] == 0) and np.all(N(grads.mean) == 0)
+
+
+def test_splat_covering_every_tile(dev, orc):
+    cam = S.front_camera(100, 70)
+    scene = S.uniform_scene(2, 3)
+    scene.mean[:] = [[0.0, 0.0, 0.0], [0.05, 0.02, -0.5], [0.3, -0.2, 1.0]]
+    scene.scale[:] = [[1.5, 1.2, 1.0], [0.05, 0.05, 0.05], [0.4, 0.9, 0.2]]
+    vb, _ = _run_all(dev, scene, cam)
+    pp = orc.preprocess(scene, cam)
+    assert vb.n_keys >= vb.gx * vb.gy
+    assert pp["radius"][0] > 50
+
+
+def test_capacity_growth_in_pipeline(dev):
+    scene, cam = S.tiny_workload(3)
+    vb, _ = _run_all(dev, scene, cam)
+    assert vb.key_capacity >= vb.n_keys > 16
+
+
+def test_invalid_arguments_raise(dev):
+    cam = S.front_camera(32, 32)
+    x = torch.zeros(16, device=dev)
+    with pytest.raises(gsr.GsrError, match="invalid"):
+        gsr.gsr_forward(32, 32, 16, 8, x, x, x, (0, 0, 0), x)
+    with pytest.raises(gsr.GsrError, match="invalid"):
+        gsr.gsr_preprocess(4, 5, x, x, x, x, x, cam, 16, 16, x, x)
