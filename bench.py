@@ -1,0 +1,481 @@
+#!/usr/bin/env python
+"""Benchmark of the splat-rasterizer hot path on GB300.
+
+A step is one pass of the whole path over one view of the workload:
+projection (grad2d zeroed in the same pass), tile binning and sort, forward
+blend, L1 loss gradient, backward blend with per-splat gradient accumulation
+(the autotuned reduction tier), and backward projection to the 3D parameters.
+The unit is the splat-grad update: one of the 9 gradient values of one active
+(pixel, splat) pair, i.e. 9 x P_active per step for every tier.
+
+``--impl ours`` (default) prints one JSON line with the whole-step throughput,
+the backward kernel alone for the plain-atomicAdd tier and the reduced tiers,
+the roofline of the backward kernel, the CPU oracle on a bounded sample, an
+end-to-end number through host buffers, and the SM clocks seen meanwhile.
+``--impl reference`` times the FP64 CPU oracle on the same workload.
+Multi-GPU (torchrun): independent replicas, one view per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "backward-raster ms/iter and splat-grad updates/s: reduced vs plain atomicAdd"
+UNIT = "splat-grad updates/s"
+N_SM = 152
+FP32_LANES_PER_SM = 128
+# Algorithmic FP32 lane operations of the backward (an FMA counts as one):
+#   per examined (pixel, splat) pair: offset (2), quadratic form (7), exp (2),
+#     opacity product, cap and floor tests (4), position test (2) -> 17;
+#   per active pair: transmittance recovery (3), colour dot (3), dL/dalpha (3),
+#     suffix update (2), colour grads (3), opacity and sigma grads (3), conic
+#     grads (8), position grads (6), accumulation of 9 values (9) -> 40.
+OPS_PER_EXAMINED = 17
+OPS_PER_ACTIVE = 40
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.lines = []
+        self.device_index = device_index
+
+    def start(self):
+        import torch
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            p = torch.cuda.get_device_properties(self.device_index)
+            bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+            cmd += ["-i", bus]
+        except Exception:
+            pass
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def make_workload(name, seed):
+    from paper_2401_05345_gb300 import scenes as S
+    if name == "single_view":
+        scene, cam = S.single_view_workload(seed)
+        desc = ("single view: 500k Gaussians from a 64-component anisotropic mixture (std 0.05-0.5), "
+                "log-scales N(-4.5,0.7), SH degree 3, 1297x840, 16x16 tiles, L1 loss vs a U[0,1] target")
+    elif name == "tiny":
+        scene, cam = S.tiny_workload(seed)
+        desc = "tiny: 1,000 Gaussians in [-1,1]^3, RGB, 128x128"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    target = S.target_image(seed, cam.width, cam.height)
+    return scene, cam, target, desc
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle on a bounded sample (band of tile rows)
+# ----------------------------------------------------------------------------
+class OracleSample:
+    """The FP64 oracle pipeline on a bounded sample of the workload.  The
+    whole-scene stages (projection, binning, backward projection) run once and
+    are timed; each sample then rasterizes (forward, L1 gradient, backward) a
+    band of ``rows`` tile rows and is charged the band's share of the
+    whole-scene stages."""
+
+    def __init__(self, scene, cam, target, rows):
+        from oracle import oracle as O
+        O.build()
+        self.O, self.scene, self.cam, self.target = O, scene, cam, target
+        W, H = cam.width, cam.height
+        self.gx, self.gy = (W + 15) // 16, (H + 15) // 16
+        self.rows = max(1, min(rows, self.gy))
+        t0 = time.perf_counter()
+        self.pp = O.preprocess(scene, cam)
+        self.keys, self.pl, self.ranges = O.bin_sort(self.pp["uv"], self.pp["depth"], self.pp["radius"], W, H)
+        t1 = time.perf_counter()
+        O.backproject(scene, cam, np.zeros((scene.n, 9)), mags=False)
+        t2 = time.perf_counter()
+        self.t_global = t2 - t0
+
+    def run(self, band_index=0):
+        O, pp, cam = self.O, self.pp, self.cam
+        W, H = cam.width, cam.height
+        r0 = (self.gy // 2 - self.rows // 2 + band_index) % max(1, self.gy - self.rows + 1)
+        mask = np.zeros((self.gy, self.gx), np.uint8)
+        mask[r0:r0 + self.rows] = 1
+        frac = self.rows / self.gy
+        bg = np.zeros(3)
+        t0 = time.perf_counter()
+        fwd = O.render(W, H, self.ranges, self.pl, pp["uv"], pp["conic"], pp["opacity"], pp["rgb"], bg, None,
+                       extras=False, tile_mask=mask.reshape(-1))
+        band = np.zeros((H, W), bool)
+        band[r0 * 16:min(H, (r0 + self.rows) * 16)] = True
+        dimg = np.where(band[None], np.sign(fwd["image"] - self.target), 0.0).astype(np.float32)
+        out = O.render(W, H, self.ranges, self.pl, pp["uv"], pp["conic"], pp["opacity"], pp["rgb"], bg, dimg,
+                       extras=False, tile_mask=mask.reshape(-1))
+        t1 = time.perf_counter()
+        updates = 9 * int(out["n_active"][band].sum())
+        seconds = (t1 - t0) + frac * self.t_global
+        desc = (f"FP64 oracle, 1 thread: forward + L1 gradient + backward on {self.rows} of {self.gy} tile rows "
+                f"per sample; projection + binning + backward projection of the whole scene "
+                f"({self.t_global:.2f} s, timed once) charged at {frac:.4f} per sample")
+        return updates, seconds, desc
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    scene, cam, target, desc = make_workload(args.workload, args.seed)
+    vals, times = [], []
+    note = ""
+    smp = OracleSample(scene, cam, target, args.cpu_rows)
+    for i in range(args.warmup + args.steps):
+        upd, sec, note = smp.run(i)
+        if i >= args.warmup:
+            vals.append(upd)
+            times.append(sec)
+    value = sum(vals) / sum(times)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "sample": f"{args.cpu_rows} tile rows per step"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": note},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# the CUDA path
+# ----------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("raster.cu", "gsr_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2401_05345_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel_hash, opts_name, n_pairs):
+    """DRAM bytes per launch of the backward from the committed ncu summary,
+    if it was taken on this exact kernel source and tier; else None."""
+    p = os.path.join(ROOT, "profiles", "backward_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(opts_name)
+    if not e or e.get("kernel_hash") != kernel_hash:
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2401_05345_gb300 import autotune, gsr, pipeline
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    gsr.lib()
+    peaks = load_peaks()
+
+    scene, cam, target_np, desc = make_workload(args.workload, args.seed + rank)
+    bg = (0.0, 0.0, 0.0)
+    sc = pipeline.SceneTensors.from_scene(scene, dev)
+    grads = sc.zeros_like_params()
+    target = torch.from_numpy(target_np).to(dev)
+    R = pipeline.Renderer(scene.n, cam, dev)
+    vb = R.vb
+    flush = autotune.L2Flusher(dev)
+    stream = torch.cuda.current_stream()
+
+    # first pass (untimed): sizes, statistics of the traversal
+    R.step(sc, target, bg, grads)
+    torch.cuda.synchronize()
+    hist = torch.zeros(36, dtype=torch.int64, device=dev)
+    gsr.gsr_backward_stats(vb.W, vb.H, 16, 16, vb.tile_ranges, vb.point_list, vb.splat2d, vb.n_contrib, hist)
+    h = hist.cpu().numpy().astype(np.int64)
+    p_active, p_exam, warp_steps = int(h[33]), int(h[34]), int(h[35])
+    units = 9 * p_active
+
+    # plain atomicAdd vs reduced tiers, backward kernel alone (untimed for the step)
+    if args.profile:
+        best = gsr.backward_opts("hybrid", 8, 1)
+        tune_table, t_plain = {}, None
+    else:
+        tr = autotune.tune(vb, bg, R.dimg, reps=3, flush=flush)
+        best = tr.best
+        tune_table = tr.table
+    R.opts = best
+    best_name = autotune.opts_name(best)
+
+    def step_once(on_backward=None):
+        grads.mean.zero_(); grads.scale.zero_(); grads.quat.zero_(); grads.opacity.zero_(); grads.feat.zero_()
+        R.step(sc, target, bg, grads, on_backward=on_backward)
+
+    for _ in range(args.warmup):
+        step_once()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed (untimed) before each
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    if not args.profile:
+        clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush()
+        e0, e1, b0, b1 = ev[k]
+        e0.record(stream)
+        step_once(lambda begin, b0=b0, b1=b1: (b0 if begin else b1).record(stream))
+        e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if not args.profile else None
+    step_ms = [e0.elapsed_time(e1) for (e0, e1, _, _) in ev]
+    bwd_ms = [b0.elapsed_time(b1) for (_, _, b0, b1) in ev]
+    tot_ms = sum(step_ms)
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": tot_ms / args.steps,
+                              "backward_ms": statistics.mean(bwd_ms), "opts": best_name}), flush=True)
+        return 0
+
+    # backward kernel alone: plain atomicAdd vs the reduced tiers
+    reps = 10
+    t_plain = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("plain", 0, best.lane_layout), reps, flush)
+    t_warp = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("warp", 0, best.lane_layout), reps, flush)
+    t_best = autotune.time_backward(vb, bg, R.dimg, best, reps, flush)
+    t_block = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("block", 0, best.lane_layout), reps, flush)
+    t_recompute = autotune.time_backward(
+        vb, bg, R.dimg, gsr.backward_opts(int(best.reduce_mode), int(best.threshold), int(best.lane_layout), False),
+        reps, flush)
+    sweep = {}
+    for thr in (4, 8, 12, 16, 20, 24, 28, 32):
+        sweep[str(thr)] = autotune.time_backward(
+            vb, bg, R.dimg, gsr.backward_opts("hybrid", thr, best.lane_layout), 5, flush)
+
+    # L2 atomic (red) throughput: the plain tier's roofline
+    red_buf = torch.zeros(12 * 1_000_000, dtype=torch.float32, device=dev)
+    red = {}
+    for pat, name in ((0, "distinct"), (1, "one_address_per_warp"), (2, "nine_lanes_one_record"),
+                      (3, "nine_per_lane_one_record")):
+        blocks, iters = N_SM * 8, 64
+        gsr.gsr_bench_red(pat, blocks, 4, red_buf)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        adds = gsr.gsr_bench_red(pat, blocks, iters, red_buf)
+        a1.record(stream)
+        a1.synchronize()
+        red[name] = adds / (a0.elapsed_time(a1) / 1e3)
+
+    # end to end through host buffers: H2D of the step's inputs, D2H of the loss
+    host_in = [t.detach().cpu().pin_memory() for t in sc.tensors()] + [target.cpu().pin_memory()]
+    dev_in = sc.tensors() + [target]
+    loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        for d, hsrc in zip(dev_in, host_in):
+            d.copy_(hsrc, non_blocking=True)
+        step_once()
+        loss_host.copy_(R.loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+
+    # aggregate over ranks
+    import torch.distributed as dist
+    units_all = units * args.steps
+    e2e_tot = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms, e2e_tot], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([units_all], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        tot_ms, e2e_tot = float(t[0]), float(t[1])
+        units_all = float(u[0])
+    value = units_all / (tot_ms / 1e3)
+    e2e_value = units_all / (e2e_tot / 1e3)
+
+    # roofline of the dominant kernel (the reduced backward): FP32 ALU issue
+    bwd_avg_s = statistics.mean(bwd_ms) / 1e3
+    ops = OPS_PER_EXAMINED * p_exam + OPS_PER_ACTIVE * p_active
+    peak_ops = N_SM * FP32_LANES_PER_SM * peaks["sm_max_mhz"] * 1e6
+    achieved = ops / bwd_avg_s
+    traffic = traffic_from_profile(kernel_source_hash(), best_name, p_active)
+    plain_atomics = 9 * p_active
+    # algorithmic bytes of one backward: 4 B id + 36 B attributes per list
+    # entry, 12 B dL/dimage + 4 B final_T + 4 B n_contrib per pixel, one read
+    # and one write of the 36 B gradient record per visible splat
+    n_vis = int((vb.radius[:scene.n] > 0).sum().item())
+    alg_bytes = 40.0 * vb.n_keys + 20.0 * vb.W * vb.H + 72.0 * n_vis
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            smp = OracleSample(scene, cam, target_np, args.cpu_rows)
+            upd, sec = 0, 0.0
+            for i in range(args.cpu_samples):
+                u, t_, note = smp.run(i)
+                upd, sec = upd + u, sec + t_
+            cpu = {"value": upd / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": note}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generator standing in for the paper's captured scenes)",
+            "config": {"workload": desc, "parallelism": f"replicas x{world}",
+                       "l2": "flushed before every timed step (256 MiB write, outside the step events)",
+                       "backward_opts": best_name, "bg": list(bg)},
+            "roofline": {"bound": "alu", "kernel": f"backward_kernel ({best_name})",
+                         "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "T fp32-ops/s",
+                         "frac": achieved / peak_ops, "traffic": traffic,
+                         "peak_source": f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                        f"{peaks['sm_max_mhz']:.0f} MHz ({peaks['source']} max SM clock)",
+                         "ops_per_launch": ops, "launch_ms": bwd_avg_s * 1e3},
+            "backward_raster": {
+                "ms_plain_atomicAdd": t_plain, "ms_warp": t_warp, "ms_block": t_block,
+                "ms_best": t_best, "best": best_name, "ms_best_recompute_T": t_recompute,
+                "speedup_best_vs_plain": t_plain / t_best,
+                "updates_per_s_plain": units / (t_plain / 1e3),
+                "updates_per_s_best": units / (t_best / 1e3),
+                "hybrid_threshold_sweep_ms": sweep, "autotune_ms": tune_table,
+                "plain_l2_atomic_roofline": {
+                    "achieved_adds_per_s": plain_atomics / (t_plain / 1e3),
+                    "peak_adds_per_s": red["nine_per_lane_one_record"],
+                    "frac": (plain_atomics / (t_plain / 1e3)) / red["nine_per_lane_one_record"],
+                    "peak_source": "gsr_bench_red pattern 3 (9 adds per lane into one record per warp), same GPU"},
+                "algorithmic_bytes_best": alg_bytes,
+                "hbm_gbs_best": alg_bytes / (t_best * 1e-3) / 1e9,
+            },
+            "l2_red_adds_per_s": red,
+            "traffic_counts": {"P_active": p_active, "P_examined": p_exam, "P_ts": vb.n_keys,
+                               "warp_steps": warp_steps, "active_lane_hist": h[:33].tolist()},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4,
+                    "ms_per_step": e2e_tot / args.steps},
+            "clocks": clk,
+            "gpu_launches": args.steps * LAUNCHES_PER_STEP,
+            "wall_s_timed_region": wall,
+            "peaks": peaks,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+# Kernels of libgsr launched per step: preprocess, tile count, exclusive scan
+# (2 CUB kernels), duplicate, radix sort (CUB: 1 histogram + 6 onesweep passes
+# for a 45-bit key), ranges, forward, L1 loss, backward, backward projection.
+LAUNCHES_PER_STEP = 17
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="single_view")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-rows", type=int, default=2, help="tile rows of the oracle sample")
+    ap.add_argument("--cpu-samples", type=int, default=4, help="oracle samples for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu)")
+    args = ap.parse_args()
+    if args.warmup < 3 and not args.profile:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

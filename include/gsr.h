@@ -189,6 +189,22 @@ int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                  const gsr_backward_opts* opts, gsr_stream_t stream);
 
 /*
+ * Traversal statistics of gsr_backward (nothing else is written): walks the
+ * same lists as the backward with the same skip tests and fills the HOST-
+ * visible-after-copy device array hist[36] (uint64, zeroed first):
+ *   hist[k], k = 0..32: number of (warp, splat) steps with k active lanes --
+ *     the active-threads-per-warp histogram of Sec. III-B, Observation 2;
+ *   hist[33]: active (pixel, splat) pairs (each adds 9 gradient values);
+ *   hist[34]: examined pairs (sum of n_contrib);
+ *   hist[35]: warp steps taken.
+ * lane_layout as in gsr_backward_opts.  n_contrib from gsr_forward.
+ */
+int gsr_backward_stats(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                       const uint32_t* tile_ranges, const uint32_t* point_list,
+                       const float* splat2d, const int32_t* n_contrib, int32_t lane_layout,
+                       uint64_t* hist, gsr_stream_t stream);
+
+/*
  * Backward projection: chain rule from grad2d to the 3D parameters through
  * the conic inverse, the EWA Jacobian (exact derivative, zero through an
  * active frustum clamp), the covariance R S S^T R^T, the quaternion

@@ -570,7 +570,8 @@ static void pixel_grads(const scene2d_t* S, const contrib_t* cs, int nc, double 
  * nc_alt [H*W]: n_contrib under the flipped decision (-1 if none);
  * pix_ambig [H*W]: count of such decisions in the pixel;
  * pix_widen [H*W]: the pixel's widening factor max(1, 8 b / 1e-5);
- * terr [H*W]: first-order FP32 relative error bound of final_T.
+ * terr [H*W]: first-order FP32 relative error bound of final_T;
+ * n_active [H*W]: number of contributing splats of the pixel.
  * tile_mask [tiles] (may be NULL = all): only tiles with a non-zero entry are
  * evaluated (sampled comparisons); other pixels' outputs are left untouched.
  * Any output pointer may be NULL.  Returns 0, or -1 on allocation failure.
@@ -580,7 +581,7 @@ int orc_render(int W, int H, int tw, int th, const uint32_t* ranges, const uint3
                const double* bg, const float* dL_dimage, const uint8_t* tile_mask, double* image,
                double* final_T, int* n_contrib, double* grad2d, double* gscale, double* glit,
                double* gallow, double* iallow, double* tallow, int* nc_alt, int* pix_ambig,
-               double* pix_widen, double* terr) {
+               double* pix_widen, double* terr, int* n_active) {
     scene2d_t S = {W, H, uv, conic, opacity, rgb, bg};
     long long gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
     int maxlen = 1;
@@ -622,6 +623,7 @@ int orc_render(int W, int H, int tw, int th, const uint32_t* ranges, const uint3
                     if (final_T) final_T[pix] = Tf;
                     if (n_contrib) n_contrib[pix] = last;
                     if (pix_ambig) pix_ambig[pix] = namb;
+                    if (n_active) n_active[pix] = nc;
                     if (nc_alt) nc_alt[pix] = -1;
                     if (iallow) for (int ch = 0; ch < 3; ++ch) iallow[ch * HW + pix] = 0;
                     if (tallow) tallow[pix] = 0;

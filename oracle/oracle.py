@@ -54,7 +54,7 @@ def _load():
     lib.orc_bin.restype = c_int
     lib.orc_render.argtypes = [c_int, c_int, c_int, c_int, U32, U32, c_int, D, D, D, D, D,
                                POINTER(c_float), POINTER(ctypes.c_uint8), D, D, I, D, D, D, D, D, D,
-                               I, I, D, D]
+                               I, I, D, D, I]
     lib.orc_render.restype = c_int
     lib.orc_backproject.argtypes = [c_int, c_int, D, D, D, D, D, POINTER(OrcCamera), c_int, c_int,
                                     D, D, D, D, D, D, D, D, D, D]
@@ -143,7 +143,7 @@ def render(W, H, ranges, point_list, uv, conic, opacity, rgb, bg, dL_dimage=None
         pl = np.zeros(1, np.uint32)
     hw = W * H
     out = dict(image=np.zeros((3, H, W)), final_T=np.zeros((H, W)),
-               n_contrib=np.zeros((H, W), np.int32))
+               n_contrib=np.zeros((H, W), np.int32), n_active=np.zeros((H, W), np.int32))
     g = None
     if dL_dimage is not None:
         g = np.ascontiguousarray(dL_dimage, np.float32)
@@ -169,7 +169,8 @@ def render(W, H, ranges, point_list, uv, conic, opacity, rgb, bg, dL_dimage=None
                         _p(tm, ctypes.c_uint8) if tm is not None else None,
                         gp("image"), gp("final_T"), gp("n_contrib", c_int), gp("grad2d"),
                         gp("gscale"), gp("glit"), gp("gallow"), gp("iallow"), gp("tallow"),
-                        gp("nc_alt", c_int), gp("pix_ambig", c_int), gp("pix_widen"), gp("terr"))
+                        gp("nc_alt", c_int), gp("pix_ambig", c_int), gp("pix_widen"), gp("terr"),
+                        gp("n_active", c_int))
     if rc != 0:
         raise MemoryError("oracle render")
     return out

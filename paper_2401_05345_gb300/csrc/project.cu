@@ -87,6 +87,40 @@ __device__ __forceinline__ void sh_basis_vjp(int deg, float x, float y, float z,
     gx += -C3a * (3.f * xx - 3.f * yy) * c[15]; gy += C3a * 6.f * x * y * c[15];
 }
 
+// Loads / accumulates the 3K feature floats of one Gaussian (16-byte vectors
+// when 3K is a multiple of 4, so a thread's record is read with few wide
+// loads).
+template <int NF>
+__device__ __forceinline__ void load_feat(const float* __restrict__ src, float* dst) {
+    if constexpr (NF % 4 == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+        for (int j = 0; j < NF / 4; ++j) {
+            float4 x = s4[j];
+            dst[4 * j] = x.x; dst[4 * j + 1] = x.y; dst[4 * j + 2] = x.z; dst[4 * j + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NF; ++j) dst[j] = src[j];
+    }
+}
+
+template <int NF>
+__device__ __forceinline__ void add_feat(float* __restrict__ dst, const float* v) {
+    if constexpr (NF % 4 == 0) {
+        float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+        for (int j = 0; j < NF / 4; ++j) {
+            float4 x = d4[j];
+            x.x += v[4 * j]; x.y += v[4 * j + 1]; x.z += v[4 * j + 2]; x.w += v[4 * j + 3];
+            d4[j] = x;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NF; ++j) dst[j] += v[j];
+    }
+}
+
 // Forward quantities of one Gaussian, kept for the backward projection.
 struct Proj {
     float p[3];          // camera-space mean
@@ -154,11 +188,13 @@ __device__ __forceinline__ bool project(const Cam& k, const float* mean, const f
     return true;
 }
 
+template <int DEG>
 __global__ void __launch_bounds__(256)
-preprocess_kernel(int n, int sh_deg, const float* __restrict__ mean, const float* __restrict__ scale,
+preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict__ scale,
                   const float* __restrict__ quat, const float* __restrict__ opacity,
                   const float* __restrict__ feat, Cam k, int gx, int gy, int tw_log2, int th_log2,
                   float* __restrict__ splat2d, int* __restrict__ radius, float* __restrict__ gzero) {
+    constexpr int K = DEG < 0 ? 1 : (DEG + 1) * (DEG + 1);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float4* rec = reinterpret_cast<float4*>(splat2d + (size_t)i * GSR_REC);
@@ -186,17 +222,18 @@ preprocess_kernel(int n, int sh_deg, const float* __restrict__ mean, const float
     }
     float idet = 1.0f / P.det;
     float rgb[3];
-    if (sh_deg < 0) {
+    if constexpr (DEG < 0) {
         for (int ch = 0; ch < 3; ++ch) rgb[ch] = feat[3 * (size_t)i + ch];
     } else {
         const float* m = mean + 3 * (size_t)i;
         float dx = m[0] - k.campos[0], dy = m[1] - k.campos[1], dz = m[2] - k.campos[2];
         float il = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
         float Y[16];
-        sh_basis(sh_deg, dx * il, dy * il, dz * il, Y);
-        int K = (sh_deg + 1) * (sh_deg + 1);
-        const float* f = feat + (size_t)i * K * 3;
+        sh_basis(DEG, dx * il, dy * il, dz * il, Y);
+        float f[3 * K];
+        load_feat<3 * K>(feat + (size_t)i * K * 3, f);
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
         for (int j = 0; j < K; ++j) {
             s0 = fmaf(Y[j], f[3 * j], s0);
             s1 = fmaf(Y[j], f[3 * j + 1], s1);
@@ -212,12 +249,14 @@ preprocess_kernel(int n, int sh_deg, const float* __restrict__ mean, const float
     rec[2] = make_float4(rgb[2], P.p[2], 0.f, 0.f);
 }
 
+template <int DEG>
 __global__ void __launch_bounds__(128)
-backproject_kernel(int n, int sh_deg, const float* __restrict__ mean, const float* __restrict__ scale,
+backproject_kernel(int n, const float* __restrict__ mean, const float* __restrict__ scale,
                    const float* __restrict__ quat, const float* __restrict__ feat, Cam k,
                    const int* __restrict__ radius, const float* __restrict__ grad2d,
                    float* __restrict__ dmean, float* __restrict__ dscale, float* __restrict__ dquat,
                    float* __restrict__ dopacity, float* __restrict__ dfeat) {
+    constexpr int K = DEG < 0 ? 1 : (DEG + 1) * (DEG + 1);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || radius[i] <= 0) return;
     Proj P;
@@ -231,7 +270,7 @@ backproject_kernel(int n, int sh_deg, const float* __restrict__ mean, const floa
     float dm[3] = {0.f, 0.f, 0.f};
 
     // colour: SH basis along the viewing direction, clamp at 0
-    if (sh_deg < 0) {
+    if constexpr (DEG < 0) {
         for (int ch = 0; ch < 3; ++ch) dfeat[3 * (size_t)i + ch] += gcol[ch];
     } else {
         float dx = m[0] - k.campos[0], dy = m[1] - k.campos[1], dz = m[2] - k.campos[2];
@@ -239,21 +278,27 @@ backproject_kernel(int n, int sh_deg, const float* __restrict__ mean, const floa
         float il = 1.0f / len;
         float x = dx * il, y = dy * il, z = dz * il;
         float Y[16];
-        sh_basis(sh_deg, x, y, z, Y);
-        int K = (sh_deg + 1) * (sh_deg + 1);
-        const float* f = feat + (size_t)i * K * 3;
+        sh_basis(DEG, x, y, z, Y);
+        float f[3 * K];
+        load_feat<3 * K>(feat + (size_t)i * K * 3, f);
         float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
         for (int j = 0; j < K; ++j)
+#pragma unroll
             for (int ch = 0; ch < 3; ++ch) raw[ch] = fmaf(Y[j], f[3 * j + ch], raw[ch]);
+#pragma unroll
         for (int ch = 0; ch < 3; ++ch) if (raw[ch] < 0.f) gcol[ch] = 0.f;
-        float* df = dfeat + (size_t)i * K * 3;
+        float df[3 * K];
         float cw[16];
+#pragma unroll
         for (int j = 0; j < K; ++j) {
-            for (int ch = 0; ch < 3; ++ch) df[3 * j + ch] += Y[j] * gcol[ch];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) df[3 * j + ch] = Y[j] * gcol[ch];
             cw[j] = f[3 * j] * gcol[0] + f[3 * j + 1] * gcol[1] + f[3 * j + 2] * gcol[2];
         }
+        add_feat<3 * K>(dfeat + (size_t)i * K * 3, df);
         float ddx, ddy, ddz;
-        sh_basis_vjp(sh_deg, x, y, z, cw, ddx, ddy, ddz);
+        sh_basis_vjp(DEG, x, y, z, cw, ddx, ddy, ddz);
         float dot = x * ddx + y * ddy + z * ddz;
         dm[0] += (ddx - x * dot) * il;
         dm[1] += (ddy - y * dot) * il;
@@ -350,9 +395,19 @@ extern "C" int gsr_preprocess(int32_t n, int32_t sh_degree, const float* mean, c
     if (cam->width <= 0 || cam->height <= 0) return GSR_EINVAL;
     Cam k = make_cam(*cam);
     int gx = (cam->width + tile_w - 1) / tile_w, gy = (cam->height + tile_h - 1) / tile_h;
-    preprocess_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
-        n, sh_degree, mean, scale, quat, opacity, feat, k, gx, gy, ilog2(tile_w), ilog2(tile_h),
-        splat2d, radius, grad2d_to_zero);
+    const int blocks = (n + 255) / 256;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int twl = ilog2(tile_w), thl = ilog2(tile_h);
+#define GSR_PRE(D) preprocess_kernel<D><<<blocks, 256, 0, st>>>(n, mean, scale, quat, opacity, feat, k, gx, gy, \
+                                                             twl, thl, splat2d, radius, grad2d_to_zero)
+    switch (sh_degree) {
+        case -1: GSR_PRE(-1); break;
+        case 0: GSR_PRE(0); break;
+        case 1: GSR_PRE(1); break;
+        case 2: GSR_PRE(2); break;
+        default: GSR_PRE(3); break;
+    }
+#undef GSR_PRE
     return check_launch();
 }
 
@@ -368,7 +423,17 @@ extern "C" int gsr_backward_project(int32_t n, int32_t sh_degree, const float* m
         !dopacity || !dfeat)
         return GSR_EINVAL;
     Cam k = make_cam(*cam);
-    backproject_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
-        n, sh_degree, mean, scale, quat, feat, k, radius, grad2d, dmean, dscale, dquat, dopacity, dfeat);
+    const int blocks = (n + 127) / 128;
+    cudaStream_t st = (cudaStream_t)stream;
+#define GSR_BP(D) backproject_kernel<D><<<blocks, 128, 0, st>>>(n, mean, scale, quat, feat, k, radius, grad2d, \
+                                                                dmean, dscale, dquat, dopacity, dfeat)
+    switch (sh_degree) {
+        case -1: GSR_BP(-1); break;
+        case 0: GSR_BP(0); break;
+        case 1: GSR_BP(1); break;
+        case 2: GSR_BP(2); break;
+        default: GSR_BP(3); break;
+    }
+#undef GSR_BP
     return check_launch();
 }

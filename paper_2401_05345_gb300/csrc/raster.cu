@@ -16,16 +16,71 @@ struct RasterGeom {
     int W, H, gx, gy;
 };
 
+// Pixel of thread `tid` inside a TW x TH tile.
+//   LAYOUT 0: row-major, a warp covers 32 consecutive pixels (16 x 2);
+//   LAYOUT 1: each warp covers an 8 x 4 pixel block.
+template <int TW, int LAYOUT>
+__device__ __forceinline__ void lane_pixel(int tid, int& lx, int& ly) {
+    if (LAYOUT == 0) {
+        lx = tid % TW;
+        ly = tid / TW;
+    } else {
+        const int w = tid >> 5, l = tid & 31;
+        constexpr int WX = TW / 8;
+        lx = (w % WX) * 8 + (l & 7);
+        ly = (w / WX) * 4 + (l >> 3);
+    }
+}
+
+// Bitmask of the warps of a TW x TH tile with origin (ox, oy) whose pixel
+// block can hold a pixel where this splat reaches alpha >= 1/255.  Uses the
+// bounding box of the ellipse sigma <= ln(255 o) (half-widths
+// sqrt(2 L C / det), sqrt(2 L A / det) for the conic [[A,B],[B,C]]), with L
+// enlarged by 1% + 0.01 and the box by 2% + 0.05 px, so FP32 rounding of
+// sigma or alpha can never let a culled pair pass the alpha test: culling
+// removes only pairs both kernels skip anyway.
+template <int TW, int TH, int LAYOUT>
+__device__ __forceinline__ unsigned warp_cull_mask(float u, float v, float A, float B, float C, float o,
+                                                   int ox, int oy) {
+    constexpr int NW = TW * TH / 32;
+    constexpr unsigned ALL = NW >= 32 ? 0xffffffffu : ((1u << NW) - 1u);
+    if (!(o >= kAlphaMin)) return 0u;  // alpha = o G <= o < 1/255 at every pixel
+    const float det = A * C - B * B;
+    if (!(det > 0.0f) || !(A > 0.0f) || !(C > 0.0f)) return ALL;
+    const float L = __logf(o * 255.0f) * 1.01f + 0.01f;
+    const float ex = sqrtf(2.0f * L * C / det) * 1.02f + 0.05f;
+    const float ey = sqrtf(2.0f * L * A / det) * 1.02f + 0.05f;
+    unsigned m = 0u;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        int x0, y0, wx, wy;
+        if (LAYOUT == 0) {
+            constexpr int RPW = 32 / TW;
+            x0 = ox; y0 = oy + w * RPW; wx = TW; wy = RPW;
+        } else {
+            constexpr int WX = TW / 8;
+            x0 = ox + (w % WX) * 8; y0 = oy + (w / WX) * 4; wx = 8; wy = 4;
+        }
+        const bool hit = (u + ex >= (float)x0) && (u - ex <= (float)(x0 + wx - 1)) &&
+                         (v + ey >= (float)y0) && (v - ey <= (float)(y0 + wy - 1));
+        m |= hit ? (1u << w) : 0u;
+    }
+    return m;
+}
+
 // Front-to-back walk of one pixel over its tile list (shared by the forward
 // kernel and the recompute mode of the backward, so both produce the same
 // final transmittance and last contributor bit for bit).  All threads of the
 // CTA must call it.
-template <int B, bool COLOR>
+template <int TW, int TH, int LAYOUT, bool COLOR>
 __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict__ point_list,
                                            const float* __restrict__ splat2d, float px, float py,
-                                           bool inside, float4* s_a, float4* s_b, float* s_c,
-                                           float& T, int& last, float& C0, float& C1, float& C2) {
+                                           bool inside, int ox, int oy, float4* s_a, float4* s_b,
+                                           float* s_c, unsigned* s_mask, float& T, int& last, float& C0,
+                                           float& C1, float& C2) {
+    constexpr int B = TW * TH;
     const int n = (int)(rg.y - rg.x);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     bool done = !inside;
     T = 1.0f;
     last = 0;
@@ -36,29 +91,45 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
         if (idx < n) {
             uint32_t id = point_list[rg.x + idx];
             const float4* rec = reinterpret_cast<const float4*>(splat2d + (size_t)id * GSR_REC);
-            s_a[threadIdx.x] = rec[0];
-            s_b[threadIdx.x] = rec[1];
+            const float4 a = rec[0], b = rec[1];
+            s_a[threadIdx.x] = a;
+            s_b[threadIdx.x] = b;
             if (COLOR) s_c[threadIdx.x] = rec[2].x;
+            s_mask[threadIdx.x] = warp_cull_mask<TW, TH, LAYOUT>(a.x, a.y, a.z, a.w, b.x, b.y, ox, oy);
         }
         __syncthreads();
         const int cnt = min(B, n - base);
-        for (int k = 0; k < cnt && !done; ++k) {
-            float4 a = s_a[k], b = s_b[k];
-            SplatEval e;
-            if (!eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, px, py, e)) continue;
-            float testT = __fmul_rn(T, __fsub_rn(1.0f, e.alpha));
-            if (testT < kTMin) {
-                done = true;
-                break;
+        bool wdone = __all_sync(kFull, done);
+        for (int c0 = 0; c0 < cnt && !wdone; c0 += 32) {
+            const int kq = c0 + lane;
+            unsigned bits = __ballot_sync(kFull, kq < cnt && ((s_mask[kq] >> w) & 1u));
+            while (bits) {
+                const int k = c0 + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                if (!done) {
+                    const float4 a = s_a[k], b = s_b[k];
+                    SplatEval e;
+                    if (eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, px, py, e)) {
+                        const float testT = __fmul_rn(T, __fsub_rn(1.0f, e.alpha));
+                        if (testT < kTMin) {
+                            done = true;
+                        } else {
+                            if (COLOR) {
+                                const float wgt = __fmul_rn(e.alpha, T);
+                                C0 = __fmaf_rn(b.z, wgt, C0);
+                                C1 = __fmaf_rn(b.w, wgt, C1);
+                                C2 = __fmaf_rn(s_c[k], wgt, C2);
+                            }
+                            T = testT;
+                            last = base + k + 1;
+                        }
+                    }
+                }
+                if (__all_sync(kFull, done)) {
+                    wdone = true;
+                    break;
+                }
             }
-            if (COLOR) {
-                float w = __fmul_rn(e.alpha, T);
-                C0 = __fmaf_rn(b.z, w, C0);
-                C1 = __fmaf_rn(b.w, w, C1);
-                C2 = __fmaf_rn(s_c[k], w, C2);
-            }
-            T = testT;
-            last = base + k + 1;
         }
     }
 }
@@ -72,14 +143,17 @@ forward_kernel(RasterGeom g, const uint2* __restrict__ ranges, const uint32_t* _
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
     __shared__ float s_c[B];
+    __shared__ unsigned s_mask[B];
     const int tile = blockIdx.x;
     const int tx = tile % g.gx, ty = tile / g.gx;
-    const int px = tx * TW + (int)threadIdx.x % TW, py = ty * TH + (int)threadIdx.x / TW;
+    int lx, ly;
+    lane_pixel<TW, 1>((int)threadIdx.x, lx, ly);
+    const int px = tx * TW + lx, py = ty * TH + ly;
     const bool inside = px < g.W && py < g.H;
     float T, C0, C1, C2;
     int last;
-    walk_front<B, true>(ranges[tile], point_list, splat2d, (float)px, (float)py, inside, s_a, s_b, s_c,
-                        T, last, C0, C1, C2);
+    walk_front<TW, TH, 1, true>(ranges[tile], point_list, splat2d, (float)px, (float)py, inside, tx * TW,
+                                ty * TH, s_a, s_b, s_c, s_mask, T, last, C0, C1, C2);
     if (inside) {
         const size_t HW = (size_t)g.W * g.H, pix = (size_t)py * g.W + px;
         image[pix] = __fmaf_rn(T, bg0, C0);
@@ -103,20 +177,6 @@ struct BwdArgs {
     int threshold;
 };
 
-// Pixel of thread (warp w, lane l) inside a TW x TH tile.
-template <int TW, int LAYOUT>
-__device__ __forceinline__ void lane_pixel(int tid, int& lx, int& ly) {
-    if (LAYOUT == 0) {  // row-major: a warp covers 32 consecutive pixels
-        lx = tid % TW;
-        ly = tid / TW;
-    } else {            // 8 x 4 pixel blocks per warp
-        const int w = tid >> 5, l = tid & 31;
-        constexpr int WX = TW / 8;
-        lx = (w % WX) * 8 + (l & 7);
-        ly = (w / WX) * 4 + (l >> 3);
-    }
-}
-
 template <int TW, int TH, int MODE, int LAYOUT, bool STORE_T>
 __global__ void __launch_bounds__(TW* TH)
 backward_kernel(BwdArgs p) {
@@ -125,10 +185,11 @@ backward_kernel(BwdArgs p) {
     __shared__ float4 s_b[B];
     __shared__ float s_c[B];
     __shared__ uint32_t s_id[B];
+    __shared__ unsigned s_mask[B];
     __shared__ float s_acc[MODE == GSR_REDUCE_BLOCK ? B * 9 : 1];
     __shared__ int s_maxlast;
 
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
     const int tx = tile % p.g.gx, ty = tile / p.g.gx;
     int lx, ly;
@@ -147,7 +208,8 @@ backward_kernel(BwdArgs p) {
         last = inside ? min(max(p.n_contrib[pix], 0), nlist) : 0;  // never walk past the list
     } else {
         float c0, c1, c2;
-        walk_front<B, false>(rg, p.point_list, p.splat2d, fpx, fpy, inside, s_a, s_b, s_c, Tf, last, c0, c1, c2);
+        walk_front<TW, TH, LAYOUT, false>(rg, p.point_list, p.splat2d, fpx, fpy, inside, tx * TW, ty * TH,
+                                          s_a, s_b, s_c, s_mask, Tf, last, c0, c1, c2);
         if (!inside) { Tf = 0.0f; last = 0; }
     }
     float g0 = 0.f, g1 = 0.f, g2 = 0.f;
@@ -176,15 +238,24 @@ backward_kernel(BwdArgs p) {
         if (tid < cnt) {
             uint32_t id = p.point_list[rg.x + (uint32_t)(top - 1 - tid)];
             const float4* rec = reinterpret_cast<const float4*>(p.splat2d + (size_t)id * GSR_REC);
+            const float4 a = rec[0], b = rec[1];
             s_id[tid] = id;
-            s_a[tid] = rec[0];
-            s_b[tid] = rec[1];
+            s_a[tid] = a;
+            s_b[tid] = b;
             s_c[tid] = rec[2].x;
+            s_mask[tid] = warp_cull_mask<TW, TH, LAYOUT>(a.x, a.y, a.z, a.w, b.x, b.y, tx * TW, ty * TH);
         }
         __syncthreads();
-        for (int k = 0; k < cnt; ++k) {
+        // each warp visits, back to front, only the staged splats whose
+        // alpha >= 1/255 region touches its pixel block and that lie before
+        // the warp's last contributor
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+          const int kq = c0 + lane;
+          unsigned bits = __ballot_sync(kFull, kq < cnt && ((s_mask[kq] >> warp) & 1u) && (top - 1 - kq < wlast));
+          while (bits) {
+            const int k = c0 + __ffs(bits) - 1;
+            bits &= bits - 1u;
             const int pos = top - 1 - k;
-            if (pos >= wlast) continue;  // warp-uniform: no lane of this warp reaches pos
             const float4 a = s_a[k], b = s_b[k];
             SplatEval e;
             const bool active = (pos < last) && eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, fpx, fpy, e);
@@ -236,6 +307,7 @@ backward_kernel(BwdArgs p) {
                     }
                 }
             }
+          }
         }
         if (MODE == GSR_REDUCE_BLOCK) {
             __syncthreads();
@@ -249,6 +321,69 @@ backward_kernel(BwdArgs p) {
             }
         }
     }
+}
+
+// Counts of the backward traversal (no gradients written): per (warp, splat)
+// step the number of active lanes -> hist[0..32]; hist[33] = active pairs,
+// hist[34] = examined pairs (sum of n_contrib), hist[35] = warp steps with at
+// least one lane still walking.  The histogram is the active-lanes-per-warp
+// measurement of Sec. III-B (Observation 2).
+template <int TW, int TH, int LAYOUT>
+__global__ void __launch_bounds__(TW* TH)
+stats_kernel(BwdArgs p, unsigned long long* __restrict__ hist) {
+    constexpr int B = TW * TH;
+    __shared__ float4 s_a[B];
+    __shared__ float4 s_b[B];
+    __shared__ unsigned long long s_h[36];
+    __shared__ int s_maxlast;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int tile = blockIdx.x;
+    const int tx = tile % p.g.gx, ty = tile / p.g.gx;
+    int lx, ly;
+    lane_pixel<TW, LAYOUT>(tid, lx, ly);
+    const int px = tx * TW + lx, py = ty * TH + ly;
+    const bool inside = px < p.g.W && py < p.g.H;
+    const uint2 rg = p.ranges[tile];
+    const int nlist = (int)(rg.y - rg.x);
+    const size_t pix = (size_t)py * p.g.W + px;
+    const int last = inside ? min(max(p.n_contrib[pix], 0), nlist) : 0;
+    for (int i = tid; i < 36; i += B) s_h[i] = 0ull;
+    if (tid == 0) s_maxlast = 0;
+    __syncthreads();
+    const int wlast = __reduce_max_sync(kFull, last);
+    if (lane == 0) atomicMax(&s_maxlast, wlast);
+    atomicAdd(&s_h[34], (unsigned long long)last);
+    __syncthreads();
+    const int maxlast = s_maxlast;
+    unsigned long long active_pairs = 0;
+    for (int top = maxlast; top > 0; top -= B) {
+        const int cnt = min(B, top);
+        __syncthreads();
+        if (tid < cnt) {
+            uint32_t id = p.point_list[rg.x + (uint32_t)(top - 1 - tid)];
+            const float4* rec = reinterpret_cast<const float4*>(p.splat2d + (size_t)id * GSR_REC);
+            s_a[tid] = rec[0];
+            s_b[tid] = rec[1];
+        }
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) {
+            const int pos = top - 1 - k;
+            if (pos >= wlast) continue;
+            const float4 a = s_a[k], b = s_b[k];
+            SplatEval e;
+            const bool active = (pos < last) && eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, (float)px, (float)py, e);
+            const unsigned m = __ballot_sync(kFull, active);
+            active_pairs += active ? 1ull : 0ull;
+            if (lane == 0) {
+                atomicAdd(&s_h[__popc(m)], 1ull);
+                atomicAdd(&s_h[35], 1ull);
+            }
+        }
+    }
+    atomicAdd(&s_h[33], active_pairs);
+    __syncthreads();
+    for (int i = tid; i < 36; i += B)
+        if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
 }
 
 template <int MODE, int LAYOUT, bool STORE_T>
@@ -320,5 +455,26 @@ extern "C" int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32
         case GSR_REDUCE_HYBRID: launch_bwd_mode<GSR_REDUCE_HYBRID>(o.lane_layout, st, tiles, a, s); break;
         default: launch_bwd_mode<GSR_REDUCE_BLOCK>(o.lane_layout, st, tiles, a, s); break;
     }
+    return check_launch();
+}
+
+extern "C" int gsr_backward_stats(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                                  const uint32_t* tile_ranges, const uint32_t* point_list,
+                                  const float* splat2d, const int32_t* n_contrib, int32_t lane_layout,
+                                  uint64_t* hist, gsr_stream_t stream) {
+    if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !n_contrib || !hist) return GSR_EINVAL;
+    if (tile_w != 16 || tile_h != 16 || (lane_layout != 0 && lane_layout != 1)) return GSR_EINVAL;
+    BwdArgs a = {};
+    a.g = RasterGeom{width, height, (width + 15) / 16, (height + 15) / 16};
+    a.ranges = reinterpret_cast<const uint2*>(tile_ranges);
+    a.point_list = point_list;
+    a.splat2d = splat2d;
+    a.n_contrib = n_contrib;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(hist, 0, 36 * sizeof(uint64_t), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int tiles = a.g.gx * a.g.gy;
+    if (lane_layout == 0) stats_kernel<16, 16, 0><<<tiles, 256, 0, s>>>(a, (unsigned long long*)hist);
+    else stats_kernel<16, 16, 1><<<tiles, 256, 0, s>>>(a, (unsigned long long*)hist);
     return check_launch();
 }

@@ -91,13 +91,14 @@ def lib():
     L.gsr_forward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P]
     L.gsr_backward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P,
                                POINTER(BackwardOpts), P]
+    L.gsr_backward_stats.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, P, c_int32, P, P]
     L.gsr_backward_project.argtypes = [c_int32, c_int32, P, P, P, P, P, POINTER(Camera), P, P, P, P, P,
                                        P, P, P]
     L.gsr_l1_loss.argtypes = [c_int64, P, P, P, P, P]
     L.gsr_adam_step.argtypes = [c_int64, P, P, P, P, c_float, c_float, c_float, c_float, c_int32, P]
     L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
     for name in ("gsr_preprocess", "gsr_bin_scratch_bytes", "gsr_bin_sort", "gsr_forward", "gsr_backward",
-                 "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red"):
+                 "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -174,6 +175,14 @@ def gsr_backward(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d
                                               _ptr(point_list), _ptr(splat2d), _f3(bg), _ptr(final_T),
                                               _ptr(n_contrib), _ptr(dL_dimage), _ptr(grad2d),
                                               ctypes.byref(o), _stream(stream)))
+
+
+def gsr_backward_stats(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, n_contrib, hist,
+                       lane_layout=0, stream=None):
+    """hist: int64 tensor [36] (uint64 counts, see include/gsr.h)."""
+    _check("gsr_backward_stats", lib().gsr_backward_stats(width, height, tile_w, tile_h, _ptr(tile_ranges),
+                                                          _ptr(point_list), _ptr(splat2d), _ptr(n_contrib),
+                                                          lane_layout, _ptr(hist), _stream(stream)))
 
 
 def gsr_backward_project(n, sh_degree, mean, scale, quat, opacity, feat, cam, radius, grad2d, dmean,

@@ -113,3 +113,35 @@ class ViewBuffers:
         gsr.gsr_backward_project(self.n, sc.sh_degree, sc.mean, sc.scale, sc.quat, sc.opacity, sc.feat,
                                  self.c_cam, self.radius, self.grad2d, grads.mean, grads.scale, grads.quat,
                                  grads.opacity, grads.feat, stream)
+
+
+class Renderer:
+    """One view's render + backward through libgsr: the unit of work of the
+    training iteration (Sec. II-B, Fig. 2): projection, binning, forward blend,
+    L1 loss gradient, backward blend with gradient accumulation, backward
+    projection."""
+
+    def __init__(self, n, cam, device="cuda", opts=None, store_T=True, key_capacity=None):
+        self.vb = ViewBuffers(n, cam, device, key_capacity, store_T)
+        self.opts = opts if opts is not None else gsr.backward_opts("warp", 0, 0, store_T)
+        self.dimg = torch.zeros_like(self.vb.image)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+
+    def step(self, sc: SceneTensors, target: torch.Tensor, bg, grads: SceneTensors, stream=None,
+             on_backward=None):
+        """Runs the whole path; ``grads`` accumulates the 3D gradients.
+        Returns the device scalar L1 loss.  ``on_backward(begin: bool)`` is
+        called around the backward launch (event recording by benchmarks)."""
+        vb = self.vb
+        self.loss.zero_()
+        vb.preprocess(sc, zero_grad=True, stream=stream)
+        vb.bin(stream)
+        vb.forward(bg, stream)
+        gsr.gsr_l1_loss(vb.image.numel(), vb.image, target, self.dimg, self.loss, stream)
+        if on_backward:
+            on_backward(True)
+        vb.backward(bg, self.dimg, self.opts, stream)
+        if on_backward:
+            on_backward(False)
+        vb.backward_project(sc, grads, stream)
+        return self.loss
