@@ -36,6 +36,7 @@ extern "C" {
 #define GSR_ECUDA      (-3)  /* CUDA runtime / launch error                  */
 #define GSR_ETIMEOUT   (-4)  /* a bounded device wait gave up                */
 #define GSR_ESCRATCH   (-5)  /* scratch buffer smaller than required         */
+#define GSR_ELIMIT     (-6)  /* size beyond gsr_bin_sort_static's fixed limit */
 
 typedef void* gsr_stream_t;
 
@@ -148,6 +149,37 @@ int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32
                  void* scratch, size_t scratch_bytes, uint32_t* point_list,
                  uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,
                  gsr_stream_t stream);
+
+/*
+ * Allocation-free binning.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code that runs in
+ * a process whose GPU memory is owned by another allocator or a fixed
+ * budget, and loops that must not pay cudaMalloc's latency and implicit
+ * synchronisation.  It computes exactly what gsr_bin_sort computes, but its
+ * scratch is a static device array inside libgsr of
+ *   (GSR_STATIC_BIN_MAX_GAUSSIANS + 1) * 4 + GSR_STATIC_BIN_MAX_KEYS * 12
+ *   + 8 MiB bytes (about 60 MB),
+ * reserved on every GPU that loads the library's device code and held until
+ * the process exits.  The caller passes only inputs and outputs (as for
+ * gsr_bin_sort, plus keys_out, which is required here: it doubles as the
+ * sort's alternate key buffer).
+ *  - n > GSR_STATIC_BIN_MAX_GAUSSIANS, or a key count above
+ *    GSR_STATIC_BIN_MAX_KEYS, returns GSR_ELIMIT (nothing sorted).
+ *  - The first call on a device looks up the array's device address (once,
+ *    with that device current); make that first call before any stream
+ *    capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; nothing a call reads from it was left by an earlier call.  Calls
+ *    that overlap on the GPU (other streams, other host threads) race on it:
+ *    serialise them.
+ *  - Synchronises `stream` once (key count), like gsr_bin_sort.
+ */
+#define GSR_STATIC_BIN_MAX_GAUSSIANS (1 << 20)
+#define GSR_STATIC_BIN_MAX_KEYS (1 << 22)
+int gsr_bin_sort_static(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                        const float* splat2d, const int32_t* radius, int64_t key_capacity,
+                        uint32_t* point_list, uint32_t* tile_ranges, uint64_t* keys_out,
+                        int64_t* n_keys, gsr_stream_t stream);
 
 /*
  * Forward blend: for each pixel, front to back over its tile's list:

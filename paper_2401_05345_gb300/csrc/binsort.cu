@@ -2,6 +2,8 @@
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
+#include <mutex>
+
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -171,5 +173,123 @@ extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t ti
                                         (int)total, 0, g.end_bit, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     ranges_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>((long long)total, sorted_keys, tile_ranges);
+    return check_launch();
+}
+
+// ----------------------------------------------------------------------------
+// Allocation-free variant of gsr_bin_sort.
+//
+// Some callers cannot allocate device memory at all: code that runs where the
+// host process has handed every byte of the GPU to another allocator (a
+// framework's caching pool, an embedding application with a fixed budget),
+// or real-time loops that must never pay cudaMalloc's latency and implicit
+// device synchronisation.  For them the scratch of the binning lives in one
+// static device array inside this library, reserved when the library's
+// device code is loaded on a GPU and held until the process exits.
+// ----------------------------------------------------------------------------
+namespace gsr {
+namespace {
+
+constexpr size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kStaticCountsBytes = round256(sizeof(uint32_t) * ((size_t)GSR_STATIC_BIN_MAX_GAUSSIANS + 1));
+constexpr size_t kStaticKeysBytes = sizeof(uint64_t) * (size_t)GSR_STATIC_BIN_MAX_KEYS;
+constexpr size_t kStaticValsBytes = sizeof(uint32_t) * (size_t)GSR_STATIC_BIN_MAX_KEYS;
+constexpr size_t kStaticCubBytes = (size_t)8 << 20;
+constexpr size_t kStaticBytes = kStaticCountsBytes + kStaticKeysBytes + kStaticValsBytes + kStaticCubBytes;
+
+// Shared by every call on a device; contents persist between calls.
+static __device__ __align__(256) unsigned char g_bin_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_bin_scratch on the current device (looked up once per
+// device; the host-side symbol is only a stand-in for it).
+int static_scratch(unsigned char** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= kMaxDevices) return GSR_EINVAL;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_bin_scratch);
+        if (e != cudaSuccess) return cuda_fail(e);
+        // CUB's own temporary storage for the largest problem must fit its slice
+        size_t scan_b = 0, sort_b = 0;
+        cub::DoubleBuffer<uint64_t> kb(nullptr, nullptr);
+        cub::DoubleBuffer<uint32_t> vb(nullptr, nullptr);
+        e = cub::DeviceScan::ExclusiveSum(nullptr, scan_b, (uint32_t*)nullptr, (uint32_t*)nullptr,
+                                          GSR_STATIC_BIN_MAX_GAUSSIANS + 1);
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cub::DeviceRadixSort::SortPairs(nullptr, sort_b, kb, vb, GSR_STATIC_BIN_MAX_KEYS, 0, 64);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (scan_b > kStaticCubBytes || sort_b > kStaticCubBytes) return GSR_ESCRATCH;
+        g_static_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_static_ptr[dev];
+    return GSR_OK;
+}
+
+}  // namespace
+}  // namespace gsr
+
+extern "C" int gsr_bin_sort_static(int32_t n, int32_t width, int32_t height, int32_t tile_w,
+                                   int32_t tile_h, const float* splat2d, const int32_t* radius,
+                                   int64_t key_capacity, uint32_t* point_list, uint32_t* tile_ranges,
+                                   uint64_t* keys_out, int64_t* n_keys, gsr_stream_t stream_) {
+    BinGeom g;
+    if (n < 0 || key_capacity < 0 || key_capacity >= 0xffffffffll || !n_keys ||
+        !make_geom(width, height, tile_w, tile_h, g))
+        return GSR_EINVAL;
+    if (n > GSR_STATIC_BIN_MAX_GAUSSIANS) return GSR_ELIMIT;
+    if (!tile_ranges || (n > 0 && (!splat2d || !radius)) || (key_capacity > 0 && (!point_list || !keys_out)))
+        return GSR_EINVAL;
+    unsigned char* base = nullptr;
+    int rc = static_scratch(&base);
+    if (rc != GSR_OK) return rc;
+    uint32_t* counts = reinterpret_cast<uint32_t*>(base);
+    uint64_t* keys_tmp = reinterpret_cast<uint64_t*>(base + kStaticCountsBytes);
+    uint32_t* vals_tmp = reinterpret_cast<uint32_t*>(base + kStaticCountsBytes + kStaticKeysBytes);
+    void* cub_tmp = base + kStaticCountsBytes + kStaticKeysBytes + kStaticValsBytes;
+
+    cudaStream_t stream = (cudaStream_t)stream_;
+    cudaError_t e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)g.tiles, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *n_keys = 0;
+    if (n == 0) return GSR_OK;
+    // every counts[0..n] is written here, so nothing left by an earlier call is read
+    count_kernel<<<(n + 1 + 255) / 256, 256, 0, stream>>>(n, splat2d, radius, g, counts);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    size_t tb = kStaticCubBytes;
+    e = cub::DeviceScan::ExclusiveSum(cub_tmp, tb, counts, counts, n + 1, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    uint32_t total = 0;
+    e = cudaMemcpyAsync(&total, counts + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *n_keys = (int64_t)total;
+    if ((long long)total > key_capacity) return GSR_ECAPACITY;
+    if ((long long)total > GSR_STATIC_BIN_MAX_KEYS) return GSR_ELIMIT;
+    if (total == 0) return GSR_OK;
+    duplicate_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, splat2d, radius, g, counts, keys_tmp, vals_tmp);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    // double-buffered sort: the caller's outputs serve as the alternate buffers
+    cub::DoubleBuffer<uint64_t> kb(keys_tmp, keys_out);
+    cub::DoubleBuffer<uint32_t> vb(vals_tmp, point_list);
+    tb = kStaticCubBytes;
+    e = cub::DeviceRadixSort::SortPairs(cub_tmp, tb, kb, vb, (int)total, 0, g.end_bit, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (kb.Current() != keys_out) {
+        e = cudaMemcpyAsync(keys_out, kb.Current(), sizeof(uint64_t) * total, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (vb.Current() != point_list) {
+        e = cudaMemcpyAsync(point_list, vb.Current(), sizeof(uint32_t) * total, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    ranges_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>((long long)total, keys_out, tile_ranges);
     return check_launch();
 }

@@ -95,6 +95,7 @@ extern "C" const char* gsr_status_string(int status) {
         case GSR_ECUDA: return "CUDA error";
         case GSR_ETIMEOUT: return "bounded device wait timed out";
         case GSR_ESCRATCH: return "scratch buffer too small";
+        case GSR_ELIMIT: return "size exceeds the fixed limit of the allocation-free variant";
         default: return "unknown status";
     }
 }

@@ -15,7 +15,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgsr.so")
 
-GSR_OK, GSR_EINVAL, GSR_ECAPACITY, GSR_ECUDA, GSR_ETIMEOUT, GSR_ESCRATCH = 0, -1, -2, -3, -4, -5
+GSR_OK, GSR_EINVAL, GSR_ECAPACITY, GSR_ECUDA, GSR_ETIMEOUT, GSR_ESCRATCH, GSR_ELIMIT = 0, -1, -2, -3, -4, -5, -6
+STATIC_BIN_MAX_GAUSSIANS, STATIC_BIN_MAX_KEYS = 1 << 20, 1 << 22
 GSR_REC = 12
 REDUCE_PLAIN, REDUCE_WARP, REDUCE_HYBRID, REDUCE_BLOCK = 0, 1, 2, 3
 REDUCE_NAMES = {"plain": REDUCE_PLAIN, "warp": REDUCE_WARP, "hybrid": REDUCE_HYBRID, "block": REDUCE_BLOCK}
@@ -88,6 +89,8 @@ def lib():
                                         POINTER(c_size_t)]
     L.gsr_bin_sort.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, c_int64, P, c_size_t,
                                P, P, P, POINTER(c_int64), P]
+    L.gsr_bin_sort_static.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, c_int64, P, P, P,
+                                      POINTER(c_int64), P]
     L.gsr_forward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P]
     L.gsr_backward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P,
                                POINTER(BackwardOpts), P]
@@ -97,7 +100,8 @@ def lib():
     L.gsr_l1_loss.argtypes = [c_int64, P, P, P, P, P]
     L.gsr_adam_step.argtypes = [c_int64, P, P, P, P, c_float, c_float, c_float, c_float, c_int32, P]
     L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
-    for name in ("gsr_preprocess", "gsr_bin_scratch_bytes", "gsr_bin_sort", "gsr_forward", "gsr_backward",
+    for name in ("gsr_preprocess", "gsr_bin_scratch_bytes", "gsr_bin_sort", "gsr_bin_sort_static",
+                 "gsr_forward", "gsr_backward",
                  "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red"):
         getattr(L, name).restype = c_int
     _lib = L
@@ -158,6 +162,19 @@ def gsr_bin_sort(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity
                             _ptr(tile_ranges), _ptr(keys_out), ctypes.byref(nk), _stream(stream))
     if st not in (GSR_OK, GSR_ECAPACITY):
         _check("gsr_bin_sort", st)
+    return st, int(nk.value)
+
+
+def gsr_bin_sort_static(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity, point_list,
+                        tile_ranges, keys_out, stream=None):
+    """Allocation-free binning (scratch in a static device array of libgsr).
+    Returns (status, n_keys); status is GSR_OK, GSR_ECAPACITY or GSR_ELIMIT."""
+    nk = c_int64(0)
+    st = lib().gsr_bin_sort_static(n, width, height, tile_w, tile_h, _ptr(splat2d), _ptr(radius), key_capacity,
+                                   _ptr(point_list), _ptr(tile_ranges), _ptr(keys_out), ctypes.byref(nk),
+                                   _stream(stream))
+    if st not in (GSR_OK, GSR_ECAPACITY, GSR_ELIMIT):
+        _check("gsr_bin_sort_static", st)
     return st, int(nk.value)
 
 
