@@ -16,6 +16,10 @@
  *  - Gradient outputs ACCUMULATE (+=): the caller zeroes them first
  *    (gsr_preprocess can do that for grad2d in the same pass).
  *  - Images are planar float32 [3][H][W]; per-pixel maps float32/int32 [H][W].
+ *  - Alignment: splat2d and grad2d records must start on 16 bytes, tile_ranges
+ *    and keys on 8 bytes, binning scratch on 16 bytes (GSR_EINVAL otherwise);
+ *    feature arrays may have any 4-byte alignment (16-byte aligned ones are
+ *    read with vector loads).
  *  - Tiles: tile_w x tile_h pixels (each a power of two in [8,32], product
  *    <= 512); the grid has gx = ceil(W/tile_w) by gy = ceil(H/tile_h) tiles,
  *    tile id = ty*gx + tx.
@@ -95,6 +99,23 @@ typedef struct gsr_backward_opts {
                               (final_T / n_contrib may be NULL) */
     int32_t reserved[4];   /* must be zero */
 } gsr_backward_opts;
+
+/* One view of a batched backward (an array of these lives in DEVICE memory).
+ * All pointers are device pointers with the meaning and layout they have in
+ * gsr_backward; final_T / n_contrib may be NULL when store_T is 0; 16x16
+ * tiles. */
+typedef struct gsr_view {
+    int32_t width, height;
+    const uint32_t* tile_ranges;
+    const uint32_t* point_list;
+    const float* splat2d;
+    const float* final_T;
+    const int32_t* n_contrib;
+    const float* dL_dimage;
+    float* grad2d;
+    float bg[3];
+    int32_t reserved;
+} gsr_view;
 
 const char* gsr_status_string(int status);
 /* Text of the last CUDA error seen by the library in this thread. */
@@ -221,6 +242,33 @@ int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                  const gsr_backward_opts* opts, gsr_stream_t stream);
 
 /*
+ * Work order of a batched backward: one item per (view, 16x16 tile), encoded
+ * (view << 24) | tile, sorted by decreasing tile-list length (ties keep view
+ * then tile order) so the persistent launch schedules the longest tiles first
+ * (longest-processing-time order; the paper launches one view at a time).
+ *   views: device array [n_views] (n_views <= 256); item_offsets: device
+ *   int32 [n_views + 1], exclusive prefix sum of the views' tile counts;
+ *   items_out: device uint32 [n_items]; scratch: >= the bytes reported by
+ *   gsr_batch_order_scratch_bytes(n_items).  No host synchronisation; sizes are
+ *   fixed, so the call can be captured in a CUDA graph.
+ */
+int gsr_batch_order_scratch_bytes(int32_t n_items, size_t* bytes);
+int gsr_batch_order(int32_t n_views, const gsr_view* views, const int32_t* item_offsets, int32_t n_items,
+                    void* scratch, size_t scratch_bytes, uint32_t* items_out, gsr_stream_t stream);
+
+/*
+ * Batched backward over many views in one persistent launch: CTAs take items
+ * (from gsr_batch_order) off one device counter until all are done; each item
+ * is the gsr_backward of one tile of one view with the accumulation tier of
+ * opts (HOST pointer).  counter: device uint32, reset by this call.
+ * ctas_per_sm: CTAs per SM of the persistent grid (0 = the occupancy limit of
+ * the chosen kernel).  Asynchronous, no host synchronisation: capturable.
+ */
+int gsr_backward_batched(int32_t n_views, const gsr_view* views, const uint32_t* items, int32_t n_items,
+                         uint32_t* counter, const gsr_backward_opts* opts, int32_t ctas_per_sm,
+                         gsr_stream_t stream);
+
+/*
  * Traversal statistics of gsr_backward (nothing else is written): walks the
  * same lists as the backward with the same skip tests and fills the HOST-
  * visible-after-copy device array hist[36] (uint64, zeroed first):
@@ -259,6 +307,19 @@ int gsr_backward_project(int32_t n, int32_t sh_degree, const float* mean, const 
  */
 int gsr_l1_loss(int64_t count, const float* image, const float* target, float* dL_dimage,
                 float* loss_sum, gsr_stream_t stream);
+
+/*
+ * Parameter activations of the trainable scene (the 3DGS parameterisation the
+ * paper's workload trains, Sec. VI): scale = exp(log_scale) [n,3],
+ * opacity = 1 / (1 + exp(-opacity_logit)) [n].
+ * gsr_activate_backward ACCUMULATES dL/dlog_scale += dL/dscale * scale and
+ * dL/dlogit += dL/dopacity * o (1 - o), from the activated values.
+ */
+int gsr_activate(int64_t n, const float* log_scale, const float* opacity_logit, float* scale,
+                 float* opacity, gsr_stream_t stream);
+int gsr_activate_backward(int64_t n, const float* scale, const float* opacity, const float* dscale,
+                          const float* dopacity, float* dlog_scale, float* dopacity_logit,
+                          gsr_stream_t stream);
 
 /*
  * Adam (Kingma & Ba) on a flat float array of n parameters, step >= 1:

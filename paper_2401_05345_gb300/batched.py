@@ -1,0 +1,202 @@
+"""Many views of several scenes through one persistent, CUDA-graph-captured
+backward.
+
+Each view keeps its own buffers (``ViewBuffers``); their device pointers go
+into one device array of ``gsr_view`` descriptors.  The backward of all views
+is then: order the (view, tile) items by decreasing list length
+(``gsr_batch_order``), reset the work counter and launch the persistent
+kernel (``gsr_backward_batched``).  Sizes are fixed once the buffers exist, so
+the three calls are captured once in a CUDA graph and replayed every
+iteration; projection and binning (which read a key count back to the host)
+stay outside the graph.  The autotuner picks the accumulation tier,
+threshold, pixel-to-lane layout and CTAs per SM of the persistent launch.
+"""
+from __future__ import annotations
+
+import ctypes
+import statistics
+from ctypes import POINTER, c_float, c_int32, c_size_t, c_void_p
+
+import torch
+
+from . import gsr
+from .pipeline import SceneTensors, ViewBuffers
+
+
+class GsrView(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("tile_ranges", c_void_p), ("point_list", c_void_p),
+                ("splat2d", c_void_p), ("final_T", c_void_p), ("n_contrib", c_void_p), ("dL_dimage", c_void_p),
+                ("grad2d", c_void_p), ("bg", c_float * 3), ("reserved", c_int32)]
+
+
+def _setup_lib():
+    L = gsr.lib()
+    if not getattr(L, "_batched_ready", False):
+        P = c_void_p
+        L.gsr_batch_order_scratch_bytes.argtypes = [c_int32, POINTER(c_size_t)]
+        L.gsr_batch_order_scratch_bytes.restype = ctypes.c_int
+        L.gsr_batch_order.argtypes = [c_int32, P, P, c_int32, P, c_size_t, P, P]
+        L.gsr_batch_order.restype = ctypes.c_int
+        L.gsr_backward_batched.argtypes = [c_int32, P, P, c_int32, P, POINTER(gsr.BackwardOpts), c_int32, P]
+        L.gsr_backward_batched.restype = ctypes.c_int
+        L._batched_ready = True
+    return L
+
+
+def gsr_batch_order_scratch_bytes(n_items) -> int:
+    out = c_size_t(0)
+    gsr._check("gsr_batch_order_scratch_bytes", _setup_lib().gsr_batch_order_scratch_bytes(n_items, ctypes.byref(out)))
+    return int(out.value)
+
+
+def gsr_batch_order(n_views, views, item_offsets, n_items, scratch, items_out, stream=None):
+    gsr._check("gsr_batch_order", _setup_lib().gsr_batch_order(
+        n_views, gsr._ptr(views), gsr._ptr(item_offsets), n_items, gsr._ptr(scratch),
+        scratch.numel() * scratch.element_size(), gsr._ptr(items_out), gsr._stream(stream)))
+
+
+def gsr_backward_batched(n_views, views, items, n_items, counter, opts, ctas_per_sm=0, stream=None):
+    gsr._check("gsr_backward_batched", _setup_lib().gsr_backward_batched(
+        n_views, gsr._ptr(views), gsr._ptr(items), n_items, gsr._ptr(counter), ctypes.byref(opts),
+        int(ctas_per_sm), gsr._stream(stream)))
+
+
+class BatchedViews:
+    """Views ``[(scene_index, camera), ...]`` of ``scenes`` (SceneTensors)."""
+
+    def __init__(self, scenes, views, device="cuda", bg=(0.0, 0.0, 0.0), store_T=True):
+        self.scenes = scenes
+        self.views = views
+        self.device = device
+        self.bg = tuple(bg)
+        self.store_T = store_T
+        self.vbs = [ViewBuffers(scenes[s].n, cam, device, None, store_T) for (s, cam) in views]
+        self.dimg = [torch.zeros_like(vb.image) for vb in self.vbs]
+        self.loss = torch.zeros(len(views), dtype=torch.float32, device=device)
+        counts = [vb.gx * vb.gy for vb in self.vbs]
+        offs = [0]
+        for c in counts:
+            offs.append(offs[-1] + c)
+        self.n_items = offs[-1]
+        self.item_offsets = torch.tensor(offs, dtype=torch.int32, device=device)
+        self.items = torch.zeros(self.n_items, dtype=torch.int32, device=device)
+        self.order_scratch = torch.empty(gsr_batch_order_scratch_bytes(self.n_items), dtype=torch.uint8,
+                                         device=device)
+        self.counter = torch.zeros(1, dtype=torch.int32, device=device)
+        self.desc = torch.zeros(len(views) * ctypes.sizeof(GsrView), dtype=torch.uint8, device=device)
+        self._desc_key = None
+        self.graph = None
+        self._graph_key = None
+
+    # -- per-view stages (outside any graph) ---------------------------------
+    def render_all(self, targets=None, stream=None):
+        """Projection, binning and forward of every view; with ``targets``
+        (list of [3,H,W] tensors) also the L1 loss gradients."""
+        for i, ((s, cam), vb) in enumerate(zip(self.views, self.vbs)):
+            vb.preprocess(self.scenes[s], zero_grad=True, stream=stream)
+            vb.bin(stream)
+            vb.forward(self.bg, stream)
+            if targets is not None:
+                gsr.gsr_l1_loss(vb.image.numel(), vb.image, targets[i], self.dimg[i], self.loss[i:i + 1], stream)
+        self._refresh_descriptors()
+
+    def _refresh_descriptors(self):
+        key = tuple((vb.point_list.data_ptr(), vb.splat2d.data_ptr()) for vb in self.vbs)
+        if key == self._desc_key:
+            return
+        arr = (GsrView * len(self.vbs))()
+        for i, vb in enumerate(self.vbs):
+            d = arr[i]
+            d.width, d.height = vb.W, vb.H
+            d.tile_ranges = vb.tile_ranges.data_ptr()
+            d.point_list = vb.point_list.data_ptr()
+            d.splat2d = vb.splat2d.data_ptr()
+            d.final_T = vb.final_T.data_ptr() if vb.final_T is not None else None
+            d.n_contrib = vb.n_contrib.data_ptr() if vb.n_contrib is not None else None
+            d.dL_dimage = self.dimg[i].data_ptr()
+            d.grad2d = vb.grad2d.data_ptr()
+            for c in range(3):
+                d.bg[c] = self.bg[c]
+        host = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
+        self.desc.copy_(host)
+        torch.cuda.current_stream().synchronize()
+        self._desc_key = key
+        self.graph = None  # pointers changed: the captured graph is stale
+
+    # -- the batched backward --------------------------------------------------
+    def backward_batched(self, opts, ctas_per_sm=0, stream=None):
+        gsr_batch_order(len(self.vbs), self.desc, self.item_offsets, self.n_items, self.order_scratch, self.items,
+                        stream)
+        gsr_backward_batched(len(self.vbs), self.desc, self.items, self.n_items, self.counter, opts, ctas_per_sm,
+                             stream)
+
+    def capture(self, opts, ctas_per_sm=0):
+        """Captures the batched backward into a CUDA graph (once per option set
+        and buffer set)."""
+        key = (tuple(gsr_opts_tuple(opts)), ctas_per_sm, self._desc_key)
+        if self.graph is not None and self._graph_key == key:
+            return self.graph
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):  # warm-up outside capture
+            self.backward_batched(opts, ctas_per_sm)
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.backward_batched(opts, ctas_per_sm)
+        self.graph, self._graph_key = g, key
+        return g
+
+    def zero_grad2d(self):
+        for vb in self.vbs:
+            vb.grad2d.zero_()
+
+    def backward_per_view(self, opts, stream=None):
+        """The same work as one ``gsr_backward`` launch per view."""
+        for i, vb in enumerate(self.vbs):
+            vb.backward(self.bg, self.dimg[i], opts, stream)
+
+    def backproject_all(self, grads, stream=None):
+        """Accumulates every view's 3D gradients into ``grads[scene]``."""
+        for (s, _), vb in zip(self.views, self.vbs):
+            vb.backward_project(self.scenes[s], grads[s], stream)
+
+
+def gsr_opts_tuple(o):
+    return (int(o.reduce_mode), int(o.threshold), int(o.lane_layout), int(o.store_T))
+
+
+def time_graph(g, reps=5, before=None):
+    ts = []
+    for _ in range(reps):
+        if before:
+            before()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def autotune_batched(bv: BatchedViews, reps=3, flush=None):
+    """Tier x threshold x layout x CTAs-per-SM for the captured persistent
+    launch; returns (best opts, best ctas_per_sm, best ms, table)."""
+    cands = []
+    for lay in (0, 1):
+        cands.append((gsr.backward_opts("warp", 0, lay, bv.store_T), 0))
+        for thr in (8, 12, 16):
+            for cps in (0, 2, 3):
+                cands.append((gsr.backward_opts("hybrid", thr, lay, bv.store_T), cps))
+        cands.append((gsr.backward_opts("block", 0, lay, bv.store_T), 0))
+    table, best = {}, None
+    for o, cps in cands:
+        g = bv.capture(o, cps)
+        ms = time_graph(g, reps, flush)
+        name = f"{gsr_opts_tuple(o)}-cps{cps}"
+        table[name] = ms
+        if best is None or ms < best[2]:
+            best = (o, cps, ms)
+    bv.graph = None
+    return best[0], best[1], best[2], table

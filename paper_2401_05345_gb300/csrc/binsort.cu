@@ -138,6 +138,7 @@ extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t ti
         return GSR_EINVAL;
     if (!tile_ranges || !scratch || (n > 0 && (!splat2d || !radius)) || (key_capacity > 0 && !point_list))
         return GSR_EINVAL;
+    if (!aligned16(splat2d) || !aligned16(scratch) || (keys_out && !aligned8(keys_out))) return GSR_EINVAL;
     cudaStream_t stream = (cudaStream_t)stream_;
     Scratch s;
     int rc = layout(n, key_capacity, (char*)scratch, s);
@@ -246,6 +247,7 @@ extern "C" int gsr_bin_sort_static(int32_t n, int32_t width, int32_t height, int
     if (n > GSR_STATIC_BIN_MAX_GAUSSIANS) return GSR_ELIMIT;
     if (!tile_ranges || (n > 0 && (!splat2d || !radius)) || (key_capacity > 0 && (!point_list || !keys_out)))
         return GSR_EINVAL;
+    if (!aligned16(splat2d) || (keys_out && !aligned8(keys_out))) return GSR_EINVAL;
     unsigned char* base = nullptr;
     int rc = static_scratch(&base);
     if (rc != GSR_OK) return rc;

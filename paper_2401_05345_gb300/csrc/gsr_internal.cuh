@@ -22,6 +22,8 @@ int cuda_fail(cudaError_t e);
 int check_launch();
 
 inline bool pow2_in(int x, int lo, int hi) { return x >= lo && x <= hi && (x & (x - 1)) == 0; }
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+inline bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 // Tile rectangle of a splat: the 3DGS bounding-box rule written with
 // floor(u) so it is exact integer arithmetic ([x0,x1) x [y0,y1)).

@@ -56,6 +56,31 @@ __global__ void adam_kernel(long long n, float* __restrict__ p, const float* __r
     }
 }
 
+__global__ void activate_kernel(long long n, const float* __restrict__ log_scale, const float* __restrict__ logit,
+                                float* __restrict__ scale, float* __restrict__ opacity) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        scale[3 * i] = expf(log_scale[3 * i]);
+        scale[3 * i + 1] = expf(log_scale[3 * i + 1]);
+        scale[3 * i + 2] = expf(log_scale[3 * i + 2]);
+        opacity[i] = 1.0f / (1.0f + expf(-logit[i]));
+    }
+}
+
+__global__ void activate_backward_kernel(long long n, const float* __restrict__ scale,
+                                         const float* __restrict__ opacity, const float* __restrict__ dscale,
+                                         const float* __restrict__ dopacity, float* __restrict__ dlog_scale,
+                                         float* __restrict__ dlogit) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        dlog_scale[3 * i] += dscale[3 * i] * scale[3 * i];
+        dlog_scale[3 * i + 1] += dscale[3 * i + 1] * scale[3 * i + 1];
+        dlog_scale[3 * i + 2] += dscale[3 * i + 2] * scale[3 * i + 2];
+        const float o = opacity[i];
+        dlogit[i] += dopacity[i] * o * (1.0f - o);
+    }
+}
+
 // pattern 0: own address per lane; 1: one address per warp; 2: 9 lanes to a
 // 48-byte record; 3: 9 adds per lane into one record per warp.
 __global__ void __launch_bounds__(256) red_bench_kernel(int pattern, int iters, float* __restrict__ buf,
@@ -136,5 +161,28 @@ extern "C" int gsr_bench_red(int32_t pattern, int32_t blocks, int32_t iters, flo
     long long per_iter = pattern == 0 ? threads : pattern == 1 ? threads : pattern == 2 ? warps * 9 : threads * 9;
     *adds = per_iter * iters;
     red_bench_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(pattern, iters, buffer, buffer_floats);
+    return check_launch();
+}
+
+extern "C" int gsr_activate(int64_t n, const float* log_scale, const float* opacity_logit, float* scale,
+                            float* opacity, gsr_stream_t stream) {
+    if (n < 0 || (n > 0 && (!log_scale || !opacity_logit || !scale || !opacity))) return GSR_EINVAL;
+    if (n == 0) return GSR_OK;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    activate_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(n, log_scale, opacity_logit, scale, opacity);
+    return check_launch();
+}
+
+extern "C" int gsr_activate_backward(int64_t n, const float* scale, const float* opacity, const float* dscale,
+                                     const float* dopacity, float* dlog_scale, float* dopacity_logit,
+                                     gsr_stream_t stream) {
+    if (n < 0 || (n > 0 && (!scale || !opacity || !dscale || !dopacity || !dlog_scale || !dopacity_logit)))
+        return GSR_EINVAL;
+    if (n == 0) return GSR_OK;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    activate_backward_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(n, scale, opacity, dscale, dopacity,
+                                                                             dlog_scale, dopacity_logit);
     return check_launch();
 }

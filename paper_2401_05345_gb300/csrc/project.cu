@@ -87,12 +87,12 @@ __device__ __forceinline__ void sh_basis_vjp(int deg, float x, float y, float z,
     gx += -C3a * (3.f * xx - 3.f * yy) * c[15]; gy += C3a * 6.f * x * y * c[15];
 }
 
-// Loads / accumulates the 3K feature floats of one Gaussian (16-byte vectors
-// when 3K is a multiple of 4, so a thread's record is read with few wide
-// loads).
-template <int NF>
+// Loads / accumulates the 3K feature floats of one Gaussian: 16-byte vectors
+// when 3K is a multiple of 4 and the array is 16-byte aligned (VEC), so a
+// thread's record is read with few wide loads; scalar accesses otherwise.
+template <int NF, bool VEC>
 __device__ __forceinline__ void load_feat(const float* __restrict__ src, float* dst) {
-    if constexpr (NF % 4 == 0) {
+    if constexpr (VEC && NF % 4 == 0) {
         const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
         for (int j = 0; j < NF / 4; ++j) {
@@ -105,9 +105,9 @@ __device__ __forceinline__ void load_feat(const float* __restrict__ src, float* 
     }
 }
 
-template <int NF>
+template <int NF, bool VEC>
 __device__ __forceinline__ void add_feat(float* __restrict__ dst, const float* v) {
-    if constexpr (NF % 4 == 0) {
+    if constexpr (VEC && NF % 4 == 0) {
         float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
         for (int j = 0; j < NF / 4; ++j) {
@@ -188,7 +188,7 @@ __device__ __forceinline__ bool project(const Cam& k, const float* mean, const f
     return true;
 }
 
-template <int DEG>
+template <int DEG, bool VEC>
 __global__ void __launch_bounds__(256)
 preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict__ scale,
                   const float* __restrict__ quat, const float* __restrict__ opacity,
@@ -231,7 +231,7 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
         float Y[16];
         sh_basis(DEG, dx * il, dy * il, dz * il, Y);
         float f[3 * K];
-        load_feat<3 * K>(feat + (size_t)i * K * 3, f);
+        load_feat<3 * K, VEC>(feat + (size_t)i * K * 3, f);
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
@@ -249,7 +249,7 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
     rec[2] = make_float4(rgb[2], P.p[2], 0.f, 0.f);
 }
 
-template <int DEG>
+template <int DEG, bool VEC>
 __global__ void __launch_bounds__(128)
 backproject_kernel(int n, const float* __restrict__ mean, const float* __restrict__ scale,
                    const float* __restrict__ quat, const float* __restrict__ feat, Cam k,
@@ -280,7 +280,7 @@ backproject_kernel(int n, const float* __restrict__ mean, const float* __restric
         float Y[16];
         sh_basis(DEG, x, y, z, Y);
         float f[3 * K];
-        load_feat<3 * K>(feat + (size_t)i * K * 3, f);
+        load_feat<3 * K, VEC>(feat + (size_t)i * K * 3, f);
         float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
         for (int j = 0; j < K; ++j)
@@ -296,7 +296,7 @@ backproject_kernel(int n, const float* __restrict__ mean, const float* __restric
             for (int ch = 0; ch < 3; ++ch) df[3 * j + ch] = Y[j] * gcol[ch];
             cw[j] = f[3 * j] * gcol[0] + f[3 * j + 1] * gcol[1] + f[3 * j + 2] * gcol[2];
         }
-        add_feat<3 * K>(dfeat + (size_t)i * K * 3, df);
+        add_feat<3 * K, VEC>(dfeat + (size_t)i * K * 3, df);
         float ddx, ddy, ddz;
         sh_basis_vjp(DEG, x, y, z, cw, ddx, ddy, ddz);
         float dot = x * ddx + y * ddy + z * ddz;
@@ -392,14 +392,23 @@ extern "C" int gsr_preprocess(int32_t n, int32_t sh_degree, const float* mean, c
     if (n < 0 || sh_degree < -1 || sh_degree > 3 || !cam || !tiles_ok(tile_w, tile_h)) return GSR_EINVAL;
     if (n == 0) return GSR_OK;
     if (!mean || !scale || !quat || !opacity || !feat || !splat2d || !radius) return GSR_EINVAL;
+    if (!aligned16(splat2d) || (grad2d_to_zero && !aligned16(grad2d_to_zero))) return GSR_EINVAL;
     if (cam->width <= 0 || cam->height <= 0) return GSR_EINVAL;
     Cam k = make_cam(*cam);
     int gx = (cam->width + tile_w - 1) / tile_w, gy = (cam->height + tile_h - 1) / tile_h;
     const int blocks = (n + 255) / 256;
     cudaStream_t st = (cudaStream_t)stream;
     const int twl = ilog2(tile_w), thl = ilog2(tile_h);
-#define GSR_PRE(D) preprocess_kernel<D><<<blocks, 256, 0, st>>>(n, mean, scale, quat, opacity, feat, k, gx, gy, \
-                                                             twl, thl, splat2d, radius, grad2d_to_zero)
+    const bool vec = aligned16(feat);
+#define GSR_PRE(D)                                                                                          \
+    do {                                                                                                    \
+        if (vec) preprocess_kernel<D, true><<<blocks, 256, 0, st>>>(n, mean, scale, quat, opacity, feat, k, \
+                                                                    gx, gy, twl, thl, splat2d, radius,      \
+                                                                    grad2d_to_zero);                        \
+        else preprocess_kernel<D, false><<<blocks, 256, 0, st>>>(n, mean, scale, quat, opacity, feat, k,   \
+                                                                 gx, gy, twl, thl, splat2d, radius,         \
+                                                                 grad2d_to_zero);                           \
+    } while (0)
     switch (sh_degree) {
         case -1: GSR_PRE(-1); break;
         case 0: GSR_PRE(0); break;
@@ -422,11 +431,20 @@ extern "C" int gsr_backward_project(int32_t n, int32_t sh_degree, const float* m
     if (!mean || !scale || !quat || !feat || !radius || !grad2d || !dmean || !dscale || !dquat ||
         !dopacity || !dfeat)
         return GSR_EINVAL;
+    if (!aligned16(grad2d)) return GSR_EINVAL;
     Cam k = make_cam(*cam);
     const int blocks = (n + 127) / 128;
     cudaStream_t st = (cudaStream_t)stream;
-#define GSR_BP(D) backproject_kernel<D><<<blocks, 128, 0, st>>>(n, mean, scale, quat, feat, k, radius, grad2d, \
-                                                                dmean, dscale, dquat, dopacity, dfeat)
+    const bool vec = aligned16(feat) && aligned16(dfeat);
+#define GSR_BP(D)                                                                                            \
+    do {                                                                                                     \
+        if (vec) backproject_kernel<D, true><<<blocks, 128, 0, st>>>(n, mean, scale, quat, feat, k, radius,  \
+                                                                     grad2d, dmean, dscale, dquat, dopacity, \
+                                                                     dfeat);                                 \
+        else backproject_kernel<D, false><<<blocks, 128, 0, st>>>(n, mean, scale, quat, feat, k, radius,    \
+                                                                  grad2d, dmean, dscale, dquat, dopacity,   \
+                                                                  dfeat);                                   \
+    } while (0)
     switch (sh_degree) {
         case -1: GSR_BP(-1); break;
         case 0: GSR_BP(0); break;

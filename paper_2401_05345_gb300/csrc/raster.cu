@@ -7,6 +7,8 @@
 // same splat at the same time -- the property that makes the warp-level
 // reduction of the backward legal without a match (Sec. V-A2 requires all
 // lanes to update the same primitive; here it holds by construction).
+#include <cub/device/device_radix_sort.cuh>
+
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -177,20 +179,32 @@ struct BwdArgs {
     int threshold;
 };
 
+template <int B, int MODE>
+struct BwdSmem {
+    float4 a[B];
+    float4 b[B];
+    float c[B];
+    uint32_t id[B];
+    unsigned mask[B];
+    float acc[MODE == GSR_REDUCE_BLOCK ? B * 9 : 1];
+    int maxlast;
+};
+
+// Backward of one tile: the gradient-computation step (Sec. III-A) for the
+// tile's pixels, accumulated by the tier MODE.  All threads of the CTA call
+// it; shared storage is reused across calls.
 template <int TW, int TH, int MODE, int LAYOUT, bool STORE_T>
-__global__ void __launch_bounds__(TW* TH)
-backward_kernel(BwdArgs p) {
+__device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, BwdSmem<TW * TH, MODE>& sm) {
     constexpr int B = TW * TH;
-    __shared__ float4 s_a[B];
-    __shared__ float4 s_b[B];
-    __shared__ float s_c[B];
-    __shared__ uint32_t s_id[B];
-    __shared__ unsigned s_mask[B];
-    __shared__ float s_acc[MODE == GSR_REDUCE_BLOCK ? B * 9 : 1];
-    __shared__ int s_maxlast;
+    float4* s_a = sm.a;
+    float4* s_b = sm.b;
+    float* s_c = sm.c;
+    uint32_t* s_id = sm.id;
+    unsigned* s_mask = sm.mask;
+    float* s_acc = sm.acc;
+    int& s_maxlast = sm.maxlast;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
     const int tx = tile % p.g.gx, ty = tile / p.g.gx;
     int lx, ly;
     lane_pixel<TW, LAYOUT>(tid, lx, ly);
@@ -323,6 +337,46 @@ backward_kernel(BwdArgs p) {
     }
 }
 
+
+template <int TW, int TH, int MODE, int LAYOUT, bool STORE_T>
+__global__ void __launch_bounds__(TW* TH)
+backward_kernel(BwdArgs p) {
+    __shared__ BwdSmem<TW * TH, MODE> sm;
+    backward_tile<TW, TH, MODE, LAYOUT, STORE_T>(p, blockIdx.x, sm);
+}
+
+// Persistent backward over many views: each CTA takes (view, tile) items in
+// the given order (longest tile lists first) from one atomic counter until
+// the list is exhausted.  No CTA waits on another.
+template <int TW, int TH, int MODE, int LAYOUT, bool STORE_T>
+__global__ void __launch_bounds__(TW* TH)
+backward_batched_kernel(const gsr_view* __restrict__ views, const uint32_t* __restrict__ items, int n_items,
+                        unsigned* __restrict__ counter, int threshold) {
+    __shared__ BwdSmem<TW * TH, MODE> sm;
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const uint32_t code = items[it];
+        const gsr_view& v = views[code >> 24];
+        BwdArgs p;
+        p.g = RasterGeom{v.width, v.height, (v.width + TW - 1) / TW, (v.height + TH - 1) / TH};
+        p.ranges = reinterpret_cast<const uint2*>(v.tile_ranges);
+        p.point_list = v.point_list;
+        p.splat2d = v.splat2d;
+        p.bg0 = v.bg[0]; p.bg1 = v.bg[1]; p.bg2 = v.bg[2];
+        p.final_T = v.final_T;
+        p.n_contrib = v.n_contrib;
+        p.dL_dimage = v.dL_dimage;
+        p.grad2d = v.grad2d;
+        p.threshold = threshold;
+        backward_tile<TW, TH, MODE, LAYOUT, STORE_T>(p, (int)(code & 0xffffffu), sm);
+    }
+}
+
 // Counts of the backward traversal (no gradients written): per (warp, splat)
 // step the number of active lanes -> hist[0..32]; hist[33] = active pairs,
 // hist[34] = examined pairs (sum of n_contrib), hist[35] = warp steps with at
@@ -386,6 +440,51 @@ stats_kernel(BwdArgs p, unsigned long long* __restrict__ hist) {
         if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
 }
 
+// Sort keys of the batched work order: larger tile lists first.
+__global__ void batch_keys_kernel(int n_views, const gsr_view* __restrict__ views,
+                                  const int* __restrict__ offsets, int n_items, uint32_t* __restrict__ keys,
+                                  uint32_t* __restrict__ vals) {
+    __shared__ int s_off[257];
+    for (int i = threadIdx.x; i <= n_views; i += blockDim.x) s_off[i] = offsets[i];
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_items; i += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_views - 1;  // last view with offset <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        const int t = i - s_off[lo];
+        const uint32_t* r = views[lo].tile_ranges;
+        const uint32_t len = r[2 * t + 1] - r[2 * t];
+        keys[i] = 0xffffffffu - len;
+        vals[i] = ((uint32_t)lo << 24) | (uint32_t)t;
+    }
+}
+
+template <int MODE, int LAYOUT, bool STORE_T>
+int launch_batched(int n_items, const gsr_view* views, const uint32_t* items, unsigned* counter, int thr,
+                   int ctas_per_sm, cudaStream_t s) {
+    auto k = backward_batched_kernel<16, 16, MODE, LAYOUT, STORE_T>;
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int per_sm = ctas_per_sm > 0 ? min(ctas_per_sm, max(occ, 1)) : max(occ, 1);
+    k<<<sms * per_sm, 256, 0, s>>>(views, items, n_items, counter, thr);
+    return check_launch();
+}
+
+template <int MODE>
+int launch_batched_mode(int layout, bool store, int n_items, const gsr_view* views, const uint32_t* items,
+                        unsigned* counter, int thr, int cps, cudaStream_t s) {
+    if (layout == 0)
+        return store ? launch_batched<MODE, 0, true>(n_items, views, items, counter, thr, cps, s)
+                     : launch_batched<MODE, 0, false>(n_items, views, items, counter, thr, cps, s);
+    return store ? launch_batched<MODE, 1, true>(n_items, views, items, counter, thr, cps, s)
+                 : launch_batched<MODE, 1, false>(n_items, views, items, counter, thr, cps, s);
+}
+
 template <int MODE, int LAYOUT, bool STORE_T>
 void launch_bwd(int tiles, const BwdArgs& a, cudaStream_t s) {
     backward_kernel<16, 16, MODE, LAYOUT, STORE_T><<<tiles, 256, 0, s>>>(a);
@@ -412,6 +511,7 @@ extern "C" int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_
                            const float* bg, float* image, float* final_T, int32_t* n_contrib,
                            gsr_stream_t stream) {
     if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !bg || !image) return GSR_EINVAL;
+    if (!aligned16(splat2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
     if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
     RasterGeom g{width, height, (width + 15) / 16, (height + 15) / 16};
     int tiles = g.gx * g.gy;
@@ -429,6 +529,7 @@ extern "C" int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32
     gsr_backward_opts o = {GSR_REDUCE_WARP, 0, 0, 1, {0, 0, 0, 0}};
     if (opts) o = *opts;
     if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !bg || !dL_dimage || !grad2d) return GSR_EINVAL;
+    if (!aligned16(splat2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
     if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
     if (o.reduce_mode < GSR_REDUCE_PLAIN || o.reduce_mode > GSR_REDUCE_BLOCK) return GSR_EINVAL;
     if (o.threshold < 0 || o.threshold > 33 || (o.lane_layout != 0 && o.lane_layout != 1)) return GSR_EINVAL;
@@ -463,6 +564,7 @@ extern "C" int gsr_backward_stats(int32_t width, int32_t height, int32_t tile_w,
                                   const float* splat2d, const int32_t* n_contrib, int32_t lane_layout,
                                   uint64_t* hist, gsr_stream_t stream) {
     if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !n_contrib || !hist) return GSR_EINVAL;
+    if (!aligned16(splat2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
     if (tile_w != 16 || tile_h != 16 || (lane_layout != 0 && lane_layout != 1)) return GSR_EINVAL;
     BwdArgs a = {};
     a.g = RasterGeom{width, height, (width + 15) / 16, (height + 15) / 16};
@@ -477,4 +579,81 @@ extern "C" int gsr_backward_stats(int32_t width, int32_t height, int32_t tile_w,
     if (lane_layout == 0) stats_kernel<16, 16, 0><<<tiles, 256, 0, s>>>(a, (unsigned long long*)hist);
     else stats_kernel<16, 16, 1><<<tiles, 256, 0, s>>>(a, (unsigned long long*)hist);
     return check_launch();
+}
+
+namespace gsr {
+namespace {
+size_t order_layout(int n_items, char* base, uint32_t** keys_in, uint32_t** keys_out, uint32_t** vals_in,
+                    void** tmp, size_t* tmp_bytes) {
+    size_t sort_bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, (uint32_t*)nullptr, (uint32_t*)nullptr,
+                                    (uint32_t*)nullptr, (uint32_t*)nullptr, n_items > 0 ? n_items : 1, 0, 32);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t vec = al(sizeof(uint32_t) * (size_t)(n_items > 0 ? n_items : 1));
+    size_t off = 0;
+    if (keys_in) *keys_in = base ? (uint32_t*)(base + off) : nullptr;
+    off += vec;
+    if (keys_out) *keys_out = base ? (uint32_t*)(base + off) : nullptr;
+    off += vec;
+    if (vals_in) *vals_in = base ? (uint32_t*)(base + off) : nullptr;
+    off += vec;
+    if (tmp) *tmp = base ? (void*)(base + off) : nullptr;
+    if (tmp_bytes) *tmp_bytes = sort_bytes;
+    return off + al(sort_bytes);
+}
+}  // namespace
+}  // namespace gsr
+
+extern "C" int gsr_batch_order_scratch_bytes(int32_t n_items, size_t* bytes) {
+    if (n_items < 0 || !bytes) return GSR_EINVAL;
+    *bytes = order_layout(n_items, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return GSR_OK;
+}
+
+extern "C" int gsr_batch_order(int32_t n_views, const gsr_view* views, const int32_t* item_offsets,
+                               int32_t n_items, void* scratch, size_t scratch_bytes, uint32_t* items_out,
+                               gsr_stream_t stream_) {
+    if (n_views <= 0 || n_views > 256 || n_items < 0 || !views || !item_offsets || !scratch || !items_out)
+        return GSR_EINVAL;
+    if (n_items == 0) return GSR_OK;
+    uint32_t *kin, *kout, *vin;
+    void* tmp;
+    size_t tb;
+    size_t need = order_layout(n_items, (char*)scratch, &kin, &kout, &vin, &tmp, &tb);
+    if (scratch_bytes < need) return GSR_ESCRATCH;
+    cudaStream_t s = (cudaStream_t)stream_;
+    const int blocks = min((n_items + 255) / 256, 152 * 4);
+    batch_keys_kernel<<<blocks, 256, 0, s>>>(n_views, views, item_offsets, n_items, kin, vin);
+    int rc = check_launch();
+    if (rc != GSR_OK) return rc;
+    cudaError_t e = cub::DeviceRadixSort::SortPairs(tmp, tb, kin, kout, vin, items_out, n_items, 0, 32, s);
+    return e == cudaSuccess ? GSR_OK : cuda_fail(e);
+}
+
+extern "C" int gsr_backward_batched(int32_t n_views, const gsr_view* views, const uint32_t* items, int32_t n_items,
+                                    uint32_t* counter, const gsr_backward_opts* opts, int32_t ctas_per_sm,
+                                    gsr_stream_t stream_) {
+    gsr_backward_opts o = {GSR_REDUCE_WARP, 0, 0, 1, {0, 0, 0, 0}};
+    if (opts) o = *opts;
+    if (n_views <= 0 || n_views > 256 || n_items < 0 || !views || !counter || (n_items > 0 && !items)) return GSR_EINVAL;
+    if (o.reduce_mode < GSR_REDUCE_PLAIN || o.reduce_mode > GSR_REDUCE_BLOCK) return GSR_EINVAL;
+    if (o.threshold < 0 || o.threshold > 33 || (o.lane_layout != 0 && o.lane_layout != 1)) return GSR_EINVAL;
+    if ((o.store_T != 0 && o.store_T != 1) || ctas_per_sm < 0) return GSR_EINVAL;
+    for (int i = 0; i < 4; ++i) if (o.reserved[i] != 0) return GSR_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream_;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (n_items == 0) return GSR_OK;
+    const bool st = o.store_T != 0;
+    unsigned* c = (unsigned*)counter;
+    switch (o.reduce_mode) {
+        case GSR_REDUCE_PLAIN:
+            return launch_batched_mode<GSR_REDUCE_PLAIN>(o.lane_layout, st, n_items, views, items, c, o.threshold, ctas_per_sm, s);
+        case GSR_REDUCE_WARP:
+            return launch_batched_mode<GSR_REDUCE_WARP>(o.lane_layout, st, n_items, views, items, c, o.threshold, ctas_per_sm, s);
+        case GSR_REDUCE_HYBRID:
+            return launch_batched_mode<GSR_REDUCE_HYBRID>(o.lane_layout, st, n_items, views, items, c, o.threshold, ctas_per_sm, s);
+        default:
+            return launch_batched_mode<GSR_REDUCE_BLOCK>(o.lane_layout, st, n_items, views, items, c, o.threshold, ctas_per_sm, s);
+    }
 }

@@ -98,11 +98,14 @@ def lib():
     L.gsr_backward_project.argtypes = [c_int32, c_int32, P, P, P, P, P, POINTER(Camera), P, P, P, P, P,
                                        P, P, P]
     L.gsr_l1_loss.argtypes = [c_int64, P, P, P, P, P]
+    L.gsr_activate.argtypes = [c_int64, P, P, P, P, P]
+    L.gsr_activate_backward.argtypes = [c_int64, P, P, P, P, P, P, P]
     L.gsr_adam_step.argtypes = [c_int64, P, P, P, P, c_float, c_float, c_float, c_float, c_int32, P]
     L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
     for name in ("gsr_preprocess", "gsr_bin_scratch_bytes", "gsr_bin_sort", "gsr_bin_sort_static",
                  "gsr_forward", "gsr_backward",
-                 "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red"):
+                 "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red",
+                 "gsr_activate", "gsr_activate_backward"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -214,6 +217,17 @@ def gsr_backward_project(n, sh_degree, mean, scale, quat, opacity, feat, cam, ra
 def gsr_l1_loss(count, image, target, dL_dimage, loss_sum=None, stream=None):
     _check("gsr_l1_loss", lib().gsr_l1_loss(count, _ptr(image), _ptr(target), _ptr(dL_dimage),
                                             _ptr(loss_sum), _stream(stream)))
+
+
+def gsr_activate(n, log_scale, opacity_logit, scale, opacity, stream=None):
+    _check("gsr_activate", lib().gsr_activate(n, _ptr(log_scale), _ptr(opacity_logit), _ptr(scale), _ptr(opacity),
+                                              _stream(stream)))
+
+
+def gsr_activate_backward(n, scale, opacity, dscale, dopacity, dlog_scale, dopacity_logit, stream=None):
+    _check("gsr_activate_backward", lib().gsr_activate_backward(
+        n, _ptr(scale), _ptr(opacity), _ptr(dscale), _ptr(dopacity), _ptr(dlog_scale), _ptr(dopacity_logit),
+        _stream(stream)))
 
 
 def gsr_adam_step(n, param, grad, m, v, lr, beta1, beta2, eps, step, stream=None):

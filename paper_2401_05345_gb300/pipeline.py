@@ -77,9 +77,14 @@ class ViewBuffers:
         sb = gsr.gsr_bin_scratch_bytes(self.n, self.W, self.H, self.tw, self.th, self.key_capacity)
         self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
 
+    def release_scratch(self):
+        """Drops the binning scratch (not needed after binning; regrown on the
+        next ``bin``)."""
+        self.scratch = None
+
     def device_bytes(self) -> int:
-        ts = [self.splat2d, self.radius, self.grad2d, self.tile_ranges, self.image, self.point_list,
-              self.scratch]
+        ts = [self.splat2d, self.radius, self.grad2d, self.tile_ranges, self.image, self.point_list]
+        ts += [self.scratch] if self.scratch is not None else []
         ts += [t for t in (self.final_T, self.n_contrib) if t is not None]
         return sum(t.numel() * t.element_size() for t in ts)
 
@@ -90,6 +95,9 @@ class ViewBuffers:
                            self.grad2d if zero_grad else None, stream)
 
     def bin(self, stream=None, keys_out=None):
+        if self.scratch is None:
+            sb = gsr.gsr_bin_scratch_bytes(self.n, self.W, self.H, self.tw, self.th, self.key_capacity)
+            self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
         while True:
             st, nk = gsr.gsr_bin_sort(self.n, self.W, self.H, self.tw, self.th, self.splat2d, self.radius,
                                       self.key_capacity, self.scratch, self.point_list, self.tile_ranges,

@@ -1,0 +1,414 @@
+"""Serving loop for concurrent scene-fitting jobs.
+
+Each job fits one Gaussian scene to target views: every request is one
+training step (render, L1 loss, backward, backward projection, activation
+backward, Adam), the iteration of Sec. II-B (Fig. 2).  A job's parameters,
+gradients, Adam moments and sort buffers stay on the device while it is
+admitted.
+
+* Admission by HBM footprint: a job is admitted (first fit, in arrival order)
+  when its device footprint fits in what the budget leaves; a job larger than
+  the whole budget is refused.  Its memory is released when its last step
+  completes or it is cancelled, and waiting jobs are admitted then.
+* Continuous batching: requests arrive over time (Poisson); whenever one of
+  the ``slots`` CUDA streams is idle, the oldest ready request (its job
+  admitted and not already stepping) is issued on it, so steps of different
+  jobs overlap on the device and new arrivals join while others run.
+* Latency of a request = device completion time - arrival time (queueing
+  included); p50 / p99 and steps/s are reported.
+
+``Scheduler`` is pure host logic (tested on the CPU with a fake executor);
+``GpuExecutor`` runs the steps through libgsr.
+"""
+from __future__ import annotations
+
+import dataclasses
+import heapq
+import json
+import math
+import time
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# host-side scheduling
+# ----------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Job:
+    job_id: int
+    n: int                     # Gaussians
+    steps: int                 # requests this job will make
+    arrival: float             # seconds
+    footprint: int = 0         # device bytes while admitted
+    state: str = "waiting"     # waiting | admitted | done | refused | cancelled
+    done_steps: int = 0
+    busy: bool = False
+    payload: object = None     # executor data (scene, camera, targets)
+
+
+@dataclasses.dataclass(order=True)
+class Request:
+    arrival: float
+    job_id: int
+    step: int
+
+
+@dataclasses.dataclass
+class Result:
+    job_id: int
+    step: int
+    arrival: float
+    issued: float
+    completed: float
+    loss: float
+
+
+class Scheduler:
+    """Admission by footprint and continuous batching over ``slots``."""
+
+    def __init__(self, budget_bytes: int, slots: int):
+        self.budget = int(budget_bytes)
+        self.slots = int(slots)
+        self.jobs: dict[int, Job] = {}
+        self.used = 0
+        self.pending: list[Request] = []      # arrived, not issued (heap by arrival)
+        self.waiting: list[int] = []          # job ids waiting for admission, arrival order
+        self.events: list[str] = []
+        self.peak_used = 0
+
+    def add_job(self, job: Job):
+        self.jobs[job.job_id] = job
+        if job.footprint > self.budget:
+            job.state = "refused"
+            self.events.append(f"refuse {job.job_id}")
+            return False
+        self.waiting.append(job.job_id)
+        return True
+
+    def admit(self, on_admit):
+        """First-fit admission in arrival order."""
+        still = []
+        for jid in self.waiting:
+            job = self.jobs[jid]
+            if job.state != "waiting":
+                continue
+            if self.used + job.footprint <= self.budget:
+                on_admit(job)
+                job.state = "admitted"
+                self.used += job.footprint
+                self.peak_used = max(self.peak_used, self.used)
+                self.events.append(f"admit {jid}")
+            else:
+                still.append(jid)
+        self.waiting = still
+
+    def arrive(self, req: Request):
+        job = self.jobs[req.job_id]
+        if job.state in ("refused", "cancelled", "done"):
+            return
+        heapq.heappush(self.pending, req)
+
+    def next_ready(self):
+        """Oldest arrived request whose job is admitted and idle and whose
+        step is that job's next one."""
+        skipped, found = [], None
+        while self.pending:
+            r = heapq.heappop(self.pending)
+            job = self.jobs[r.job_id]
+            if job.state in ("cancelled", "refused", "done"):
+                continue
+            if job.state == "admitted" and not job.busy and r.step == job.done_steps:
+                found = r
+                break
+            skipped.append(r)
+        for r in skipped:
+            heapq.heappush(self.pending, r)
+        if found is not None:
+            self.jobs[found.job_id].busy = True
+        return found
+
+    def complete(self, job_id, on_release):
+        job = self.jobs[job_id]
+        job.busy = False
+        job.done_steps += 1
+        if job.done_steps >= job.steps and job.state == "admitted":
+            job.state = "done"
+            self._release(job, on_release)
+
+    def cancel(self, job_id, on_release):
+        job = self.jobs[job_id]
+        if job.state == "admitted" and not job.busy:
+            self._release(job, on_release)
+        elif job.state == "waiting":
+            self.waiting = [j for j in self.waiting if j != job_id]
+        job.state = "cancelled"
+        self.events.append(f"cancel {job_id}")
+
+    def _release(self, job, on_release):
+        self.used -= job.footprint
+        on_release(job)
+        self.events.append(f"release {job.job_id}")
+
+    def all_finished(self):
+        return all(j.state in ("done", "refused", "cancelled") for j in self.jobs.values())
+
+
+def poisson_requests(jobs, rate_per_job, seed):
+    """Per job, step requests after its arrival with exponential gaps."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for j in jobs:
+        t = j.arrival
+        for s in range(j.steps):
+            t += rng.exponential(1.0 / rate_per_job)
+            reqs.append(Request(t, j.job_id, s))
+    reqs.sort()
+    return reqs
+
+
+def percentile(xs, q):
+    if not xs:
+        return float("nan")
+    return float(np.percentile(np.asarray(xs, np.float64), q))
+
+
+def summarize(results, wall_s):
+    lat = [1e3 * (r.completed - r.arrival) for r in results]
+    return {"requests": len(results), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+            "mean_ms": float(np.mean(lat)) if lat else float("nan"),
+            "steps_per_s": len(results) / wall_s if wall_s > 0 else float("nan"), "wall_s": wall_s}
+
+
+def serve(scheduler: Scheduler, requests, executor, cancel_at=None, poll_sleep=0.0):
+    """Runs the loop until every job is finished.  ``requests`` are released
+    at their arrival times (seconds from start); ``executor`` provides
+    load/unload/issue/poll/now.  ``cancel_at``: {job_id: time}."""
+    results = []
+    inflight = {}  # slot -> (request, handle)
+    free_slots = list(range(scheduler.slots))
+    reqs = list(requests)
+    ri = 0
+    cancel_at = dict(cancel_at or {})
+    t0 = executor.now()
+    while True:
+        now = executor.now() - t0
+        while ri < len(reqs) and reqs[ri].arrival <= now:
+            scheduler.arrive(reqs[ri])
+            ri += 1
+        for jid, tc in list(cancel_at.items()):
+            if tc <= now and not scheduler.jobs[jid].busy:
+                scheduler.cancel(jid, executor.unload)
+                del cancel_at[jid]
+        scheduler.admit(executor.load)
+        while free_slots:
+            r = scheduler.next_ready()
+            if r is None:
+                break
+            slot = free_slots.pop()
+            inflight[slot] = (r, executor.issue(slot, scheduler.jobs[r.job_id], r.step), now)
+        for slot in list(inflight):
+            r, h, issued = inflight[slot]
+            done = executor.poll(h)
+            if done is not None:
+                completed, loss = done
+                results.append(Result(r.job_id, r.step, r.arrival, issued, completed - t0, loss))
+                scheduler.complete(r.job_id, executor.unload)
+                del inflight[slot]
+                free_slots.append(slot)
+        if scheduler.all_finished() and not inflight:
+            break
+        if ri >= len(reqs) and not inflight and not scheduler.pending:
+            break  # nothing can arrive or complete any more (e.g. a job is still waiting forever)
+        if poll_sleep:
+            time.sleep(poll_sleep)
+    return results
+
+# ----------------------------------------------------------------------------
+# GPU executor
+# ----------------------------------------------------------------------------
+
+
+def job_footprint(n, sh_degree, width, height, keys_per_gaussian=16):
+    """Device bytes of one admitted job: raw params, gradients and two Adam
+    moments (4 x 59 floats per Gaussian at SH degree 3), activated scale and
+    opacity, the view buffers (2D records, gradient records, radius, bins and
+    binning scratch sized for ``keys_per_gaussian`` keys per Gaussian),
+    images, loss gradient and target."""
+    k = 1 if sh_degree < 0 else (sh_degree + 1) ** 2
+    per = 3 + 3 + 4 + 1 + 3 * k
+    params = 4 * per * 4 * n
+    act = 16 * n + 16 * n
+    keys = keys_per_gaussian * n
+    view = 48 * n + 48 * n + 4 * n + 4 * keys + (20 * keys + 4 * n + (8 << 20))
+    img = 4 * width * height * (3 * 3 + 2)
+    return params + act + view + img
+
+
+class GpuExecutor:
+    """Runs job steps on CUDA streams through libgsr."""
+
+    def __init__(self, device, slots, opts, lr=1e-3, bg=(0.0, 0.0, 0.0)):
+        import torch
+
+        from . import gsr, pipeline
+        self.torch, self.gsr, self.pipeline = torch, gsr, pipeline
+        self.device = device
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+        self.opts = opts
+        self.lr = lr
+        self.bg = bg
+        self.t0_event = torch.cuda.Event(enable_timing=True)
+        self.t0_event.record()
+        self.t0_host = time.perf_counter()
+        self.loaded = {}
+        self.loss_log = {}
+
+    def now(self):
+        return time.perf_counter() - self.t0_host
+
+    # job state on the device ------------------------------------------------
+    def load(self, job):
+        torch = self.torch
+        scene, cam, targets = job.payload
+        n = scene.n
+        k = scene.feat.reshape(n, -1).shape[1]
+        sizes = [3 * n, 3 * n, 4 * n, n, k * n]
+        # every segment starts on a 16-byte boundary (vector loads of the features)
+        padded = [(x + 3) // 4 * 4 for x in sizes]
+        P = torch.zeros(sum(padded), dtype=torch.float32, device=self.device)
+        offs = np.cumsum([0] + padded)
+        views = [P[offs[i]:offs[i] + sizes[i]] for i in range(5)]
+        views[0].copy_(torch.from_numpy(scene.mean.reshape(-1)))
+        views[1].copy_(torch.from_numpy(np.log(scene.scale.astype(np.float64)).astype(np.float32).reshape(-1)))
+        views[2].copy_(torch.from_numpy(scene.quat.reshape(-1)))
+        o = scene.opacity.astype(np.float64)
+        views[3].copy_(torch.from_numpy((np.log(o) - np.log1p(-o)).astype(np.float32)))
+        views[4].copy_(torch.from_numpy(scene.feat.reshape(-1)))
+        G = torch.zeros_like(P)
+        gv = [G[offs[i]:offs[i] + sizes[i]] for i in range(5)]
+        st = dict(P=P, G=G, M=torch.zeros_like(P), V=torch.zeros_like(P), pv=views, gv=gv, n=n,
+                  sh=scene.sh_degree, scale=torch.empty(3 * n, device=self.device),
+                  opac=torch.empty(n, device=self.device), dscale=torch.empty(3 * n, device=self.device),
+                  dopac=torch.empty(n, device=self.device),
+                  vb=self.pipeline.ViewBuffers(n, cam, self.device, 16 * n),
+                  targets=[torch.from_numpy(t).to(self.device) for t in targets],
+                  loss=torch.zeros(1, device=self.device),
+                  loss_host=torch.zeros(1).pin_memory(), adam_step=0)
+        st["dimg"] = torch.empty_like(st["vb"].image)
+        torch.cuda.synchronize(self.device)
+        self.loaded[job.job_id] = st
+
+    def unload(self, job):
+        st = self.loaded.pop(job.job_id, None)
+        if st is not None:
+            self.final_params = getattr(self, "final_params", {})
+            self.final_params[job.job_id] = st["P"].detach().cpu().numpy()
+
+    def issue(self, slot, job, step):
+        torch, gsr = self.torch, self.gsr
+        st = self.loaded[job.job_id]
+        s = self.streams[slot]
+        n = st["n"]
+        pv, gv, vb = st["pv"], st["gv"], st["vb"]
+        with torch.cuda.stream(s):
+            gsr.gsr_activate(n, pv[1], pv[3], st["scale"], st["opac"], s)
+            sc = self.pipeline.SceneTensors(pv[0], st["scale"], pv[2], st["opac"], pv[4], st["sh"])
+            vb.preprocess(sc, zero_grad=True, stream=s)
+            vb.bin(s)
+            vb.forward(self.bg, s)
+            st["loss"].zero_()
+            tgt = st["targets"][step % len(st["targets"])]
+            gsr.gsr_l1_loss(vb.image.numel(), vb.image, tgt, st["dimg"], st["loss"], s)
+            vb.backward(self.bg, st["dimg"], self.opts, s)
+            st["G"].zero_()
+            st["dscale"].zero_()
+            st["dopac"].zero_()
+            grads = self.pipeline.SceneTensors(gv[0], st["dscale"], gv[2], st["dopac"], gv[4], st["sh"])
+            vb.backward_project(sc, grads, s)
+            gsr.gsr_activate_backward(n, st["scale"], st["opac"], st["dscale"], st["dopac"], gv[1], gv[3], s)
+            st["adam_step"] += 1
+            gsr.gsr_adam_step(st["P"].numel(), st["P"], st["G"], st["M"], st["V"], self.lr, 0.9, 0.999, 1e-8,
+                              st["adam_step"], s)
+            st["loss_host"].copy_(st["loss"], non_blocking=True)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(s)
+        return (ev, st, job.job_id, step)
+
+    def poll(self, h):
+        ev, st, jid, step = h
+        if not ev.query():
+            return None
+        completed = self.t0_event.elapsed_time(ev) / 1e3
+        loss = float(st["loss_host"][0])
+        self.loss_log.setdefault(jid, []).append(loss)
+        return completed + 0.0, loss
+
+
+def make_jobs(spec, seed=0):
+    """``spec``: list of (n, steps, arrival_s, width, height)."""
+    from . import scenes as S
+    jobs = []
+    for i, (n, steps, arrival, w, h) in enumerate(spec):
+        scene = S.gmm_scene(seed + 101 * i, n, 64, (-4.5, 0.7), 3)
+        rng = np.random.default_rng(seed + 7 * i)
+        cams = S.sphere_cameras(rng, 1, (0.0, 0.0, 0.0), 4.0, [(w, h)])
+        targets = [S.target_image(seed + i, w, h)]
+        jobs.append(Job(i, n, steps, arrival, job_footprint(n, 3, w, h), payload=(scene, cams[0], targets)))
+    return jobs
+
+
+def run_serving(spec, slots, budget_bytes, opts, rate_per_job, seed=0, device="cuda", jobs=None):
+    ex = GpuExecutor(device, slots, opts)
+    jobs = jobs if jobs is not None else make_jobs(spec, seed)
+    for j in jobs:
+        j.state, j.done_steps, j.busy = "waiting", 0, False
+    sch = Scheduler(budget_bytes, slots)
+    for j in jobs:
+        sch.add_job(j)
+    reqs = poisson_requests(jobs, rate_per_job, seed + 999)
+    wall0 = time.perf_counter()
+    res = serve(sch, reqs, ex)
+    wall = time.perf_counter() - wall0
+    return res, summarize(res, wall), ex, sch
+
+
+def main():
+    import argparse
+
+    import torch
+
+    from . import gsr
+    ap = argparse.ArgumentParser(description="serving benchmark: 16 concurrent scene-fitting jobs")
+    ap.add_argument("--jobs", type=int, default=16)
+    ap.add_argument("--steps", type=int, default=12)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--budget-gb", type=float, default=24.0)
+    ap.add_argument("--rate", type=float, default=20.0, help="step requests per second per job")
+    ap.add_argument("--min-n", type=int, default=100_000)
+    ap.add_argument("--max-n", type=int, default=2_000_000)
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args()
+    rng = np.random.default_rng(args.seed)
+    ns = np.exp(rng.uniform(math.log(args.min_n), math.log(args.max_n), size=args.jobs)).astype(int)
+    arrivals = np.cumsum(rng.exponential(0.05, size=args.jobs))
+    res_list = [(1297, 840), (1920, 1080)]
+    spec = [(int(ns[i]), args.steps, float(arrivals[i]), *res_list[i % 2]) for i in range(args.jobs)]
+    jobs = make_jobs(spec, args.seed)
+    budget = int(args.budget_gb * (1 << 30))
+    _, cont, _, sch = run_serving(spec, args.slots, budget, gsr.backward_opts("hybrid", 12, 1), args.rate,
+                                  args.seed, jobs=jobs)
+    torch.cuda.synchronize()
+    one_budget = max(j.footprint for j in jobs)
+    _, seq, _, _ = run_serving(spec, 1, one_budget, gsr.backward_opts("plain", 0, 1), args.rate, args.seed,
+                               jobs=jobs)
+    print(json.dumps({"workload": f"{args.jobs} jobs, N log-uniform {args.min_n}-{args.max_n}, SH3, "
+                                  f"1297x840 / 1920x1080, {args.steps} steps each, Poisson {args.rate}/s per job",
+                      "continuous_batching_hybrid": dict(cont, slots=args.slots, budget_gb=args.budget_gb,
+                                                         peak_admitted_gb=sch.peak_used / (1 << 30)),
+                      "one_at_a_time_plain": seq}))
+
+
+if __name__ == "__main__":
+    main()

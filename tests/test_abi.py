@@ -62,6 +62,11 @@ def test_argument_errors_are_reported_before_any_launch(lib):
     opts = gsr.backward_opts("warp", store_T=True)
     assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, None, None, p, p, ctypes.byref(opts), None) == gsr.GSR_EINVAL
     assert lib.gsr_backward(32, 32, 12, 16, p, p, p, bg, p, p, p, p, None, None) == gsr.GSR_EINVAL
+    # records must be 16-byte aligned, ranges 8-byte aligned
+    p8 = ctypes.c_void_p(24)
+    assert lib.gsr_backward(32, 32, 16, 16, p, p, p8, bg, p, p, p, p, None, None) == gsr.GSR_EINVAL
+    assert lib.gsr_backward(32, 32, 16, 16, ctypes.c_void_p(20), p, p, bg, p, p, p, p, None, None) == gsr.GSR_EINVAL
+    assert lib.gsr_forward(32, 32, 16, 16, p, p, p8, bg, p, None, None, None) == gsr.GSR_EINVAL
     cam = gsr.Camera()
     assert lib.gsr_preprocess(10, 4, p, p, p, p, p, ctypes.byref(cam), 16, 16, p, p, None, None) == gsr.GSR_EINVAL
     out = ctypes.c_size_t(0)

@@ -346,3 +346,33 @@ def test_invalid_arguments_raise(dev):
         gsr.gsr_forward(32, 32, 16, 8, x, x, x, (0, 0, 0), x)
     with pytest.raises(gsr.GsrError, match="invalid"):
         gsr.gsr_preprocess(4, 5, x, x, x, x, x, cam, 16, 16, x, x)
+
+
+def test_unaligned_features_take_the_scalar_path(dev):
+    """Feature arrays that start off a 16-byte boundary (e.g. a segment of a
+    packed parameter buffer) give the same projection and backward
+    projection as aligned ones."""
+    scene = S.gmm_scene(9, 1001, 8, (-3.3, 0.4), 3)
+    cam = S.front_camera(96, 80)
+    n = scene.n
+    feat = scene.feat.reshape(n, -1)
+    buf = torch.zeros(feat.size + 1, device=dev)
+    buf[1:] = torch.from_numpy(feat.reshape(-1)).to(dev)
+    unaligned = buf[1:]
+    assert unaligned.data_ptr() % 16 != 0
+    outs = []
+    for f in (T(feat), unaligned):
+        splat = torch.zeros((n, 12), device=dev)
+        radius = torch.zeros(n, dtype=torch.int32, device=dev)
+        gsr.gsr_preprocess(n, 3, T(scene.mean), T(scene.scale), T(scene.quat), T(scene.opacity), f, cam, 16, 16,
+                           splat, radius)
+        g12 = torch.ones((n, 12), device=dev)
+        dbuf = torch.zeros(feat.size + 1, device=dev)
+        df = dbuf[1:] if f is unaligned else torch.zeros(feat.size, device=dev)
+        z = lambda c: torch.zeros((n, c), device=dev)
+        dm, ds, dq, do = z(3), z(3), z(4), torch.zeros(n, device=dev)
+        gsr.gsr_backward_project(n, 3, T(scene.mean), T(scene.scale), T(scene.quat), T(scene.opacity), f, cam,
+                                 radius, g12, dm, ds, dq, do, df)
+        outs.append((N(splat), N(radius), N(df), N(dm)))
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
