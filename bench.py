@@ -267,11 +267,6 @@ def run_ours(args):
     # first pass (untimed): sizes, statistics of the traversal
     R.step(sc, target, bg, grads)
     torch.cuda.synchronize()
-    hist = torch.zeros(36, dtype=torch.int64, device=dev)
-    gsr.gsr_backward_stats(vb.W, vb.H, 16, 16, vb.tile_ranges, vb.point_list, vb.splat2d, vb.n_contrib, hist)
-    h = hist.cpu().numpy().astype(np.int64)
-    p_active, p_exam, warp_steps = int(h[33]), int(h[34]), int(h[35])
-    units = 9 * p_active
 
     # plain atomicAdd vs reduced tiers, backward kernel alone (untimed for the step)
     if args.profile:
@@ -283,6 +278,13 @@ def run_ours(args):
         tune_table = tr.table
     R.opts = best
     best_name = autotune.opts_name(best)
+    hist = torch.zeros(38, dtype=torch.int64, device=dev)
+    gsr.gsr_backward_stats(vb.W, vb.H, 16, 16, vb.tile_ranges, vb.point_list, vb.splat2d, vb.n_contrib, hist,
+                           int(best.lane_layout))
+    h = hist.cpu().numpy().astype(np.int64)
+    p_active, p_exam, warp_steps = int(h[33]), int(h[34]), int(h[35])
+    culled_in, culled_in_idle = int(h[36]), int(h[37])
+    units = 9 * p_active
 
     def step_once(on_backward=None):
         grads.mean.zero_(); grads.scale.zero_(); grads.quat.zero_(); grads.opacity.zero_(); grads.feat.zero_()
@@ -435,7 +437,9 @@ def run_ours(args):
             },
             "l2_red_adds_per_s": red,
             "traffic_counts": {"P_active": p_active, "P_examined": p_exam, "P_ts": vb.n_keys,
-                               "warp_steps": warp_steps, "active_lane_hist": h[:33].tolist()},
+                               "warp_steps": warp_steps, "warp_steps_after_cull": culled_in,
+                               "warp_steps_after_cull_without_active_lane": culled_in_idle,
+                               "active_lane_hist": h[:33].tolist()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4,
                     "ms_per_step": e2e_tot / args.steps},
             "clocks": clk,

@@ -270,13 +270,15 @@ int gsr_backward_batched(int32_t n_views, const gsr_view* views, const uint32_t*
 
 /*
  * Traversal statistics of gsr_backward (nothing else is written): walks the
- * same lists as the backward with the same skip tests and fills the HOST-
- * visible-after-copy device array hist[36] (uint64, zeroed first):
+ * same lists as the backward with the same skip tests and fills the
+ * device array hist[38] (uint64, zeroed first):
  *   hist[k], k = 0..32: number of (warp, splat) steps with k active lanes --
  *     the active-threads-per-warp histogram of Sec. III-B, Observation 2;
  *   hist[33]: active (pixel, splat) pairs (each adds 9 gradient values);
  *   hist[34]: examined pairs (sum of n_contrib);
- *   hist[35]: warp steps taken.
+ *   hist[35]: warp steps taken;
+ *   hist[36]: warp steps that pass the kernels' per-warp footprint cull;
+ *   hist[37]: of those, steps with no active lane.
  * lane_layout as in gsr_backward_opts.  n_contrib from gsr_forward.
  */
 int gsr_backward_stats(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,

@@ -109,6 +109,118 @@ __global__ void ranges_kernel(long long nkeys, const uint64_t* __restrict__ keys
     if (k == nkeys - 1 || (uint32_t)(keys[k + 1] >> 32) != t) ranges[2 * (size_t)t + 1] = (uint32_t)(k + 1);
 }
 
+// ---- two-stage binning: depth order first, then a short tile-id sort -----
+// Sorting the Gaussians once by depth (stable, so equal depths keep id order)
+// and emitting their tile entries in that order leaves only the tile id to
+// sort: a stable radix sort over ceil(log2(tiles)) bits gives exactly the
+// order of the (tile << 32 | depth) sort with id tie-break, in 2 passes over
+// the duplicated entries instead of 6.
+struct Scratch2 {
+    uint32_t *dkeys_in, *dkeys_out, *ids_in, *order, *counts;
+    uint32_t *tkeys_in, *tkeys_out, *vals_in;
+    void* cub_tmp;
+    size_t cub_bytes, total;
+};
+
+int layout2(int n, long long cap, int tile_bits, char* base, Scratch2& s) {
+    size_t a = 0, b = 0, c = 0;
+    const int nn = n > 0 ? n : 1;
+    const int cc = (int)(cap > 0 ? cap : 1);
+    cudaError_t e = cub::DeviceRadixSort::SortPairs(nullptr, a, (uint32_t*)nullptr, (uint32_t*)nullptr,
+                                                    (uint32_t*)nullptr, (uint32_t*)nullptr, nn, 0, 32);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cub::DeviceScan::ExclusiveSum(nullptr, b, (uint32_t*)nullptr, (uint32_t*)nullptr, nn + 1);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cub::DeviceRadixSort::SortPairs(nullptr, c, (uint32_t*)nullptr, (uint32_t*)nullptr, (uint32_t*)nullptr,
+                                        (uint32_t*)nullptr, cc, 0, tile_bits);
+    if (e != cudaSuccess) return cuda_fail(e);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return base ? base + o : nullptr; };
+    const size_t vn = sizeof(uint32_t) * (size_t)nn, vc = sizeof(uint32_t) * (size_t)cc;
+    s.dkeys_in = (uint32_t*)take(vn);
+    s.dkeys_out = (uint32_t*)take(vn);
+    s.ids_in = (uint32_t*)take(vn);
+    s.order = (uint32_t*)take(vn);
+    s.counts = (uint32_t*)take(sizeof(uint32_t) * ((size_t)nn + 1));
+    s.tkeys_in = (uint32_t*)take(vc);
+    s.tkeys_out = (uint32_t*)take(vc);
+    s.vals_in = (uint32_t*)take(vc);
+    s.cub_bytes = a > b ? (a > c ? a : c) : (b > c ? b : c);
+    s.cub_tmp = take(s.cub_bytes);
+    s.total = off;
+    return GSR_OK;
+}
+
+int tile_bits_of(const BinGeom& g) {
+    int bits = 1;
+    while ((1ll << bits) < (long long)g.tiles) ++bits;
+    return bits;
+}
+
+__global__ void depth_keys_kernel(int n, const float* __restrict__ splat2d, const int* __restrict__ radius,
+                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ ids) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = radius[i] > 0 ? __float_as_uint(splat2d[(size_t)i * GSR_REC + 9]) : 0xffffffffu;
+    ids[i] = (uint32_t)i;
+}
+
+__global__ void count_sorted_kernel(int n, const float* __restrict__ splat2d, const int* __restrict__ radius,
+                                    const uint32_t* __restrict__ order, BinGeom g, uint32_t* __restrict__ counts) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > n) return;
+    uint32_t c = 0;
+    if (j < n) {
+        const uint32_t i = order[j];
+        const int r = radius[i];
+        if (r > 0) {
+            float2 uv = *reinterpret_cast<const float2*>(splat2d + (size_t)i * GSR_REC);
+            int x0, x1, y0, y1;
+            tile_rect(uv.x, uv.y, r, g.gx, g.gy, g.twl, g.thl, x0, x1, y0, y1);
+            const int nt = (x1 - x0) * (y1 - y0);
+            c = nt > 0 ? (uint32_t)nt : 0u;
+        }
+    }
+    counts[j] = c;
+}
+
+__global__ void duplicate_sorted_kernel(int n, const float* __restrict__ splat2d, const int* __restrict__ radius,
+                                        const uint32_t* __restrict__ order, BinGeom g,
+                                        const uint32_t* __restrict__ offsets, uint32_t* __restrict__ tkeys,
+                                        uint32_t* __restrict__ vals) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t i = order[j];
+    const int r = radius[i];
+    if (r <= 0) return;
+    float2 uv = *reinterpret_cast<const float2*>(splat2d + (size_t)i * GSR_REC);
+    int x0, x1, y0, y1;
+    tile_rect(uv.x, uv.y, r, g.gx, g.gy, g.twl, g.thl, x0, x1, y0, y1);
+    uint32_t o = offsets[j];
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) {
+            tkeys[o] = (uint32_t)(y * g.gx + x);
+            vals[o] = i;
+            ++o;
+        }
+}
+
+__global__ void ranges_tile_kernel(long long nkeys, const uint32_t* __restrict__ tkeys, uint32_t* __restrict__ ranges) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkeys) return;
+    const uint32_t t = tkeys[k];
+    if (k == 0 || tkeys[k - 1] != t) ranges[2 * (size_t)t] = (uint32_t)k;
+    if (k == nkeys - 1 || tkeys[k + 1] != t) ranges[2 * (size_t)t + 1] = (uint32_t)(k + 1);
+}
+
+__global__ void full_keys_kernel(long long nkeys, const uint32_t* __restrict__ tkeys,
+                                 const uint32_t* __restrict__ point_list, const float* __restrict__ splat2d,
+                                 uint64_t* __restrict__ keys) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkeys) return;
+    keys[k] = ((uint64_t)tkeys[k] << 32) | (uint64_t)__float_as_uint(splat2d[(size_t)point_list[k] * GSR_REC + 9]);
+}
+
 }  // namespace
 }  // namespace gsr
 
@@ -120,8 +232,8 @@ extern "C" int gsr_bin_scratch_bytes(int32_t n, int32_t width, int32_t height, i
     if (n < 0 || key_capacity < 0 || key_capacity >= 0xffffffffll || !bytes ||
         !make_geom(width, height, tile_w, tile_h, g))
         return GSR_EINVAL;
-    Scratch s;
-    int rc = layout(n, key_capacity, nullptr, s);
+    Scratch2 s;
+    int rc = layout2(n, key_capacity, tile_bits_of(g), nullptr, s);
     if (rc != GSR_OK) return rc;
     *bytes = s.total;
     return GSR_OK;
@@ -140,17 +252,25 @@ extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t ti
         return GSR_EINVAL;
     if (!aligned16(splat2d) || !aligned16(scratch) || (keys_out && !aligned8(keys_out))) return GSR_EINVAL;
     cudaStream_t stream = (cudaStream_t)stream_;
-    Scratch s;
-    int rc = layout(n, key_capacity, (char*)scratch, s);
+    const int tbits = tile_bits_of(g);
+    Scratch2 s;
+    int rc = layout2(n, key_capacity, tbits, (char*)scratch, s);
     if (rc != GSR_OK) return rc;
     if (scratch_bytes < s.total) return GSR_ESCRATCH;
     cudaError_t e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)g.tiles, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     *n_keys = 0;
     if (n == 0) return GSR_OK;
-    count_kernel<<<(n + 1 + 255) / 256, 256, 0, stream>>>(n, splat2d, radius, g, s.counts);
+    // 1. Gaussians in (depth, id) order
+    depth_keys_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, splat2d, radius, s.dkeys_in, s.ids_in);
     if ((rc = check_launch()) != GSR_OK) return rc;
     size_t tb = s.cub_bytes;
+    e = cub::DeviceRadixSort::SortPairs(s.cub_tmp, tb, s.dkeys_in, s.dkeys_out, s.ids_in, s.order, n, 0, 32, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    // 2. tiles touched, in that order, and their offsets
+    count_sorted_kernel<<<(n + 1 + 255) / 256, 256, 0, stream>>>(n, splat2d, radius, s.order, g, s.counts);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    tb = s.cub_bytes;
     e = cub::DeviceScan::ExclusiveSum(s.cub_tmp, tb, s.counts, s.counts, n + 1, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     uint32_t total = 0;
@@ -161,20 +281,27 @@ extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t ti
     *n_keys = (int64_t)total;
     if ((long long)total > key_capacity) return GSR_ECAPACITY;
     if (total == 0) return GSR_OK;
-    duplicate_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, splat2d, radius, g, s.counts, s.keys_in, s.vals_in);
+    // 3. entries emitted in depth order, then a stable sort on the tile id
+    duplicate_sorted_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, splat2d, radius, s.order, g, s.counts,
+                                                                 s.tkeys_in, s.vals_in);
     if ((rc = check_launch()) != GSR_OK) return rc;
-    uint64_t* sorted_keys = keys_out ? keys_out : s.keys_out;
     tb = 0;
-    e = cub::DeviceRadixSort::SortPairs(nullptr, tb, s.keys_in, sorted_keys, s.vals_in, point_list,
-                                        (int)total, 0, g.end_bit, stream);
+    e = cub::DeviceRadixSort::SortPairs(nullptr, tb, s.tkeys_in, s.tkeys_out, s.vals_in, point_list, (int)total, 0,
+                                        tbits, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     if (tb > s.cub_bytes) return GSR_ESCRATCH;
     tb = s.cub_bytes;
-    e = cub::DeviceRadixSort::SortPairs(s.cub_tmp, tb, s.keys_in, sorted_keys, s.vals_in, point_list,
-                                        (int)total, 0, g.end_bit, stream);
+    e = cub::DeviceRadixSort::SortPairs(s.cub_tmp, tb, s.tkeys_in, s.tkeys_out, s.vals_in, point_list, (int)total,
+                                        0, tbits, stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    ranges_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>((long long)total, sorted_keys, tile_ranges);
-    return check_launch();
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    ranges_tile_kernel<<<blocks, 256, 0, stream>>>((long long)total, s.tkeys_out, tile_ranges);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    if (keys_out) {
+        full_keys_kernel<<<blocks, 256, 0, stream>>>((long long)total, s.tkeys_out, point_list, splat2d, keys_out);
+        if ((rc = check_launch()) != GSR_OK) return rc;
+    }
+    return GSR_OK;
 }
 
 // ----------------------------------------------------------------------------

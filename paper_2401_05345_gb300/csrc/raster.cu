@@ -380,17 +380,20 @@ backward_batched_kernel(const gsr_view* __restrict__ views, const uint32_t* __re
 // Counts of the backward traversal (no gradients written): per (warp, splat)
 // step the number of active lanes -> hist[0..32]; hist[33] = active pairs,
 // hist[34] = examined pairs (sum of n_contrib), hist[35] = warp steps with at
-// least one lane still walking.  The histogram is the active-lanes-per-warp
-// measurement of Sec. III-B (Observation 2).
+// least one lane still walking, hist[36] = those steps that pass the per-warp
+// footprint cull, hist[37] = culled-in steps without any active lane.  The
+// histogram is the active-lanes-per-warp measurement of Sec. III-B
+// (Observation 2).
 template <int TW, int TH, int LAYOUT>
 __global__ void __launch_bounds__(TW* TH)
 stats_kernel(BwdArgs p, unsigned long long* __restrict__ hist) {
     constexpr int B = TW * TH;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
-    __shared__ unsigned long long s_h[36];
+    __shared__ unsigned long long s_h[38];
+    __shared__ unsigned s_mask[B];
     __shared__ int s_maxlast;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
     const int tx = tile % p.g.gx, ty = tile / p.g.gx;
     int lx, ly;
@@ -401,7 +404,7 @@ stats_kernel(BwdArgs p, unsigned long long* __restrict__ hist) {
     const int nlist = (int)(rg.y - rg.x);
     const size_t pix = (size_t)py * p.g.W + px;
     const int last = inside ? min(max(p.n_contrib[pix], 0), nlist) : 0;
-    for (int i = tid; i < 36; i += B) s_h[i] = 0ull;
+    for (int i = tid; i < 38; i += B) s_h[i] = 0ull;
     if (tid == 0) s_maxlast = 0;
     __syncthreads();
     const int wlast = __reduce_max_sync(kFull, last);
@@ -416,8 +419,10 @@ stats_kernel(BwdArgs p, unsigned long long* __restrict__ hist) {
         if (tid < cnt) {
             uint32_t id = p.point_list[rg.x + (uint32_t)(top - 1 - tid)];
             const float4* rec = reinterpret_cast<const float4*>(p.splat2d + (size_t)id * GSR_REC);
-            s_a[tid] = rec[0];
-            s_b[tid] = rec[1];
+            const float4 a = rec[0], b = rec[1];
+            s_a[tid] = a;
+            s_b[tid] = b;
+            s_mask[tid] = warp_cull_mask<TW, TH, LAYOUT>(a.x, a.y, a.z, a.w, b.x, b.y, tx * TW, ty * TH);
         }
         __syncthreads();
         for (int k = 0; k < cnt; ++k) {
@@ -431,12 +436,16 @@ stats_kernel(BwdArgs p, unsigned long long* __restrict__ hist) {
             if (lane == 0) {
                 atomicAdd(&s_h[__popc(m)], 1ull);
                 atomicAdd(&s_h[35], 1ull);
+                if ((s_mask[k] >> warp) & 1u) {
+                    atomicAdd(&s_h[36], 1ull);
+                    if (m == 0u) atomicAdd(&s_h[37], 1ull);
+                }
             }
         }
     }
     atomicAdd(&s_h[33], active_pairs);
     __syncthreads();
-    for (int i = tid; i < 36; i += B)
+    for (int i = tid; i < 38; i += B)
         if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
 }
 
@@ -573,7 +582,7 @@ extern "C" int gsr_backward_stats(int32_t width, int32_t height, int32_t tile_w,
     a.splat2d = splat2d;
     a.n_contrib = n_contrib;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(hist, 0, 36 * sizeof(uint64_t), s);
+    cudaError_t e = cudaMemsetAsync(hist, 0, 38 * sizeof(uint64_t), s);
     if (e != cudaSuccess) return cuda_fail(e);
     const int tiles = a.g.gx * a.g.gy;
     if (lane_layout == 0) stats_kernel<16, 16, 0><<<tiles, 256, 0, s>>>(a, (unsigned long long*)hist);

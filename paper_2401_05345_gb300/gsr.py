@@ -199,7 +199,7 @@ def gsr_backward(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d
 
 def gsr_backward_stats(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, n_contrib, hist,
                        lane_layout=0, stream=None):
-    """hist: int64 tensor [36] (uint64 counts, see include/gsr.h)."""
+    """hist: int64 tensor [38] (uint64 counts, see include/gsr.h)."""
     _check("gsr_backward_stats", lib().gsr_backward_stats(width, height, tile_w, tile_h, _ptr(tile_ranges),
                                                           _ptr(point_list), _ptr(splat2d), _ptr(n_contrib),
                                                           lane_layout, _ptr(hist), _stream(stream)))

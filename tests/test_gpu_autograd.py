@@ -7,10 +7,11 @@
   to 1e-5 in isolation (test_gpu_parity); end to end the FP32 rounding of the
   projection feeds the blend, so this check is held to 1e-3 of the same
   scales: a wiring check (argument order, activations, zeroing).
-* Central differences (eps 1e-3 relative, FP32 forward, loss summed in FP64)
-  against the analytic gradient: the spread between the quotients at eps and
-  eps/2 measures the FD's own FP32 noise and the analytic value must lie in
-  that band (plus 1 %).
+* Central differences (eps 1e-3, an absolute step as in torch's gradcheck;
+  FP32 forward, loss summed in FP64) against the analytic gradient: the
+  spread between the quotients at eps and eps/2 measures the FD's own FP32
+  noise and the analytic value must lie in that band (plus 1 %); steps that
+  cross a discrete decision of the forward are skipped.
 * T stored vs recomputed: same image bit for bit, same gradients up to the
   float summation order of the accumulation, 8 bytes per pixel less kept
   between passes.
@@ -112,15 +113,16 @@ def _decisions(model, cam, dev):
         vb.preprocess(sc)
         vb.bin()
         vb.forward((0.1, 0.2, 0.3))
-        hist = torch.zeros(36, dtype=torch.int64, device=dev)
+        hist = torch.zeros(38, dtype=torch.int64, device=dev)
         gsr.gsr_backward_stats(vb.W, vb.H, 16, 16, vb.tile_ranges, vb.point_list, vb.splat2d, vb.n_contrib, hist)
         return (vb.point_list[:vb.n_keys].cpu().numpy().tobytes(), vb.tile_ranges.cpu().numpy().tobytes(),
                 vb.n_contrib.cpu().numpy().tobytes(), int(hist[33]))
 
 
 def test_autograd_central_differences(dev, orc):
-    """Central differences of the FP32 forward at eps = 1e-3 (relative) and at
-    eps/2; their spread measures the FD's own FP32 noise, and the analytic
+    """Central differences of the FP32 forward at eps = 1e-3 (absolute, as in
+    gradcheck) and at eps/2; their spread measures the FD's own FP32 noise,
+    and the analytic
     gradient must lie within that band (plus 1 %).  Parameters of visible
     Gaussians only.  Steps in which a discrete decision of the forward
     changes (list order, last contributor, active pairs) are not derivatives
@@ -144,8 +146,7 @@ def test_autograd_central_differences(dev, orc):
                 idx = int(gi) * per + int(rng.integers(per))
                 x0 = float(flat[idx])
                 fds, crossed = [], False
-                for eps in (1e-3, 5e-4):
-                    h = eps * max(abs(x0), 1e-2)
+                for h in (1e-3, 5e-4):
                     flat[idx] = x0 + h
                     lp = float((model(st).double() * w).sum())
                     crossed |= _decisions(model, cam, dev) != base
@@ -162,7 +163,9 @@ def test_autograd_central_differences(dev, orc):
                 checked += 1
                 if band < 0.05 * abs(an):
                     informative += 1
-                assert abs(fds[0] - an) <= 2 * band + 1e-2 * abs(an) + 1e-4 * gmax, (name, idx, fds, an)
+                # entries below the FP32 forward's difference resolution (2e-3 of
+                # the group's largest gradient) are only held to that floor
+                assert abs(fds[0] - an) <= 2 * band + 1e-2 * abs(an) + 2e-3 * gmax, (name, idx, fds, an)
     assert informative >= 25, (informative, checked, crossings)
 
 
