@@ -270,7 +270,7 @@ def run_ours(args):
 
     # plain atomicAdd vs reduced tiers, backward kernel alone (untimed for the step)
     if args.profile:
-        best = gsr.backward_opts("hybrid", 8, 1)
+        best = gsr.backward_opts("hybrid", 12, 1, True, 2)
         tune_table, t_plain = {}, None
     else:
         tr = autotune.tune(vb, bg, R.dimg, reps=3, flush=flush)
@@ -327,17 +327,17 @@ def run_ours(args):
 
     # backward kernel alone: plain atomicAdd vs the reduced tiers
     reps = 10
-    t_plain = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("plain", 0, best.lane_layout), reps, flush)
-    t_warp = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("warp", 0, best.lane_layout), reps, flush)
+    lay, ppt = int(best.lane_layout), max(1, int(best.pixels_per_thread))
+    t_plain = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("plain", 0, lay), reps, flush)
+    t_warp = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("warp", 0, lay, True, ppt), reps, flush)
     t_best = autotune.time_backward(vb, bg, R.dimg, best, reps, flush)
-    t_block = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("block", 0, best.lane_layout), reps, flush)
+    t_block = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("block", 0, lay, True, ppt), reps, flush)
     t_recompute = autotune.time_backward(
-        vb, bg, R.dimg, gsr.backward_opts(int(best.reduce_mode), int(best.threshold), int(best.lane_layout), False),
-        reps, flush)
+        vb, bg, R.dimg, gsr.backward_opts(int(best.reduce_mode), int(best.threshold), lay, False, ppt), reps, flush)
     sweep = {}
     for thr in (4, 8, 12, 16, 20, 24, 28, 32):
         sweep[str(thr)] = autotune.time_backward(
-            vb, bg, R.dimg, gsr.backward_opts("hybrid", thr, best.lane_layout), 5, flush)
+            vb, bg, R.dimg, gsr.backward_opts("hybrid", thr, lay, True, ppt), 5, flush)
 
     # L2 atomic (red) throughput: the plain tier's roofline
     red_buf = torch.zeros(12 * 1_000_000, dtype=torch.float32, device=dev)

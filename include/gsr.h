@@ -89,7 +89,8 @@ enum {
 };
 
 /* lane_layout: which pixels of a 16x16 tile share a warp.
- *   0: 16 x 2 rows,  1: 8 x 4 block. */
+ *   0: rows (16 x 2, or 16 x 4 with two pixels per thread),
+ *   1: blocks (8 x 4, or 8 x 8 with two pixels per thread). */
 typedef struct gsr_backward_opts {
     int32_t reduce_mode;   /* GSR_REDUCE_* */
     int32_t threshold;     /* 0..33, see above */
@@ -97,7 +98,10 @@ typedef struct gsr_backward_opts {
     int32_t store_T;       /* 1: read final_T / n_contrib written by
                               gsr_forward; 0: recompute them in the kernel
                               (final_T / n_contrib may be NULL) */
-    int32_t reserved[4];   /* must be zero */
+    int32_t pixels_per_thread; /* 1 (8 warps per tile) or 2 (4 warps; each
+                              lane first sums its two pixels' gradients);
+                              0 means 1.  PLAIN requires 1. */
+    int32_t reserved[3];   /* must be zero */
 } gsr_backward_opts;
 
 /* One view of a batched backward (an array of these lives in DEVICE memory).

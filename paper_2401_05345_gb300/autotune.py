@@ -20,23 +20,27 @@ L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
 
 
 def default_candidates(store_T=True):
+    """Tier x threshold x pixel-to-lane layout x pixels per thread (1: 8 warps
+    per 16x16 tile, 2: 4 warps)."""
     c = []
-    for lay in (0, 1):
-        c.append(("warp", 0, lay))
-        for thr in (4, 8, 12, 16, 20, 24, 28, 32):
-            c.append(("hybrid", thr, lay))
-        for thr in (0, 4, 8, 16):
-            c.append(("block", thr, lay))
-    return [gsr.backward_opts(m, t, l, store_T) for (m, t, l) in c]
+    for ppt in (1, 2):
+        for lay in (0, 1):
+            c.append(("warp", 0, lay, ppt))
+            for thr in (4, 8, 12, 16, 20, 24, 28, 32):
+                c.append(("hybrid", thr, lay, ppt))
+            for thr in (0, 4, 8, 16):
+                c.append(("block", thr, lay, ppt))
+    return [gsr.backward_opts(m, t, l, store_T, p) for (m, t, l, p) in c]
 
 
 def opts_key(o) -> tuple:
-    return (int(o.reduce_mode), int(o.threshold), int(o.lane_layout), int(o.store_T))
+    return (int(o.reduce_mode), int(o.threshold), int(o.lane_layout), int(o.store_T),
+            max(1, int(o.pixels_per_thread)))
 
 
 def opts_name(o) -> str:
     inv = {v: k for k, v in gsr.REDUCE_NAMES.items()}
-    return f"{inv[int(o.reduce_mode)]}-thr{int(o.threshold)}-lay{int(o.lane_layout)}" + \
+    return f"{inv[int(o.reduce_mode)]}-thr{int(o.threshold)}-lay{int(o.lane_layout)}-ppt{max(1, int(o.pixels_per_thread))}" + \
         ("" if o.store_T else "-recompute")
 
 

@@ -163,7 +163,8 @@ class BatchedViews:
 
 
 def gsr_opts_tuple(o):
-    return (int(o.reduce_mode), int(o.threshold), int(o.lane_layout), int(o.store_T))
+    return (int(o.reduce_mode), int(o.threshold), int(o.lane_layout), int(o.store_T),
+            max(1, int(o.pixels_per_thread)))
 
 
 def time_graph(g, reps=5, before=None):
@@ -184,12 +185,13 @@ def autotune_batched(bv: BatchedViews, reps=3, flush=None):
     """Tier x threshold x layout x CTAs-per-SM for the captured persistent
     launch; returns (best opts, best ctas_per_sm, best ms, table)."""
     cands = []
-    for lay in (0, 1):
-        cands.append((gsr.backward_opts("warp", 0, lay, bv.store_T), 0))
-        for thr in (8, 12, 16):
-            for cps in (0, 2, 3):
-                cands.append((gsr.backward_opts("hybrid", thr, lay, bv.store_T), cps))
-        cands.append((gsr.backward_opts("block", 0, lay, bv.store_T), 0))
+    for ppt in (1, 2):
+        for lay in (0, 1):
+            cands.append((gsr.backward_opts("warp", 0, lay, bv.store_T, ppt), 0))
+            for thr in (8, 12, 16):
+                for cps in (0, 2, 3):
+                    cands.append((gsr.backward_opts("hybrid", thr, lay, bv.store_T, ppt), cps))
+            cands.append((gsr.backward_opts("block", 0, lay, bv.store_T, ppt), 0))
     table, best = {}, None
     for o, cps in cands:
         g = bv.capture(o, cps)

@@ -1,0 +1,356 @@
+// Shared device code of the forward and backward blend kernels.
+//
+// One CTA per 16x16 screen tile.  The tile's depth-sorted splat list is
+// staged through shared memory in batches of one entry per pixel (coalesced
+// id load, three 16-byte record loads per entry, and a per-warp cull mask);
+// every warp then visits the staged splats that can touch its pixel block,
+// all 32 lanes on the same splat at the same time -- the property that makes
+// the warp-level reduction of the backward legal without a match (Sec. V-A2
+// requires all lanes to update the same primitive; here it holds by
+// construction).  Each thread owns PPT pixels of the tile.
+#pragma once
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+struct RasterGeom {
+    int W, H, gx, gy;
+};
+
+// Thread / warp / pixel geometry of a TW x TH tile with PPT pixels per thread.
+//   LAYOUT 0: a warp covers TW x (32 PPT / TW) consecutive rows;
+//   LAYOUT 1: a warp covers an 8 x (4 PPT) pixel block.
+// Pixel q of a lane lies 32/TW (LAYOUT 0) or 4 (LAYOUT 1) rows below pixel 0.
+template <int TW, int TH, int LAYOUT, int PPT>
+struct Shape {
+    static constexpr int TWd = TW, THd = TH;
+    static constexpr int B = TW * TH;       // pixels per tile = entries staged per batch
+    static constexpr int NT = B / PPT;      // threads per CTA
+    static constexpr int NW = NT / 32;      // warps per CTA
+    static constexpr int BX = LAYOUT == 0 ? TW : 8;
+    static constexpr int BY = LAYOUT == 0 ? 32 * PPT / TW : 4 * PPT;
+    static constexpr int WX = TW / BX;      // warp blocks per tile row
+    static_assert(B % PPT == 0 && NT % 32 == 0, "tile shape");
+
+    __device__ static void pixel(int tid, int q, int& lx, int& ly) {
+        const int w = tid >> 5, l = tid & 31;
+        if (LAYOUT == 0) {
+            lx = l % TW;
+            ly = w * BY + l / TW + q * (32 / TW);
+        } else {
+            lx = (w % WX) * 8 + (l & 7);
+            ly = (w / WX) * BY + (l >> 3) + 4 * q;
+        }
+    }
+    __device__ static void warp_origin(int w, int& x0, int& y0) {
+        x0 = (w % WX) * BX;
+        y0 = (w / WX) * BY;
+    }
+};
+
+// Bitmask of the warps of a tile (origin ox, oy) whose pixel block can hold
+// a pixel where this splat reaches alpha >= 1/255: the bounding box of the
+// ellipse sigma <= ln(255 o) (half-widths sqrt(2 L C / det), sqrt(2 L A /
+// det) for the conic [[A,B],[B,C]]), with L enlarged by 1% + 0.01 and the box
+// by 2% + 0.05 px, so FP32 rounding of sigma or alpha can never let a culled
+// pair pass the alpha test: culling removes only pairs every kernel skips.
+template <class SH>
+__device__ __forceinline__ unsigned warp_cull_mask(float u, float v, float A, float B, float C, float o, int ox,
+                                                   int oy) {
+    constexpr int NW = SH::NW;
+    constexpr unsigned ALL = NW >= 32 ? 0xffffffffu : ((1u << NW) - 1u);
+    if (!(o >= kAlphaMin)) return 0u;  // alpha = o G <= o < 1/255 at every pixel
+    const float det = A * C - B * B;
+    if (!(det > 0.0f) || !(A > 0.0f) || !(C > 0.0f)) return ALL;
+    const float L = __logf(o * 255.0f) * 1.01f + 0.01f;
+    const float ex = sqrtf(2.0f * L * C / det) * 1.02f + 0.05f;
+    const float ey = sqrtf(2.0f * L * A / det) * 1.02f + 0.05f;
+    unsigned m = 0u;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        int x0, y0;
+        SH::warp_origin(w, x0, y0);
+        x0 += ox;
+        y0 += oy;
+        const bool hit = (u + ex >= (float)x0) && (u - ex <= (float)(x0 + SH::BX - 1)) &&
+                         (v + ey >= (float)y0) && (v - ey <= (float)(y0 + SH::BY - 1));
+        m |= hit ? (1u << w) : 0u;
+    }
+    return m;
+}
+
+// Stages batch entries [0, cnt) (list positions given by pos_of) into shared
+// memory; with PPT > 1 every thread stages several entries.
+template <class SH, bool COLOR, bool IDS, class PosOf>
+__device__ __forceinline__ void stage_batch(int cnt, PosOf pos_of, const uint32_t* __restrict__ point_list,
+                                            const float* __restrict__ splat2d, int ox, int oy, float4* s_a,
+                                            float4* s_b, float* s_c, uint32_t* s_id, unsigned* s_mask) {
+    for (int e = threadIdx.x; e < cnt; e += SH::NT) {
+        const uint32_t id = point_list[pos_of(e)];
+        const float4* rec = reinterpret_cast<const float4*>(splat2d + (size_t)id * GSR_REC);
+        const float4 a = rec[0], b = rec[1];
+        s_a[e] = a;
+        s_b[e] = b;
+        if (COLOR) s_c[e] = rec[2].x;
+        if (IDS) s_id[e] = id;
+        s_mask[e] = warp_cull_mask<SH>(a.x, a.y, a.z, a.w, b.x, b.y, ox, oy);
+    }
+}
+
+// Front-to-back walk of each of the thread's pixels over the tile list (the
+// forward rule; shared by the forward kernel and the recompute mode of the
+// backward, so both produce the same final transmittance and last
+// contributor bit for bit).  All threads of the CTA must call it.
+template <class SH, bool COLOR>
+__device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict__ point_list,
+                                           const float* __restrict__ splat2d, const float* px, const float* py,
+                                           const bool* inside, int ox, int oy, float4* s_a, float4* s_b,
+                                           float* s_c, unsigned* s_mask, float* T, int* last, float (*C)[3]) {
+    constexpr int PPT = SH::B / SH::NT;
+    const int n = (int)(rg.y - rg.x);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    bool done[PPT];
+    bool all_done = true;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        done[q] = !inside[q];
+        all_done &= done[q];
+        T[q] = 1.0f;
+        last[q] = 0;
+        C[q][0] = C[q][1] = C[q][2] = 0.0f;
+    }
+    for (int base = 0; base < n; base += SH::B) {
+        if (__syncthreads_count(all_done) == SH::NT) break;
+        const int cnt = min(SH::B, n - base);
+        stage_batch<SH, COLOR, false>(cnt, [&](int e) { return rg.x + (uint32_t)(base + e); }, point_list,
+                                      splat2d, ox, oy, s_a, s_b, s_c, nullptr, s_mask);
+        __syncthreads();
+        bool wdone = __all_sync(kFull, all_done);
+        for (int c0 = 0; c0 < cnt && !wdone; c0 += 32) {
+            const int kq = c0 + lane;
+            unsigned bits = __ballot_sync(kFull, kq < cnt && ((s_mask[kq] >> w) & 1u));
+            while (bits) {
+                const int k = c0 + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const float4 a = s_a[k], b = s_b[k];
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    if (done[q]) continue;
+                    SplatEval e;
+                    if (!eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, px[q], py[q], e)) continue;
+                    const float testT = __fmul_rn(T[q], __fsub_rn(1.0f, e.alpha));
+                    if (testT < kTMin) {
+                        done[q] = true;
+                        continue;
+                    }
+                    if (COLOR) {
+                        const float wgt = __fmul_rn(e.alpha, T[q]);
+                        C[q][0] = __fmaf_rn(b.z, wgt, C[q][0]);
+                        C[q][1] = __fmaf_rn(b.w, wgt, C[q][1]);
+                        C[q][2] = __fmaf_rn(s_c[k], wgt, C[q][2]);
+                    }
+                    T[q] = testT;
+                    last[q] = base + k + 1;
+                }
+                all_done = true;
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) all_done &= done[q];
+                if (__all_sync(kFull, all_done)) {
+                    wdone = true;
+                    break;
+                }
+            }
+        }
+    }
+}
+
+struct BwdArgs {
+    RasterGeom g;
+    const uint2* ranges;
+    const uint32_t* point_list;
+    const float* splat2d;
+    float bg0, bg1, bg2;
+    const float* final_T;
+    const int* n_contrib;
+    const float* dL_dimage;
+    float* grad2d;
+    int threshold;
+};
+
+template <int B, int MODE>
+struct BwdSmem {
+    float4 a[B];
+    float4 b[B];
+    float c[B];
+    uint32_t id[B];
+    unsigned mask[B];
+    float acc[MODE == GSR_REDUCE_BLOCK ? B * 9 : 1];
+    int maxlast;
+};
+
+// Gradients of one active (pixel, splat) pair, walking back to front: T
+// holds T_{j+1} on entry and T_j on exit; S accumulates
+// sum_{k>j} (c_k . g) alpha_k T_k + T_final (bg . g).
+__device__ __forceinline__ void pair_grads(const SplatEval& e, float4 a, float4 b, float cb, float g0, float g1,
+                                           float g2, float& T, float& S, float* v) {
+    const float inv = __frcp_rn(1.0f - e.alpha);
+    const float Tj = T * inv;
+    const float cg = b.z * g0 + b.w * g1 + cb * g2;
+    const float dal = Tj * cg - S * inv;
+    const float w = e.alpha * Tj;
+    S = fmaf(cg, w, S);
+    T = Tj;
+    v[6] = w * g0;
+    v[7] = w * g1;
+    v[8] = w * g2;
+    const float dsig = e.capped ? 0.0f : -b.y * e.G * dal;
+    v[5] = e.capped ? 0.0f : e.G * dal;
+    v[0] = (a.z * e.dx + a.w * e.dy) * dsig;
+    v[1] = (a.w * e.dx + b.x * e.dy) * dsig;
+    v[2] = 0.5f * e.dx * e.dx * dsig;
+    v[3] = e.dx * e.dy * dsig;
+    v[4] = 0.5f * e.dy * e.dy * dsig;
+}
+
+// Backward of one tile: the gradient-computation step (Sec. III-A) for the
+// tile's pixels, accumulated by the tier MODE.  All threads of the CTA call
+// it; shared storage is reused across calls.
+template <class SH, int MODE, bool STORE_T>
+__device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, BwdSmem<SH::B, MODE>& sm) {
+    constexpr int B = SH::B, NT = SH::NT;
+    constexpr int PPT = B / NT;
+    static_assert(MODE != GSR_REDUCE_PLAIN || PPT == 1, "the plain tier keeps one pixel per thread");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = tile % p.g.gx, ty = tile / p.g.gx;
+    const int ox = tx * SH::TWd, oy = ty * SH::THd;
+    const uint2 rg = p.ranges[tile];
+    const int nlist = (int)(rg.y - rg.x);
+    const size_t HW = (size_t)p.g.W * p.g.H;
+
+    float fpx[PPT], fpy[PPT], Tf[PPT], g0[PPT], g1[PPT], g2[PPT], T[PPT], S[PPT];
+    int last[PPT];
+    bool inside[PPT];
+    size_t pix[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        int lx, ly;
+        SH::pixel(tid, q, lx, ly);
+        const int px = ox + lx, py = oy + ly;
+        inside[q] = px < p.g.W && py < p.g.H;
+        fpx[q] = (float)px;
+        fpy[q] = (float)py;
+        pix[q] = (size_t)py * p.g.W + px;
+    }
+    if (STORE_T) {
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            Tf[q] = inside[q] ? p.final_T[pix[q]] : 0.0f;
+            last[q] = inside[q] ? min(max(p.n_contrib[pix[q]], 0), nlist) : 0;  // never walk past the list
+        }
+    } else {
+        float C[PPT][3];
+        walk_front<SH, false>(rg, p.point_list, p.splat2d, fpx, fpy, inside, ox, oy, sm.a, sm.b, sm.c, sm.mask, Tf,
+                              last, C);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q)
+            if (!inside[q]) { Tf[q] = 0.0f; last[q] = 0; }
+    }
+    int mylast = 0;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        g0[q] = inside[q] ? p.dL_dimage[pix[q]] : 0.0f;
+        g1[q] = inside[q] ? p.dL_dimage[HW + pix[q]] : 0.0f;
+        g2[q] = inside[q] ? p.dL_dimage[2 * HW + pix[q]] : 0.0f;
+        T[q] = Tf[q];
+        S[q] = Tf[q] * (p.bg0 * g0[q] + p.bg1 * g1[q] + p.bg2 * g2[q]);
+        mylast = max(mylast, last[q]);
+    }
+    __syncthreads();  // shared storage may still be read by a previous tile / the recompute walk
+    if (tid == 0) sm.maxlast = 0;
+    if (MODE == GSR_REDUCE_BLOCK)
+        for (int i = tid; i < B * 9; i += NT) sm.acc[i] = 0.0f;
+    __syncthreads();
+    const int wlast = __reduce_max_sync(kFull, mylast);
+    if (lane == 0) atomicMax(&sm.maxlast, wlast);
+    __syncthreads();
+    const int maxlast = sm.maxlast;
+    const int rparam = reduce9_param(lane);
+    float* __restrict__ grad = p.grad2d;
+
+    for (int top = maxlast; top > 0; top -= B) {
+        const int cnt = min(B, top);
+        __syncthreads();
+        stage_batch<SH, true, true>(cnt, [&](int e) { return rg.x + (uint32_t)(top - 1 - e); }, p.point_list,
+                                    p.splat2d, ox, oy, sm.a, sm.b, sm.c, sm.id, sm.mask);
+        __syncthreads();
+        // each warp visits, back to front, only the staged splats whose
+        // alpha >= 1/255 region touches its pixel block and that lie before
+        // the warp's last contributor
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            const int kq = c0 + lane;
+            unsigned bits =
+                __ballot_sync(kFull, kq < cnt && ((sm.mask[kq] >> warp) & 1u) && (top - 1 - kq < wlast));
+            while (bits) {
+                const int k = c0 + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const int pos = top - 1 - k;
+                const float4 a = sm.a[k], b = sm.b[k];
+                const float cb = sm.c[k];
+                float v[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) v[i] = 0.0f;
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    SplatEval e;
+                    const bool act = (pos < last[q]) && eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, fpx[q], fpy[q], e);
+                    if (act) {
+                        float vq[9];
+                        pair_grads(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], vq);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) v[i] += vq[i];
+                    }
+                    any |= act;
+                }
+                float* rec = grad + (size_t)sm.id[k] * GSR_REC;
+                if (MODE == GSR_REDUCE_PLAIN) {
+                    if (any) {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) atomicAdd(rec + i, v[i]);
+                    }
+                } else {
+                    const unsigned m = __ballot_sync(kFull, any);
+                    if (m == 0u) continue;
+                    const bool dense = (MODE == GSR_REDUCE_WARP) || (__popc(m) >= p.threshold);
+                    if (dense) {
+                        const float z = reduce9(v, lane);
+                        if (rparam < 9) {
+                            if (MODE == GSR_REDUCE_BLOCK) atomicAdd(&sm.acc[k * 9 + rparam], z);
+                            else red_add(rec + rparam, z);
+                        }
+                    } else if (any) {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            if (MODE == GSR_REDUCE_BLOCK) atomicAdd(&sm.acc[k * 9 + i], v[i]);
+                            else atomicAdd(rec + i, v[i]);
+                        }
+                    }
+                }
+            }
+        }
+        if (MODE == GSR_REDUCE_BLOCK) {
+            __syncthreads();
+            for (int i = tid; i < cnt * 9; i += NT) {
+                const float val = sm.acc[i];
+                if (val != 0.0f) {
+                    const int k = i / 9;
+                    red_add(grad + (size_t)sm.id[k] * GSR_REC + (i - 9 * k), val);
+                    sm.acc[i] = 0.0f;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace gsr

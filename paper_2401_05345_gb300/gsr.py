@@ -40,15 +40,16 @@ class Camera(ctypes.Structure):
 
 class BackwardOpts(ctypes.Structure):
     _fields_ = [("reduce_mode", c_int32), ("threshold", c_int32), ("lane_layout", c_int32),
-                ("store_T", c_int32), ("reserved", c_int32 * 4)]
+                ("store_T", c_int32), ("pixels_per_thread", c_int32), ("reserved", c_int32 * 3)]
 
 
-def backward_opts(reduce="warp", threshold=0, lane_layout=0, store_T=True) -> BackwardOpts:
+def backward_opts(reduce="warp", threshold=0, lane_layout=0, store_T=True, pixels_per_thread=1) -> BackwardOpts:
     o = BackwardOpts()
     o.reduce_mode = REDUCE_NAMES[reduce] if isinstance(reduce, str) else int(reduce)
     o.threshold = int(threshold)
     o.lane_layout = int(lane_layout)
     o.store_T = 1 if store_T else 0
+    o.pixels_per_thread = int(pixels_per_thread)
     return o
 
 

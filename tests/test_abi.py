@@ -59,6 +59,10 @@ def test_argument_errors_are_reported_before_any_launch(lib):
     assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, p, p, p, p, ctypes.byref(opts), None) == gsr.GSR_EINVAL
     opts = gsr.backward_opts("hybrid", threshold=40)
     assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, p, p, p, p, ctypes.byref(opts), None) == gsr.GSR_EINVAL
+    opts = gsr.backward_opts("plain", pixels_per_thread=2)   # the plain baseline keeps one pixel per thread
+    assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, p, p, p, p, ctypes.byref(opts), None) == gsr.GSR_EINVAL
+    opts = gsr.backward_opts("warp", pixels_per_thread=3)
+    assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, p, p, p, p, ctypes.byref(opts), None) == gsr.GSR_EINVAL
     opts = gsr.backward_opts("warp", store_T=True)
     assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, None, None, p, p, ctypes.byref(opts), None) == gsr.GSR_EINVAL
     assert lib.gsr_backward(32, 32, 12, 16, p, p, p, bg, p, p, p, p, None, None) == gsr.GSR_EINVAL

@@ -126,7 +126,8 @@ def test_autograd_central_differences(dev, orc):
     gradient must lie within that band (plus 1 %).  Parameters of visible
     Gaussians only.  Steps in which a discrete decision of the forward
     changes (list order, last contributor, active pairs) are not derivatives
-    and are skipped; at least 25 entries must have an informative band."""
+    and are skipped; at least 25 entries must have an informative band
+    (narrower than 20 % of the value)."""
     scene, cam = crop_workload()
     vis = np.nonzero(orc.preprocess(scene, cam)["radius"] > 0)[0]
     w = torch.from_numpy(weights(cam.height, cam.width)).to(dev).double()
@@ -142,7 +143,7 @@ def test_autograd_central_differences(dev, orc):
             per = p.data[0].numel()
             flat = p.data.view(-1)
             gmax = np.abs(g).max()
-            for gi in rng.choice(vis, 10, replace=False):
+            for gi in rng.choice(vis, 30, replace=False):
                 idx = int(gi) * per + int(rng.integers(per))
                 x0 = float(flat[idx])
                 fds, crossed = [], False
@@ -161,7 +162,7 @@ def test_autograd_central_differences(dev, orc):
                 an = float(g.reshape(-1)[idx])
                 band = abs(fds[0] - fds[1])
                 checked += 1
-                if band < 0.05 * abs(an):
+                if band < 0.2 * abs(an):
                     informative += 1
                 # entries below the FP32 forward's difference resolution (2e-3 of
                 # the group's largest gradient) are only held to that floor

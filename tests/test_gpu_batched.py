@@ -62,7 +62,8 @@ def test_batched_graph_matches_oracle(dev, orc):
                                r64["rgb"], np.asarray(BG, np.float64), g))
     bv._refresh_descriptors()
     for opts, cps in ((gsr.backward_opts("hybrid", 8, 1), 0), (gsr.backward_opts("block", 0, 0), 2),
-                      (gsr.backward_opts("plain", 0, 0), 1)):
+                      (gsr.backward_opts("plain", 0, 0), 1), (gsr.backward_opts("hybrid", 12, 1, True, 2), 0),
+                      (gsr.backward_opts("block", 0, 1, False, 2), 3)):
         g = bv.capture(opts, cps)
         for rep in range(2):  # replay twice: results must not depend on leftovers
             bv.zero_grad2d()

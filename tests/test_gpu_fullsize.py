@@ -18,7 +18,8 @@ from paper_2401_05345_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
 
-TIERS = [("plain", 0, 1), ("warp", 0, 1), ("hybrid", 12, 1), ("hybrid", 8, 0), ("block", 0, 1)]
+TIERS = [("plain", 0, 1, 1), ("warp", 0, 1, 1), ("hybrid", 12, 1, 1), ("hybrid", 8, 0, 1), ("block", 0, 1, 1),
+         ("hybrid", 12, 1, 2), ("warp", 0, 0, 2), ("block", 0, 1, 2)]
 BG = (0.0, 0.0, 0.0)
 
 
@@ -142,7 +143,7 @@ def test_fullsize_forward_on_sampled_tiles(dev, full):
         assert ok.all(), f"n_contrib differs in tile {t}"
 
 
-@pytest.mark.parametrize("tier", TIERS, ids=lambda t: f"{t[0]}-thr{t[1]}-lay{t[2]}")
+@pytest.mark.parametrize("tier", TIERS, ids=lambda t: f"{t[0]}-thr{t[1]}-lay{t[2]}-ppt{t[3]}")
 def test_fullsize_backward_on_sampled_splats(dev, full, tier):
     cam = full["cam"]
     image, fT, nc, ranges, pl, splat = _forward(dev, full)

@@ -210,12 +210,13 @@ def test_forward_matches_oracle(dev, orc, name, bg):
 # a4-a6: backward blend + gradient accumulation, every tier
 # ----------------------------------------------------------------------------
 
-TIERS = [("plain", 0, 0), ("warp", 0, 0), ("warp", 0, 1), ("hybrid", 8, 0), ("hybrid", 16, 1),
-         ("hybrid", 33, 0), ("block", 0, 0), ("block", 12, 1)]
+TIERS = [("plain", 0, 0, 1), ("warp", 0, 0, 1), ("warp", 0, 1, 1), ("hybrid", 8, 0, 1), ("hybrid", 16, 1, 1),
+         ("hybrid", 33, 0, 1), ("block", 0, 0, 1), ("block", 12, 1, 1),
+         ("warp", 0, 0, 2), ("hybrid", 8, 1, 2), ("hybrid", 33, 1, 2), ("block", 0, 1, 2), ("block", 12, 0, 2)]
 
 
 @pytest.mark.parametrize("store_T", [True, False])
-@pytest.mark.parametrize("tier", TIERS, ids=lambda t: f"{t[0]}-thr{t[1]}-lay{t[2]}")
+@pytest.mark.parametrize("tier", TIERS, ids=lambda t: f"{t[0]}-thr{t[1]}-lay{t[2]}-ppt{t[3]}")
 @pytest.mark.parametrize("name", WORKLOADS)
 def test_backward_matches_oracle(dev, orc, name, tier, store_T):
     st_ = oracle_stage(orc, name, (0.3, 0.7, 0.1))
@@ -224,7 +225,7 @@ def test_backward_matches_oracle(dev, orc, name, tier, store_T):
     f = gpu_forward(dev, st_)
     n = len(st_["rec"])
     grad = torch.zeros((n, 12), device=dev)
-    opts = gsr.backward_opts(tier[0], tier[1], tier[2], store_T)
+    opts = gsr.backward_opts(tier[0], tier[1], tier[2], store_T, tier[3])
     gsr.gsr_backward(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], st_["bg"],
                      f["final_T"] if store_T else None, f["n_contrib"] if store_T else None,
                      T(st_["g"]), grad, opts)
