@@ -184,25 +184,62 @@ __global__ void count_sorted_kernel(int n, const float* __restrict__ splat2d, co
     counts[j] = c;
 }
 
-__global__ void duplicate_sorted_kernel(int n, const float* __restrict__ splat2d, const int* __restrict__ radius,
-                                        const uint32_t* __restrict__ order, BinGeom g,
-                                        const uint32_t* __restrict__ offsets, uint32_t* __restrict__ tkeys,
-                                        uint32_t* __restrict__ vals) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const uint32_t i = order[j];
-    const int r = radius[i];
-    if (r <= 0) return;
-    float2 uv = *reinterpret_cast<const float2*>(splat2d + (size_t)i * GSR_REC);
-    int x0, x1, y0, y1;
-    tile_rect(uv.x, uv.y, r, g.gx, g.gy, g.twl, g.thl, x0, x1, y0, y1);
-    uint32_t o = offsets[j];
-    for (int y = y0; y < y1; ++y)
-        for (int x = x0; x < x1; ++x) {
-            tkeys[o] = (uint32_t)(y * g.gx + x);
-            vals[o] = i;
-            ++o;
+// Writes every visible Gaussian's tile entries (depth rank j, tiles
+// row-major inside its rectangle).  A warp takes 32 consecutive ranks, whose
+// entries form one contiguous range, and its lanes write that range together
+// (entry e goes to the lane whose prefix interval holds it), so the stores
+// are coalesced whatever the per-Gaussian counts.
+__global__ void __launch_bounds__(256)
+duplicate_sorted_kernel(int n, const float* __restrict__ splat2d, const int* __restrict__ radius,
+                        const uint32_t* __restrict__ order, BinGeom g, const uint32_t* __restrict__ offsets,
+                        uint32_t* __restrict__ tkeys, uint32_t* __restrict__ vals) {
+    __shared__ uint32_t s_pre[8][33];
+    __shared__ int s_x0[8][32], s_wd[8][32], s_y0[8][32];
+    __shared__ uint32_t s_id[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j0 = j - lane;
+    if (j0 >= n) return;  // whole warp past the end
+    uint32_t c = 0, id = 0;
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    if (j < n) {
+        id = order[j];
+        const int r = radius[id];
+        if (r > 0) {
+            float2 uv = *reinterpret_cast<const float2*>(splat2d + (size_t)id * GSR_REC);
+            tile_rect(uv.x, uv.y, r, g.gx, g.gy, g.twl, g.thl, x0, x1, y0, y1);
+            const int nt = (x1 - x0) * (y1 - y0);
+            c = nt > 0 ? (uint32_t)nt : 0u;
         }
+    }
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    s_pre[w][lane] = incl - c;
+    if (lane == 31) s_pre[w][32] = incl;
+    s_x0[w][lane] = x0;
+    s_wd[w][lane] = x1 - x0;
+    s_y0[w][lane] = y0;
+    s_id[w][lane] = id;
+    __syncwarp();
+    const uint32_t total = s_pre[w][32];
+    const uint32_t base = offsets[j0];
+    for (uint32_t e = lane; e < total; e += 32) {
+        int lo = 0, hi = 31;  // last lane whose prefix start <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pre[w][mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t local = e - s_pre[w][lo];
+        const int wd = s_wd[w][lo];
+        const int ty = s_y0[w][lo] + (int)(local / (uint32_t)wd);
+        const int tx = s_x0[w][lo] + (int)(local % (uint32_t)wd);
+        tkeys[base + e] = (uint32_t)(ty * g.gx + tx);
+        vals[base + e] = s_id[w][lo];
+    }
 }
 
 __global__ void ranges_tile_kernel(long long nkeys, const uint32_t* __restrict__ tkeys, uint32_t* __restrict__ ranges) {

@@ -87,39 +87,55 @@ __device__ __forceinline__ void sh_basis_vjp(int deg, float x, float y, float z,
     gx += -C3a * (3.f * xx - 3.f * yy) * c[15]; gy += C3a * 6.f * x * y * c[15];
 }
 
-// Loads / accumulates the 3K feature floats of one Gaussian: 16-byte vectors
-// when 3K is a multiple of 4 and the array is 16-byte aligned (VEC), so a
-// thread's record is read with few wide loads; scalar accesses otherwise.
-template <int NF, bool VEC>
-__device__ __forceinline__ void load_feat(const float* __restrict__ src, float* dst) {
-    if constexpr (VEC && NF % 4 == 0) {
-        const float4* s4 = reinterpret_cast<const float4*>(src);
-#pragma unroll
-        for (int j = 0; j < NF / 4; ++j) {
-            float4 x = s4[j];
-            dst[4 * j] = x.x; dst[4 * j + 1] = x.y; dst[4 * j + 2] = x.z; dst[4 * j + 3] = x.w;
+// Feature rows of a chunk of CH Gaussians staged through shared memory:
+// global rows of NF floats are read (and written back) with coalesced
+// 16-byte accesses when VEC, and kept in shared memory with an odd row
+// stride NF + 1 so that each thread's own row is read without bank conflicts.
+template <int NF>
+__device__ __forceinline__ int srow(int f) { return (f / NF) * (NF + 1) + f % NF; }
+
+template <int NF, int CH, bool VEC>
+__device__ __forceinline__ void stage_rows_in(const float* __restrict__ g, int rows, float* s) {
+    const int total = rows * NF;
+    int f0 = 0;
+    if (VEC) {
+        const float4* g4 = reinterpret_cast<const float4*>(g);
+        const int n4 = total >> 2;
+        for (int t = threadIdx.x; t < n4; t += CH) {
+            const float4 x = g4[t];
+            const int f = 4 * t;
+            s[srow<NF>(f)] = x.x;
+            s[srow<NF>(f + 1)] = x.y;
+            s[srow<NF>(f + 2)] = x.z;
+            s[srow<NF>(f + 3)] = x.w;
         }
-    } else {
-#pragma unroll
-        for (int j = 0; j < NF; ++j) dst[j] = src[j];
+        f0 = n4 << 2;
     }
+    for (int f = f0 + threadIdx.x; f < total; f += CH) s[srow<NF>(f)] = g[f];
 }
 
-template <int NF, bool VEC>
-__device__ __forceinline__ void add_feat(float* __restrict__ dst, const float* v) {
-    if constexpr (VEC && NF % 4 == 0) {
-        float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-        for (int j = 0; j < NF / 4; ++j) {
-            float4 x = d4[j];
-            x.x += v[4 * j]; x.y += v[4 * j + 1]; x.z += v[4 * j + 2]; x.w += v[4 * j + 3];
-            d4[j] = x;
+template <int NF, int CH, bool VEC>
+__device__ __forceinline__ void stage_rows_add_out(float* __restrict__ g, int rows, const float* s) {
+    const int total = rows * NF;
+    int f0 = 0;
+    if (VEC) {
+        float4* g4 = reinterpret_cast<float4*>(g);
+        const int n4 = total >> 2;
+        for (int t = threadIdx.x; t < n4; t += CH) {
+            float4 x = g4[t];
+            const int f = 4 * t;
+            x.x += s[srow<NF>(f)];
+            x.y += s[srow<NF>(f + 1)];
+            x.z += s[srow<NF>(f + 2)];
+            x.w += s[srow<NF>(f + 3)];
+            g4[t] = x;
         }
-    } else {
-#pragma unroll
-        for (int j = 0; j < NF; ++j) dst[j] += v[j];
+        f0 = n4 << 2;
     }
+    for (int f = f0 + threadIdx.x; f < total; f += CH) g[f] += s[srow<NF>(f)];
 }
+
+constexpr int kChunk = 128;  // Gaussians per CTA of the projection kernels
 
 // Forward quantities of one Gaussian, kept for the backward projection.
 struct Proj {
@@ -189,13 +205,20 @@ __device__ __forceinline__ bool project(const Cam& k, const float* mean, const f
 }
 
 template <int DEG, bool VEC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kChunk)
 preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict__ scale,
                   const float* __restrict__ quat, const float* __restrict__ opacity,
                   const float* __restrict__ feat, Cam k, int gx, int gy, int tw_log2, int th_log2,
                   float* __restrict__ splat2d, int* __restrict__ radius, float* __restrict__ gzero) {
     constexpr int K = DEG < 0 ? 1 : (DEG + 1) * (DEG + 1);
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int NF = 3 * K;
+    __shared__ float s_f[DEG < 0 ? 1 : kChunk * (NF + 1)];
+    const int base = blockIdx.x * kChunk;
+    if constexpr (DEG >= 0) {
+        stage_rows_in<NF, kChunk, VEC>(feat + (size_t)base * NF, min(kChunk, n - base), s_f);
+        __syncthreads();
+    }
+    const int i = base + threadIdx.x;
     if (i >= n) return;
     float4* rec = reinterpret_cast<float4*>(splat2d + (size_t)i * GSR_REC);
     if (gzero) {
@@ -230,8 +253,7 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
         float il = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
         float Y[16];
         sh_basis(DEG, dx * il, dy * il, dz * il, Y);
-        float f[3 * K];
-        load_feat<3 * K, VEC>(feat + (size_t)i * K * 3, f);
+        const float* f = s_f + threadIdx.x * (NF + 1);
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
@@ -250,60 +272,79 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
 }
 
 template <int DEG, bool VEC>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kChunk)
 backproject_kernel(int n, const float* __restrict__ mean, const float* __restrict__ scale,
                    const float* __restrict__ quat, const float* __restrict__ feat, Cam k,
                    const int* __restrict__ radius, const float* __restrict__ grad2d,
                    float* __restrict__ dmean, float* __restrict__ dscale, float* __restrict__ dquat,
                    float* __restrict__ dopacity, float* __restrict__ dfeat) {
     constexpr int K = DEG < 0 ? 1 : (DEG + 1) * (DEG + 1);
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || radius[i] <= 0) return;
+    constexpr int NF = 3 * K;
+    __shared__ float s_f[DEG < 0 ? 1 : kChunk * (NF + 1)];
+    const int base = blockIdx.x * kChunk;
+    const int rows = min(kChunk, n - base);
+    const int i = base + threadIdx.x;
+    const bool valid = i < n && radius[i] > 0;
+    float dm[3] = {0.f, 0.f, 0.f};
+    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, gc = ga;
+    if (valid) {
+        const float4* g4 = reinterpret_cast<const float4*>(grad2d + (size_t)i * GSR_REC);
+        ga = g4[0];
+        gb = g4[1];
+        gc = g4[2];
+    }
+    float gcol[3] = {gb.z, gb.w, gc.x};
+
+    // colour: SH basis along the viewing direction, clamp at 0
+    if constexpr (DEG < 0) {
+        if (valid)
+            for (int ch = 0; ch < 3; ++ch) dfeat[3 * (size_t)i + ch] += gcol[ch];
+    } else {
+        stage_rows_in<NF, kChunk, VEC>(feat + (size_t)base * NF, rows, s_f);
+        __syncthreads();
+        float* f = s_f + threadIdx.x * (NF + 1);
+        if (valid) {
+            const float* m = mean + 3 * (size_t)i;
+            float dx = m[0] - k.campos[0], dy = m[1] - k.campos[1], dz = m[2] - k.campos[2];
+            float len = sqrtf(dx * dx + dy * dy + dz * dz);
+            float il = 1.0f / len;
+            float x = dx * il, y = dy * il, z = dz * il;
+            float Y[16];
+            sh_basis(DEG, x, y, z, Y);
+            float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) raw[ch] = fmaf(Y[j], f[3 * j + ch], raw[ch]);
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) if (raw[ch] < 0.f) gcol[ch] = 0.f;
+            float cw[16];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                cw[j] = f[3 * j] * gcol[0] + f[3 * j + 1] * gcol[1] + f[3 * j + 2] * gcol[2];
+                // this thread's row now receives its feature gradient
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) f[3 * j + ch] = Y[j] * gcol[ch];
+            }
+            float ddx, ddy, ddz;
+            sh_basis_vjp(DEG, x, y, z, cw, ddx, ddy, ddz);
+            float dot = x * ddx + y * ddy + z * ddz;
+            dm[0] += (ddx - x * dot) * il;
+            dm[1] += (ddy - y * dot) * il;
+            dm[2] += (ddz - z * dot) * il;
+        } else if (threadIdx.x < rows) {
+#pragma unroll
+            for (int j = 0; j < NF; ++j) f[j] = 0.f;
+        }
+        __syncthreads();
+        stage_rows_add_out<NF, kChunk, VEC>(dfeat + (size_t)base * NF, rows, s_f);
+    }
+    if (!valid) return;
     Proj P;
     const float* m = mean + 3 * (size_t)i;
     const float* s = scale + 3 * (size_t)i;
     if (!project(k, m, s, quat + 4 * (size_t)i, P)) return;
-    const float4* g4 = reinterpret_cast<const float4*>(grad2d + (size_t)i * GSR_REC);
-    float4 ga = g4[0], gb = g4[1], gc = g4[2];
     const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, go = gb.y;
-    float gcol[3] = {gb.z, gb.w, gc.x};
-    float dm[3] = {0.f, 0.f, 0.f};
-
-    // colour: SH basis along the viewing direction, clamp at 0
-    if constexpr (DEG < 0) {
-        for (int ch = 0; ch < 3; ++ch) dfeat[3 * (size_t)i + ch] += gcol[ch];
-    } else {
-        float dx = m[0] - k.campos[0], dy = m[1] - k.campos[1], dz = m[2] - k.campos[2];
-        float len = sqrtf(dx * dx + dy * dy + dz * dz);
-        float il = 1.0f / len;
-        float x = dx * il, y = dy * il, z = dz * il;
-        float Y[16];
-        sh_basis(DEG, x, y, z, Y);
-        float f[3 * K];
-        load_feat<3 * K, VEC>(feat + (size_t)i * K * 3, f);
-        float raw[3] = {0.5f, 0.5f, 0.5f};
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) raw[ch] = fmaf(Y[j], f[3 * j + ch], raw[ch]);
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) if (raw[ch] < 0.f) gcol[ch] = 0.f;
-        float df[3 * K];
-        float cw[16];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) df[3 * j + ch] = Y[j] * gcol[ch];
-            cw[j] = f[3 * j] * gcol[0] + f[3 * j + 1] * gcol[1] + f[3 * j + 2] * gcol[2];
-        }
-        add_feat<3 * K, VEC>(dfeat + (size_t)i * K * 3, df);
-        float ddx, ddy, ddz;
-        sh_basis_vjp(DEG, x, y, z, cw, ddx, ddy, ddz);
-        float dot = x * ddx + y * ddy + z * ddz;
-        dm[0] += (ddx - x * dot) * il;
-        dm[1] += (ddy - y * dot) * il;
-        dm[2] += (ddz - z * dot) * il;
-    }
     dopacity[i] += go;
 
     // conic (A,B,C) = inverse of [[a,b],[b,c]]
@@ -396,16 +437,16 @@ extern "C" int gsr_preprocess(int32_t n, int32_t sh_degree, const float* mean, c
     if (cam->width <= 0 || cam->height <= 0) return GSR_EINVAL;
     Cam k = make_cam(*cam);
     int gx = (cam->width + tile_w - 1) / tile_w, gy = (cam->height + tile_h - 1) / tile_h;
-    const int blocks = (n + 255) / 256;
+    const int blocks = (n + kChunk - 1) / kChunk;
     cudaStream_t st = (cudaStream_t)stream;
     const int twl = ilog2(tile_w), thl = ilog2(tile_h);
     const bool vec = aligned16(feat);
 #define GSR_PRE(D)                                                                                          \
     do {                                                                                                    \
-        if (vec) preprocess_kernel<D, true><<<blocks, 256, 0, st>>>(n, mean, scale, quat, opacity, feat, k, \
+        if (vec) preprocess_kernel<D, true><<<blocks, kChunk, 0, st>>>(n, mean, scale, quat, opacity, feat, k, \
                                                                     gx, gy, twl, thl, splat2d, radius,      \
                                                                     grad2d_to_zero);                        \
-        else preprocess_kernel<D, false><<<blocks, 256, 0, st>>>(n, mean, scale, quat, opacity, feat, k,   \
+        else preprocess_kernel<D, false><<<blocks, kChunk, 0, st>>>(n, mean, scale, quat, opacity, feat, k,   \
                                                                  gx, gy, twl, thl, splat2d, radius,         \
                                                                  grad2d_to_zero);                           \
     } while (0)
@@ -438,10 +479,10 @@ extern "C" int gsr_backward_project(int32_t n, int32_t sh_degree, const float* m
     const bool vec = aligned16(feat) && aligned16(dfeat);
 #define GSR_BP(D)                                                                                            \
     do {                                                                                                     \
-        if (vec) backproject_kernel<D, true><<<blocks, 128, 0, st>>>(n, mean, scale, quat, feat, k, radius,  \
+        if (vec) backproject_kernel<D, true><<<blocks, kChunk, 0, st>>>(n, mean, scale, quat, feat, k, radius,  \
                                                                      grad2d, dmean, dscale, dquat, dopacity, \
                                                                      dfeat);                                 \
-        else backproject_kernel<D, false><<<blocks, 128, 0, st>>>(n, mean, scale, quat, feat, k, radius,    \
+        else backproject_kernel<D, false><<<blocks, kChunk, 0, st>>>(n, mean, scale, quat, feat, k, radius,    \
                                                                   grad2d, dmean, dscale, dquat, dopacity,   \
                                                                   dfeat);                                   \
     } while (0)
