@@ -354,6 +354,33 @@ def run_ours(args):
         a1.synchronize()
         red[name] = adds / (a0.elapsed_time(a1) / 1e3)
 
+    # divergent-destination accumulation (Sec. V-A1): plain atomics vs the
+    # serialized warp reduction (SW-S) vs the sorted segmented reduction
+    scat = {}
+    rng = np.random.default_rng(5)
+    n_items, rows = 1 << 22, 500_000
+    vals_t = torch.from_numpy(rng.normal(size=(n_items, 9)).astype(np.float32)).to(dev)
+    out_t = torch.zeros((rows, 12), device=dev)
+    for distinct in (1, 2, 4, 8, 32):
+        pools = rng.integers(0, rows, size=(n_items // 32, distinct))
+        pick = rng.integers(0, distinct, size=(n_items // 32, 32))
+        idx_np = np.take_along_axis(pools, pick, axis=1).reshape(-1).astype(np.int32)
+        idx_t = torch.from_numpy(idx_np).to(dev)
+        row = {}
+        for name, m, thr in (("plain", 0, 0), ("serial_thr2", 1, 2), ("serial_thr8", 1, 8), ("sorted", 2, 0)):
+            ts = []
+            for r in range(4):
+                flush()
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                gsr.gsr_scatter_add9(n_items, idx_t, vals_t, out_t, 12, m, thr)
+                a1.record(stream)
+                a1.synchronize()
+                if r:
+                    ts.append(a0.elapsed_time(a1))
+            row[name] = statistics.median(ts)
+        scat[str(distinct)] = row
+
     # end to end through host buffers: H2D of the step's inputs, D2H of the loss
     host_in = [t.detach().cpu().pin_memory() for t in sc.tensors()] + [target.cpu().pin_memory()]
     dev_in = sc.tensors() + [target]
@@ -436,6 +463,8 @@ def run_ours(args):
                 "hbm_gbs_best": alg_bytes / (t_best * 1e-3) / 1e9,
             },
             "l2_red_adds_per_s": red,
+            "divergent_accumulation_ms": {"items": n_items, "records": rows,
+                                          "by_distinct_destinations_per_warp": scat},
             "traffic_counts": {"P_active": p_active, "P_examined": p_exam, "P_ts": vb.n_keys,
                                "warp_steps": warp_steps, "warp_steps_after_cull": culled_in,
                                "warp_steps_after_cull_without_active_lane": culled_in_idle,

@@ -337,6 +337,27 @@ int gsr_adam_step(int64_t n, float* param, const float* grad, float* m, float* v
                   float beta1, float beta2, float eps, int32_t step, gsr_stream_t stream);
 
 /*
+ * Scatter-add of n records of 9 floats: out[idx[i]*stride + q] += vals[9*i + q]
+ * (q = 0..8) -- the gradient accumulation with arbitrary destinations, where
+ * the lanes of a warp may update different primitives.  method:
+ *   0 PLAIN  one atomic add per value (the baseline of Sec. III-A);
+ *   1 SERIAL the serialized warp reduction of Sec. V-A1 (SW-S): lanes with
+ *            equal destinations are grouped (match_any); groups of at least
+ *            `threshold` lanes are summed by their lowest lane, which pulls
+ *            the 9 values of each peer in turn and issues one red per value;
+ *            smaller groups use per-lane atomics;
+ *   2 SORTED the warp's destinations are sorted in registers (bitonic
+ *            network) and a segmented shuffle scan sums each run of equal
+ *            destinations, whose last lane issues one red per value
+ *            (threshold ignored).
+ * idx [n] (uint32 row indices), vals [n,9], out [rows,stride] (stride >= 9,
+ * accumulated).  Every method forms the same sums; only the float summation
+ * order differs.
+ */
+int gsr_scatter_add9(int64_t n, const uint32_t* idx, const float* vals, float* out, int32_t stride,
+                     int32_t method, int32_t threshold, gsr_stream_t stream);
+
+/*
  * Microbenchmark of the L2 atomic (red) path, the roofline of the PLAIN tier
  * (Sec. II-A: atomics are processed by the ROP units at the L2 slices).
  *   pattern 0: every lane adds to its own address (coalesced, distinct);

@@ -238,3 +238,11 @@ def render_scene(scene, cam, bg=(0.0, 0.0, 0.0), dL_dimage=None, tile=(16, 16), 
                  dL_dimage, tile, extras)
     out.update(pp=pp, keys=keys, point_list=pl, ranges=ranges)
     return out
+
+
+def scatter_add9(idx, vals, rows):
+    """FP64 scatter-add of 9-value records: out[idx[i]] += vals[i] (the plain
+    definition of the gradient accumulation with arbitrary destinations)."""
+    out = np.zeros((rows, 9))
+    np.add.at(out, np.asarray(idx, np.int64), np.asarray(vals, np.float64))
+    return out

@@ -1,0 +1,131 @@
+// Scatter-add of 9-value records with divergent destinations: the general
+// form of the gradient accumulation, where the lanes of a warp may update
+// different primitives (Sec. V-A1, the serialized reduction SW-S, used when
+// warps cannot be made to update a single primitive, e.g. Pulsar's spheres).
+#include "gsr_internal.cuh"
+
+namespace gsr {
+namespace {
+
+__device__ __forceinline__ void load9(const float* __restrict__ v, float* x) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) x[q] = v[q];
+}
+
+// PLAIN: one atomic add per parameter per item.
+// SERIAL: lanes with the same destination are found with match_any; a group
+//   of at least `threshold` lanes is summed by its lowest lane, which pulls
+//   each peer's 9 values in turn (all parameters per peer) and issues one red
+//   per parameter; smaller groups send per-lane atomics to L2.
+// SORTED: the warp's (destination, lane) pairs are sorted with a bitonic
+//   network in registers, each lane fetches the values of its sorted
+//   position, and a 5-step segmented shuffle scan leaves every group's total
+//   with the group's last lane, which issues the 9 reds.
+template <int METHOD>
+__global__ void __launch_bounds__(256)
+scatter9_kernel(long long n, const uint32_t* __restrict__ idx, const float* __restrict__ vals,
+                float* __restrict__ out, int stride, int threshold) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < n;
+    const uint32_t d = valid ? idx[i] : 0xffffffffu;
+    float x[9];
+    if (valid) load9(vals + 9 * i, x);
+    else
+#pragma unroll
+        for (int q = 0; q < 9; ++q) x[q] = 0.f;
+    if (METHOD == 0) {
+        if (valid) {
+            float* rec = out + (size_t)d * stride;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) atomicAdd(rec + q, x[q]);
+        }
+        return;
+    }
+    if (METHOD == 1) {
+        const unsigned act = __ballot_sync(kFull, valid);
+        const unsigned same = __match_any_sync(kFull, d) & act;
+        if (!valid) return;
+        float* rec = out + (size_t)d * stride;
+        if (__popc(same) >= threshold) {
+            const int leader = __ffs(same) - 1;
+            unsigned peers = same & ~(1u << leader);
+            // every lane of the group takes part in each pull (the same
+            // sequence of sources in the whole group), the leader keeps the sums
+            while (peers) {
+                const int src = __ffs(peers) - 1;
+                peers &= peers - 1u;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    const float y = __shfl_sync(same, x[q], src);
+                    if (lane == leader) x[q] += y;
+                }
+            }
+            if (lane == leader)
+#pragma unroll
+                for (int q = 0; q < 9; ++q) red_add(rec + q, x[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) atomicAdd(rec + q, x[q]);
+        }
+        return;
+    }
+    // METHOD 2: bitonic sort of (destination, source lane) over the warp
+    uint32_t key = d, src = (uint32_t)lane;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint32_t ok = __shfl_xor_sync(kFull, key, j);
+            const uint32_t os = __shfl_xor_sync(kFull, src, j);
+            const bool up = ((lane & k) == 0);
+            const bool lower = ((lane & j) == 0);
+            const bool take_min = (up == lower);
+            const bool other_smaller = (ok < key) || (ok == key && os < src);
+            if (take_min == other_smaller) {
+                key = ok;
+                src = os;
+            }
+        }
+    }
+    float y[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) y[q] = __shfl_sync(kFull, x[q], (int)src);
+    // segmented inclusive scan over runs of equal keys
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t kp = __shfl_up_sync(kFull, key, o);
+        const bool same_run = lane >= o && kp == key;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float t = __shfl_up_sync(kFull, y[q], o);
+            if (same_run) y[q] += t;
+        }
+    }
+    const uint32_t kn = __shfl_down_sync(kFull, key, 1);
+    const bool run_end = (lane == 31) || (kn != key);
+    if (run_end && key != 0xffffffffu) {
+        float* rec = out + (size_t)key * stride;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) red_add(rec + q, y[q]);
+    }
+}
+
+}  // namespace
+}  // namespace gsr
+
+using namespace gsr;
+
+extern "C" int gsr_scatter_add9(int64_t n, const uint32_t* idx, const float* vals, float* out, int32_t stride,
+                                int32_t method, int32_t threshold, gsr_stream_t stream) {
+    if (n < 0 || (n > 0 && (!idx || !vals || !out)) || stride < 9 || method < 0 || method > 2 || threshold < 0 ||
+        threshold > 33)
+        return GSR_EINVAL;
+    if (n == 0) return GSR_OK;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (method == 0) scatter9_kernel<0><<<blocks, 256, 0, s>>>(n, idx, vals, out, stride, threshold);
+    else if (method == 1) scatter9_kernel<1><<<blocks, 256, 0, s>>>(n, idx, vals, out, stride, threshold);
+    else scatter9_kernel<2><<<blocks, 256, 0, s>>>(n, idx, vals, out, stride, threshold);
+    return check_launch();
+}

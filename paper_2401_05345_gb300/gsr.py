@@ -102,11 +102,12 @@ def lib():
     L.gsr_activate.argtypes = [c_int64, P, P, P, P, P]
     L.gsr_activate_backward.argtypes = [c_int64, P, P, P, P, P, P, P]
     L.gsr_adam_step.argtypes = [c_int64, P, P, P, P, c_float, c_float, c_float, c_float, c_int32, P]
+    L.gsr_scatter_add9.argtypes = [c_int64, P, P, P, c_int32, c_int32, c_int32, P]
     L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
     for name in ("gsr_preprocess", "gsr_bin_scratch_bytes", "gsr_bin_sort", "gsr_bin_sort_static",
                  "gsr_forward", "gsr_backward",
                  "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red",
-                 "gsr_activate", "gsr_activate_backward"):
+                 "gsr_activate", "gsr_activate_backward", "gsr_scatter_add9"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -234,6 +235,15 @@ def gsr_activate_backward(n, scale, opacity, dscale, dopacity, dlog_scale, dopac
 def gsr_adam_step(n, param, grad, m, v, lr, beta1, beta2, eps, step, stream=None):
     _check("gsr_adam_step", lib().gsr_adam_step(n, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), lr, beta1,
                                                 beta2, eps, step, _stream(stream)))
+
+
+SCATTER_METHODS = {"plain": 0, "serial": 1, "sorted": 2}
+
+
+def gsr_scatter_add9(n, idx, vals, out, stride=GSR_REC, method="serial", threshold=2, stream=None):
+    m = SCATTER_METHODS[method] if isinstance(method, str) else int(method)
+    _check("gsr_scatter_add9", lib().gsr_scatter_add9(n, _ptr(idx), _ptr(vals), _ptr(out), stride, m, threshold,
+                                                      _stream(stream)))
 
 
 def gsr_bench_red(pattern, blocks, iters, buffer, stream=None) -> int:

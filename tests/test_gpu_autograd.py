@@ -123,7 +123,8 @@ def test_autograd_central_differences(dev, orc):
     """Central differences of the FP32 forward at eps = 1e-3 (absolute, as in
     gradcheck) and at eps/2; their spread measures the FD's own FP32 noise,
     and the analytic gradient must lie within that band plus 1 % plus the
-    quotient's FP32 rounding floor, 3 sqrt(2) eps32 ||w image|| / 2h.
+    quotient's FP32 rounding floor (3 eps32 times the weighted norm of the
+    pixels the step changes, over 2h).
     Parameters of visible Gaussians only.  Steps in which a discrete decision
     of the forward changes (list order, last contributor, active pairs) are
     not derivatives and are skipped; at least 25 entries must have an
@@ -136,10 +137,15 @@ def test_autograd_central_differences(dev, orc):
     img0 = model(st)
     (img0.double() * w).sum().backward()
     base = _decisions(model, cam, dev)
-    # FP32 rounding of every image value (independent, unit roundoff 2^-24)
-    # leaves each loss with noise ~ eps32 * ||w * image||; the central
-    # quotient's noise floor is sqrt(2) times that over 2h (3 sigma below)
-    rnd = 3 * np.sqrt(2) * 2.0 ** -24 * float(torch.linalg.norm(img0.detach().double() * w))
+
+    def rounding_floor(ip, im, h):
+        # the forward is deterministic: pixels the step does not change round
+        # identically and cancel; each changed pixel carries independent FP32
+        # rounding (unit roundoff 2^-24) in both evaluations -> 3 sigma of the
+        # central quotient's noise
+        ch = ip != im
+        nrm = float(torch.linalg.norm((ip.double() * w)[ch])) + float(torch.linalg.norm((im.double() * w)[ch]))
+        return 3 * 2.0 ** -24 * nrm / (2 * h)
     rng = np.random.default_rng(0)
     informative, checked, crossings = 0, 0, 0
     with torch.no_grad():
@@ -151,23 +157,24 @@ def test_autograd_central_differences(dev, orc):
             for gi in rng.choice(vis, 30, replace=False):
                 idx = int(gi) * per + int(rng.integers(per))
                 x0 = float(flat[idx])
-                fds, crossed = [], False
+                fds, crossed, floor = [], False, 0.0
                 for h in (1e-3, 5e-4):
                     flat[idx] = x0 + h
-                    lp = float((model(st).double() * w).sum())
+                    ip = model(st).detach()
                     crossed |= _decisions(model, cam, dev) != base
                     flat[idx] = x0 - h
-                    lm = float((model(st).double() * w).sum())
+                    im = model(st).detach()
                     crossed |= _decisions(model, cam, dev) != base
                     flat[idx] = x0
-                    fds.append((lp - lm) / (2 * h))
+                    fds.append(float(((ip.double() - im.double()) * w).sum()) / (2 * h))
+                    if h == 1e-3:
+                        floor = rounding_floor(ip, im, h)
                 if crossed:
                     crossings += 1
                     continue
                 an = float(g.reshape(-1)[idx])
                 band = abs(fds[0] - fds[1])
                 checked += 1
-                floor = rnd / (2 * 1e-3)
                 if band + floor < 0.2 * abs(an):
                     informative += 1
                 assert abs(fds[0] - an) <= 2 * band + 1e-2 * abs(an) + floor, (name, idx, fds, an, floor)

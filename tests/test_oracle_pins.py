@@ -520,3 +520,15 @@ def test_adam_first_steps_closed_form(orc):
     for step in (1, 2, 3):
         orc.adam(p, gr.copy(), m, v, lr, 0.9, 0.999, eps, step)
         np.testing.assert_allclose(p, p0 - step * lr * gr / (np.abs(gr) + eps), rtol=1e-9, atol=1e-12)
+
+
+def test_scatter_add_definition_by_brute_force(orc):
+    rng = np.random.default_rng(12)
+    idx = rng.integers(0, 7, size=200)
+    vals = rng.normal(size=(200, 9))
+    got = orc.scatter_add9(idx, vals, 7)
+    ref = np.zeros((7, 9))
+    for i, d in enumerate(idx):
+        for q in range(9):
+            ref[d, q] += vals[i, q]
+    np.testing.assert_allclose(got, ref, rtol=1e-14, atol=1e-14)
