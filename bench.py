@@ -334,6 +334,19 @@ def run_ours(args):
     t_block = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("block", 0, lay, True, ppt), reps, flush)
     t_recompute = autotune.time_backward(
         vb, bg, R.dimg, gsr.backward_opts(int(best.reduce_mode), int(best.threshold), lay, False, ppt), reps, flush)
+    # deterministic tier (no float atomics): backward + per-Gaussian reduction
+    det_ts = []
+    det_opts = gsr.backward_opts("warp", 0, lay, True, ppt)
+    vb.backward_deterministic(bg, R.dimg, det_opts)
+    for _ in range(reps):
+        flush()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        vb.backward_deterministic(bg, R.dimg, det_opts)
+        d1.record(stream)
+        d1.synchronize()
+        det_ts.append(d0.elapsed_time(d1))
+    t_det = statistics.median(det_ts)
     sweep = {}
     for thr in (4, 8, 12, 16, 20, 24, 28, 32):
         sweep[str(thr)] = autotune.time_backward(
@@ -450,6 +463,7 @@ def run_ours(args):
             "backward_raster": {
                 "ms_plain_atomicAdd": t_plain, "ms_warp": t_warp, "ms_block": t_block,
                 "ms_best": t_best, "best": best_name, "ms_best_recompute_T": t_recompute,
+                "ms_deterministic_no_atomics": t_det,
                 "speedup_best_vs_plain": t_plain / t_best,
                 "updates_per_s_plain": units / (t_plain / 1e3),
                 "updates_per_s_best": units / (t_best / 1e3),

@@ -273,6 +273,41 @@ int gsr_backward_batched(int32_t n_views, const gsr_view* views, const uint32_t*
                          gsr_stream_t stream);
 
 /*
+ * Per-Gaussian entry offsets of a binned view, for the deterministic tier:
+ * offsets[i] = number of (tile, Gaussian) list entries of Gaussians 0..i-1
+ * (exclusive scan of tiles touched, Gaussian order), offsets[n] = key count.
+ * The entries of Gaussian i occupy slots offsets[i] .. offsets[i+1]-1 in the
+ * row-major order of its tiles.  splat2d / radius as for gsr_bin_sort;
+ * offsets: device uint32 [n+1]; scratch >= gsr_entry_offsets_scratch_bytes.
+ */
+int gsr_entry_offsets_scratch_bytes(int32_t n, size_t* bytes);
+int gsr_entry_offsets(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                      const float* splat2d, const int32_t* radius, void* scratch, size_t scratch_bytes,
+                      uint32_t* offsets, gsr_stream_t stream);
+
+/*
+ * Deterministic backward: the same gradients as gsr_backward, formed without
+ * any float atomic, so the result is bit-identical from run to run whatever
+ * else runs on the GPU (the atomic buffering idea of Sec. VIII, "DAB", done
+ * in software).  Inside a tile every warp reduces its lanes (fixed shuffle
+ * tree) into its own shared-memory slot; the slots are combined in warp
+ * order and written to the entry's slot of `partial`; a second kernel sums
+ * each Gaussian's entries in slot order into grad2d (accumulated).
+ *   radius: from gsr_preprocess; entry_offsets: from gsr_entry_offsets (n+1);
+ *   partial: device float [entry_offsets[n] * 9] scratch; other arguments as
+ *   gsr_backward.  opts: lane_layout, store_T, pixels_per_thread are used
+ *   (reduce_mode and threshold are ignored: every active warp reduces).  The
+ *   bits of the result depend on lane_layout and pixels_per_thread (they fix
+ *   the summation order), not on scheduling.
+ */
+int gsr_backward_deterministic(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                               const uint32_t* tile_ranges, const uint32_t* point_list,
+                               const float* splat2d, const int32_t* radius, int32_t n,
+                               const uint32_t* entry_offsets, const float* bg, const float* final_T,
+                               const int32_t* n_contrib, const float* dL_dimage, float* partial,
+                               float* grad2d, const gsr_backward_opts* opts, gsr_stream_t stream);
+
+/*
  * Traversal statistics of gsr_backward (nothing else is written): walks the
  * same lists as the backward with the same skip tests and fills the
  * device array hist[38] (uint64, zeroed first):

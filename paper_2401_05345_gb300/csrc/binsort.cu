@@ -341,6 +341,33 @@ extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t ti
     return GSR_OK;
 }
 
+extern "C" int gsr_entry_offsets_scratch_bytes(int32_t n, size_t* bytes) {
+    if (n < 0 || !bytes) return GSR_EINVAL;
+    size_t b = 0;
+    cudaError_t e = cub::DeviceScan::ExclusiveSum(nullptr, b, (uint32_t*)nullptr, (uint32_t*)nullptr, n + 1);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *bytes = b > 0 ? b : 1;
+    return GSR_OK;
+}
+
+extern "C" int gsr_entry_offsets(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                                 const float* splat2d, const int32_t* radius, void* scratch, size_t scratch_bytes,
+                                 uint32_t* offsets, gsr_stream_t stream_) {
+    BinGeom g;
+    if (n < 0 || !offsets || !scratch || !make_geom(width, height, tile_w, tile_h, g)) return GSR_EINVAL;
+    if (n > 0 && (!splat2d || !radius || !aligned16(splat2d))) return GSR_EINVAL;
+    size_t need = 0;
+    int rc = gsr_entry_offsets_scratch_bytes(n, &need);
+    if (rc != GSR_OK) return rc;
+    if (scratch_bytes < need) return GSR_ESCRATCH;
+    cudaStream_t s = (cudaStream_t)stream_;
+    count_kernel<<<(n + 1 + 255) / 256, 256, 0, s>>>(n, splat2d, radius, g, offsets);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    size_t tb = scratch_bytes;
+    cudaError_t e = cub::DeviceScan::ExclusiveSum(scratch, tb, offsets, offsets, n + 1, s);
+    return e == cudaSuccess ? GSR_OK : cuda_fail(e);
+}
+
 // ----------------------------------------------------------------------------
 // Allocation-free variant of gsr_bin_sort.
 //

@@ -120,6 +120,52 @@ stats_kernel(BwdArgs p, unsigned long long* __restrict__ hist) {
         if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
 }
 
+template <class SH, bool STORE_T>
+__global__ void __launch_bounds__(SH::NT)
+backward_det_kernel(BwdArgs p) {
+    __shared__ BwdSmem<SH::B, kModeDet> sm;
+    extern __shared__ float s_dyn[];
+    DetSmem det;
+    det.part = s_dyn;
+    det.wflags = reinterpret_cast<unsigned*>(s_dyn + SH::NW * SH::B * 9);
+    det.slot = det.wflags + SH::B;
+    backward_tile<SH, kModeDet, STORE_T>(p, blockIdx.x, sm, det);
+}
+
+// grad2d[i] += sum of Gaussian i's entry partials, in slot (tile) order.
+__global__ void entries_reduce_kernel(int n, const uint32_t* __restrict__ off, const float* __restrict__ partial,
+                                      float* __restrict__ grad2d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t e0 = off[i], e1 = off[i + 1];
+    if (e0 == e1) return;
+    float acc[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = 0.0f;
+    for (uint32_t e = e0; e < e1; ++e)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] += partial[9 * (size_t)e + q];
+    float* rec = grad2d + (size_t)i * GSR_REC;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) rec[q] += acc[q];
+}
+
+template <class SH, bool STORE_T>
+int launch_det(int tiles, const BwdArgs& a, cudaStream_t s) {
+    constexpr size_t dyn = sizeof(float) * SH::NW * SH::B * 9 + 2 * sizeof(uint32_t) * SH::B;
+    auto k = backward_det_kernel<SH, STORE_T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return cuda_fail(e);
+    k<<<tiles, SH::NT, dyn, s>>>(a);
+    return check_launch();
+}
+
+template <int LAYOUT, int PPT>
+int launch_det_store(bool store, int tiles, const BwdArgs& a, cudaStream_t s) {
+    using SH = Shape<16, 16, LAYOUT, PPT>;
+    return store ? launch_det<SH, true>(tiles, a, s) : launch_det<SH, false>(tiles, a, s);
+}
+
 template <int MODE, int LAYOUT, int PPT, bool STORE_T>
 void launch_bwd(int tiles, const BwdArgs& a, cudaStream_t s) {
     using SH = Shape<16, 16, LAYOUT, PPT>;
@@ -231,5 +277,48 @@ extern "C" int gsr_backward_stats(int32_t width, int32_t height, int32_t tile_w,
     const int tiles = a.g.gx * a.g.gy;
     if (lane_layout == 0) stats_kernel<Shape<16, 16, 0, 1>><<<tiles, 256, 0, s>>>(a, (unsigned long long*)hist);
     else stats_kernel<Shape<16, 16, 1, 1>><<<tiles, 256, 0, s>>>(a, (unsigned long long*)hist);
+    return check_launch();
+}
+
+extern "C" int gsr_backward_deterministic(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                                          const uint32_t* tile_ranges, const uint32_t* point_list,
+                                          const float* splat2d, const int32_t* radius, int32_t n,
+                                          const uint32_t* entry_offsets, const float* bg, const float* final_T,
+                                          const int32_t* n_contrib, const float* dL_dimage, float* partial,
+                                          float* grad2d, const gsr_backward_opts* opts, gsr_stream_t stream_) {
+    gsr_backward_opts o = {GSR_REDUCE_WARP, 0, 1, 1, 2, {0, 0, 0}};
+    if (opts) o = *opts;
+    if (width <= 0 || height <= 0 || n < 0 || !tile_ranges || !splat2d || !bg || !dL_dimage || !grad2d)
+        return GSR_EINVAL;
+    if (n > 0 && (!radius || !entry_offsets || !partial || !point_list)) return GSR_EINVAL;
+    if (!aligned16(splat2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
+    if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
+    if ((o.lane_layout != 0 && o.lane_layout != 1) || (o.store_T != 0 && o.store_T != 1)) return GSR_EINVAL;
+    if (o.pixels_per_thread < 0 || o.pixels_per_thread > 2) return GSR_EINVAL;
+    if (o.store_T && (!final_T || !n_contrib)) return GSR_EINVAL;
+    if (n == 0) return GSR_OK;
+    BwdArgs a = {};
+    a.g = RasterGeom{width, height, (width + 15) / 16, (height + 15) / 16};
+    a.ranges = reinterpret_cast<const uint2*>(tile_ranges);
+    a.point_list = point_list;
+    a.splat2d = splat2d;
+    a.bg0 = bg[0]; a.bg1 = bg[1]; a.bg2 = bg[2];
+    a.final_T = final_T;
+    a.n_contrib = n_contrib;
+    a.dL_dimage = dL_dimage;
+    a.grad2d = grad2d;
+    a.radius = radius;
+    a.entry_off = entry_offsets;
+    a.partial = partial;
+    const int tiles = a.g.gx * a.g.gy;
+    cudaStream_t s = (cudaStream_t)stream_;
+    const bool st = o.store_T != 0;
+    int rc;
+    if (o.pixels_per_thread == 2)
+        rc = o.lane_layout ? launch_det_store<1, 2>(st, tiles, a, s) : launch_det_store<0, 2>(st, tiles, a, s);
+    else
+        rc = o.lane_layout ? launch_det_store<1, 1>(st, tiles, a, s) : launch_det_store<0, 1>(st, tiles, a, s);
+    if (rc != GSR_OK) return rc;
+    entries_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, entry_offsets, partial, grad2d);
     return check_launch();
 }

@@ -176,7 +176,32 @@ struct BwdArgs {
     const float* dL_dimage;
     float* grad2d;
     int threshold;
+    // deterministic tier only
+    const int* radius;
+    const uint32_t* entry_off;
+    float* partial;
 };
+
+// Deterministic tier: per-warp partial sums are combined in warp order and
+// written, without atomics, to one 9-float slot per (tile, splat) list entry.
+constexpr int kModeDet = 4;
+
+// Shared arrays of the deterministic tier (dynamic shared memory).
+struct DetSmem {
+    float* part;        // [warps][B][9] per-warp partial sums of the batch
+    unsigned* wflags;   // [B] warps that wrote a partial for entry k
+    uint32_t* slot;     // [B] entry slot of staged entry k
+};
+
+// Slot of the (tile, Gaussian) entry in the per-Gaussian layout: the
+// Gaussian's first slot plus the tile's row-major rank inside its rectangle
+// (the order binning emits the entries in).
+__device__ __forceinline__ uint32_t entry_slot(const BwdArgs& p, uint32_t id, float u, float v, int tile) {
+    int x0, x1, y0, y1;
+    tile_rect(u, v, p.radius[id], p.g.gx, p.g.gy, 4, 4, x0, x1, y0, y1);
+    const int tx = tile % p.g.gx, ty = tile / p.g.gx;
+    return p.entry_off[id] + (uint32_t)((ty - y0) * (x1 - x0) + (tx - x0));
+}
 
 template <int B, int MODE>
 struct BwdSmem {
@@ -217,7 +242,8 @@ __device__ __forceinline__ void pair_grads(const SplatEval& e, float4 a, float4 
 // tile's pixels, accumulated by the tier MODE.  All threads of the CTA call
 // it; shared storage is reused across calls.
 template <class SH, int MODE, bool STORE_T>
-__device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, BwdSmem<SH::B, MODE>& sm) {
+__device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, BwdSmem<SH::B, MODE>& sm,
+                                              DetSmem det = DetSmem{nullptr, nullptr, nullptr}) {
     constexpr int B = SH::B, NT = SH::NT;
     constexpr int PPT = B / NT;
     static_assert(MODE != GSR_REDUCE_PLAIN || PPT == 1, "the plain tier keeps one pixel per thread");
@@ -277,12 +303,27 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
     const int maxlast = sm.maxlast;
     const int rparam = reduce9_param(lane);
     float* __restrict__ grad = p.grad2d;
+    if (MODE == kModeDet) {
+        // entries no pixel of the tile reaches still get their (zero) slot
+        for (int q = maxlast + tid; q < nlist; q += NT) {
+            const uint32_t id = p.point_list[rg.x + (uint32_t)q];
+            const float2 uv = *reinterpret_cast<const float2*>(p.splat2d + (size_t)id * GSR_REC);
+            float* dst = p.partial + 9 * (size_t)entry_slot(p, id, uv.x, uv.y, tile);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) dst[i] = 0.0f;
+        }
+    }
 
     for (int top = maxlast; top > 0; top -= B) {
         const int cnt = min(B, top);
         __syncthreads();
         stage_batch<SH, true, true>(cnt, [&](int e) { return rg.x + (uint32_t)(top - 1 - e); }, p.point_list,
                                     p.splat2d, ox, oy, sm.a, sm.b, sm.c, sm.id, sm.mask);
+        if (MODE == kModeDet)
+            for (int e = tid; e < cnt; e += NT) {  // entries this thread staged
+                det.wflags[e] = 0u;
+                det.slot[e] = entry_slot(p, sm.id[e], sm.a[e].x, sm.a[e].y, tile);
+            }
         __syncthreads();
         // each warp visits, back to front, only the staged splats whose
         // alpha >= 1/255 region touches its pixel block and that lie before
@@ -314,7 +355,12 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                     any |= act;
                 }
                 float* rec = grad + (size_t)sm.id[k] * GSR_REC;
-                if (MODE == GSR_REDUCE_PLAIN) {
+                if (MODE == kModeDet) {
+                    if (__ballot_sync(kFull, any) == 0u) continue;
+                    const float z = reduce9(v, lane);
+                    if (rparam < 9) det.part[(warp * B + k) * 9 + rparam] = z;
+                    if (lane == 0) atomicOr(&det.wflags[k], 1u << warp);
+                } else if (MODE == GSR_REDUCE_PLAIN) {
                     if (any) {
 #pragma unroll
                         for (int i = 0; i < 9; ++i) atomicAdd(rec + i, v[i]);
@@ -337,6 +383,19 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                         }
                     }
                 }
+            }
+        }
+        if (MODE == kModeDet) {
+            // warp partials combined in warp order: a fixed summation order
+            __syncthreads();
+            for (int i = tid; i < cnt * 9; i += NT) {
+                const int k = i / 9, q = i - 9 * k;
+                const unsigned fl = det.wflags[k];
+                float sum = 0.0f;
+#pragma unroll
+                for (int w = 0; w < SH::NW; ++w)
+                    if ((fl >> w) & 1u) sum += det.part[(w * B + k) * 9 + q];
+                p.partial[9 * (size_t)det.slot[k] + q] = sum;
             }
         }
         if (MODE == GSR_REDUCE_BLOCK) {

@@ -102,12 +102,17 @@ def lib():
     L.gsr_activate.argtypes = [c_int64, P, P, P, P, P]
     L.gsr_activate_backward.argtypes = [c_int64, P, P, P, P, P, P, P]
     L.gsr_adam_step.argtypes = [c_int64, P, P, P, P, c_float, c_float, c_float, c_float, c_int32, P]
+    L.gsr_entry_offsets_scratch_bytes.argtypes = [c_int32, POINTER(c_size_t)]
+    L.gsr_entry_offsets.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, P, c_size_t, P, P]
+    L.gsr_backward_deterministic.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, P, c_int32, P,
+                                             POINTER(c_float), P, P, P, P, P, POINTER(BackwardOpts), P]
     L.gsr_scatter_add9.argtypes = [c_int64, P, P, P, c_int32, c_int32, c_int32, P]
     L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
     for name in ("gsr_preprocess", "gsr_bin_scratch_bytes", "gsr_bin_sort", "gsr_bin_sort_static",
                  "gsr_forward", "gsr_backward",
                  "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red",
-                 "gsr_activate", "gsr_activate_backward", "gsr_scatter_add9"):
+                 "gsr_activate", "gsr_activate_backward", "gsr_scatter_add9", "gsr_entry_offsets_scratch_bytes",
+                 "gsr_entry_offsets", "gsr_backward_deterministic"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -197,6 +202,28 @@ def gsr_backward(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d
                                               _ptr(point_list), _ptr(splat2d), _f3(bg), _ptr(final_T),
                                               _ptr(n_contrib), _ptr(dL_dimage), _ptr(grad2d),
                                               ctypes.byref(o), _stream(stream)))
+
+
+def gsr_entry_offsets_scratch_bytes(n) -> int:
+    out = c_size_t(0)
+    _check("gsr_entry_offsets_scratch_bytes", lib().gsr_entry_offsets_scratch_bytes(n, ctypes.byref(out)))
+    return int(out.value)
+
+
+def gsr_entry_offsets(n, width, height, tile_w, tile_h, splat2d, radius, scratch, offsets, stream=None):
+    _check("gsr_entry_offsets", lib().gsr_entry_offsets(n, width, height, tile_w, tile_h, _ptr(splat2d), _ptr(radius),
+                                                        _ptr(scratch), scratch.numel() * scratch.element_size(),
+                                                        _ptr(offsets), _stream(stream)))
+
+
+def gsr_backward_deterministic(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, radius, n,
+                               entry_offsets, bg, final_T, n_contrib, dL_dimage, partial, grad2d, opts=None,
+                               stream=None):
+    o = opts if opts is not None else backward_opts("warp", 0, 1, True, 2)
+    _check("gsr_backward_deterministic", lib().gsr_backward_deterministic(
+        width, height, tile_w, tile_h, _ptr(tile_ranges), _ptr(point_list), _ptr(splat2d), _ptr(radius), n,
+        _ptr(entry_offsets), _f3(bg), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage), _ptr(partial), _ptr(grad2d),
+        ctypes.byref(o), _stream(stream)))
 
 
 def gsr_backward_stats(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, n_contrib, hist,

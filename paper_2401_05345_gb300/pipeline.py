@@ -117,6 +117,21 @@ class ViewBuffers:
         gsr.gsr_backward(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
                          bg, self.final_T, self.n_contrib, dL_dimage, self.grad2d, opts, stream)
 
+    def backward_deterministic(self, bg, dL_dimage, opts=None, stream=None):
+        """Backward without float atomics (bit-identical run to run); keeps
+        its per-entry partial buffer between calls."""
+        nk = max(self.n_keys, 1)
+        if getattr(self, "_det_partial", None) is None or self._det_partial.numel() < 9 * nk:
+            self._det_partial = torch.empty(9 * nk + 1024, dtype=torch.float32, device=self.device)
+            self._det_offsets = torch.empty(self.n + 1, dtype=torch.int32, device=self.device)
+            self._det_scratch = torch.empty(gsr.gsr_entry_offsets_scratch_bytes(self.n), dtype=torch.uint8,
+                                            device=self.device)
+        gsr.gsr_entry_offsets(self.n, self.W, self.H, self.tw, self.th, self.splat2d, self.radius, self._det_scratch,
+                              self._det_offsets, stream)
+        gsr.gsr_backward_deterministic(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list,
+                                       self.splat2d, self.radius, self.n, self._det_offsets, bg, self.final_T,
+                                       self.n_contrib, dL_dimage, self._det_partial, self.grad2d, opts, stream)
+
     def backward_project(self, sc: SceneTensors, grads: SceneTensors, stream=None):
         gsr.gsr_backward_project(self.n, sc.sh_degree, sc.mean, sc.scale, sc.quat, sc.opacity, sc.feat,
                                  self.c_cam, self.radius, self.grad2d, grads.mean, grads.scale, grads.quat,
@@ -129,9 +144,10 @@ class Renderer:
     L1 loss gradient, backward blend with gradient accumulation, backward
     projection."""
 
-    def __init__(self, n, cam, device="cuda", opts=None, store_T=True, key_capacity=None):
+    def __init__(self, n, cam, device="cuda", opts=None, store_T=True, key_capacity=None, deterministic=False):
         self.vb = ViewBuffers(n, cam, device, key_capacity, store_T)
         self.opts = opts if opts is not None else gsr.backward_opts("warp", 0, 0, store_T)
+        self.deterministic = deterministic
         self.dimg = torch.zeros_like(self.vb.image)
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
 
@@ -148,7 +164,10 @@ class Renderer:
         gsr.gsr_l1_loss(vb.image.numel(), vb.image, target, self.dimg, self.loss, stream)
         if on_backward:
             on_backward(True)
-        vb.backward(bg, self.dimg, self.opts, stream)
+        if self.deterministic:
+            vb.backward_deterministic(bg, self.dimg, self.opts, stream)
+        else:
+            vb.backward(bg, self.dimg, self.opts, stream)
         if on_backward:
             on_backward(False)
         vb.backward_project(sc, grads, stream)

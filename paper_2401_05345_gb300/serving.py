@@ -249,7 +249,7 @@ def job_footprint(n, sh_degree, width, height, keys_per_gaussian=16):
 class GpuExecutor:
     """Runs job steps on CUDA streams through libgsr."""
 
-    def __init__(self, device, slots, opts, lr=1e-3, bg=(0.0, 0.0, 0.0)):
+    def __init__(self, device, slots, opts, lr=1e-3, bg=(0.0, 0.0, 0.0), deterministic=False):
         import torch
 
         from . import gsr, pipeline
@@ -257,6 +257,7 @@ class GpuExecutor:
         self.device = device
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.opts = opts
+        self.deterministic = deterministic
         self.lr = lr
         self.bg = bg
         self.t0_event = torch.cuda.Event(enable_timing=True)
@@ -321,7 +322,10 @@ class GpuExecutor:
             st["loss"].zero_()
             tgt = st["targets"][step % len(st["targets"])]
             gsr.gsr_l1_loss(vb.image.numel(), vb.image, tgt, st["dimg"], st["loss"], s)
-            vb.backward(self.bg, st["dimg"], self.opts, s)
+            if self.deterministic:
+                vb.backward_deterministic(self.bg, st["dimg"], self.opts, s)
+            else:
+                vb.backward(self.bg, st["dimg"], self.opts, s)
             st["G"].zero_()
             st["dscale"].zero_()
             st["dopac"].zero_()
@@ -359,8 +363,9 @@ def make_jobs(spec, seed=0):
     return jobs
 
 
-def run_serving(spec, slots, budget_bytes, opts, rate_per_job, seed=0, device="cuda", jobs=None):
-    ex = GpuExecutor(device, slots, opts)
+def run_serving(spec, slots, budget_bytes, opts, rate_per_job, seed=0, device="cuda", jobs=None,
+                deterministic=False):
+    ex = GpuExecutor(device, slots, opts, deterministic=deterministic)
     jobs = jobs if jobs is not None else make_jobs(spec, seed)
     for j in jobs:
         j.state, j.done_steps, j.busy = "waiting", 0, False

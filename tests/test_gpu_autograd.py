@@ -124,7 +124,7 @@ def test_autograd_central_differences(dev, orc):
     gradcheck) and at eps/2; their spread measures the FD's own FP32 noise,
     and the analytic gradient must lie within that band plus 1 % plus the
     quotient's FP32 rounding floor (3 eps32 times the weighted norm of the
-    pixels the step changes, over 2h).
+    perturbed Gaussian's footprint pixels, over 2h).
     Parameters of visible Gaussians only.  Steps in which a discrete decision
     of the forward changes (list order, last contributor, active pairs) are
     not derivatives and are skipped; at least 25 entries must have an
@@ -138,13 +138,18 @@ def test_autograd_central_differences(dev, orc):
     (img0.double() * w).sum().backward()
     base = _decisions(model, cam, dev)
 
-    def rounding_floor(ip, im, h):
-        # the forward is deterministic: pixels the step does not change round
-        # identically and cancel; each changed pixel carries independent FP32
-        # rounding (unit roundoff 2^-24) in both evaluations -> 3 sigma of the
-        # central quotient's noise
-        ch = ip != im
-        nrm = float(torch.linalg.norm((ip.double() * w)[ch])) + float(torch.linalg.norm((im.double() * w)[ch]))
+    pp = orc.preprocess(scene, cam)
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+
+    def rounding_floor(gi, ip, im, h):
+        # the forward is deterministic: only pixels inside the perturbed
+        # Gaussian's footprint (u, v +- radius) can change; each carries
+        # independent FP32 rounding (unit roundoff 2^-24) in both evaluations,
+        # and changes below it round away -> 3 sigma of the quotient's noise
+        u, v = pp["uv"][gi]
+        r = pp["radius"][gi] + 1
+        fp = torch.from_numpy((np.abs(xs - u) <= r) & (np.abs(ys - v) <= r)).to(dev)[None].expand_as(ip)
+        nrm = float(torch.linalg.norm((ip.double() * w)[fp])) + float(torch.linalg.norm((im.double() * w)[fp]))
         return 3 * 2.0 ** -24 * nrm / (2 * h)
     rng = np.random.default_rng(0)
     informative, checked, crossings = 0, 0, 0
@@ -168,7 +173,7 @@ def test_autograd_central_differences(dev, orc):
                     flat[idx] = x0
                     fds.append(float(((ip.double() - im.double()) * w).sum()) / (2 * h))
                     if h == 1e-3:
-                        floor = rounding_floor(ip, im, h)
+                        floor = rounding_floor(int(gi), ip, im, h)
                 if crossed:
                     crossings += 1
                     continue

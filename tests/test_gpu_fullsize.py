@@ -175,3 +175,25 @@ def test_fullsize_backward_projection(dev, orc, full):
     for key, got, mag in (("dmean", dm, "dmean_mag"), ("dscale", ds, "dscale_mag"), ("dquat", dq, "dquat_mag"),
                           ("dfeat", df, "dfeat_mag")):
         check_scaled(key, N(got)[ok], ref[key].reshape(n, -1)[ok], ref[mag].reshape(n, -1)[ok])
+
+
+def test_fullsize_deterministic_backward(dev, full):
+    cam = full["cam"]
+    image, fT, nc, ranges, pl, splat = _forward(dev, full)
+    n = full["scene"].n
+    radius = T(full["radius"])
+    off = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+    scr = torch.empty(gsr.gsr_entry_offsets_scratch_bytes(n), dtype=torch.uint8, device=dev)
+    gsr.gsr_entry_offsets(n, cam.width, cam.height, 16, 16, splat, radius, scr, off)
+    nk = int(off[n])
+    partial = torch.empty(9 * nk, device=dev)
+    res = []
+    for _ in range(2):
+        grad = torch.zeros((n, 12), device=dev)
+        gsr.gsr_backward_deterministic(cam.width, cam.height, 16, 16, ranges, pl, splat, radius, n, off, BG, fT, nc,
+                                       T(full["g"]), partial, grad, gsr.backward_opts("warp", 0, 1, True, 2))
+        res.append(N(grad))
+    np.testing.assert_array_equal(res[0], res[1])
+    s = full["splats"]
+    out = full["out"]
+    check_scaled("grad2d deterministic", res[0][s, :9], out["grad2d"][s], out["gscale"][s], out["gallow"][s])

@@ -377,3 +377,34 @@ def test_unaligned_features_take_the_scalar_path(dev):
         outs.append((N(splat), N(radius), N(df), N(dm)))
     for a, b in zip(outs[0], outs[1]):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("ppt,layout", [(1, 0), (1, 1), (2, 0), (2, 1)])
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_deterministic_backward_matches_oracle_and_repeats_bitwise(dev, orc, name, ppt, layout):
+    """The atomic-free tier: oracle parity, and the same bits on every run and
+    whether T is stored or recomputed."""
+    st_ = oracle_stage(orc, name, (0.3, 0.7, 0.1))
+    cam = st_["cam"]
+    W, H = cam.width, cam.height
+    f = gpu_forward(dev, st_)
+    n = len(st_["rec"])
+    radius = T(st_["radius"])
+    off = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+    scr = torch.empty(gsr.gsr_entry_offsets_scratch_bytes(n), dtype=torch.uint8, device=dev)
+    gsr.gsr_entry_offsets(n, W, H, 16, 16, f["splat"], radius, scr, off)
+    nk = int(off[n])
+    assert nk == len(st_["pl"])
+    partial = torch.full((9 * nk + 9,), float("nan"), device=dev)   # every slot must be written
+    outs = []
+    for store_T in (True, True, False):
+        grad = torch.zeros((n, 12), device=dev)
+        gsr.gsr_backward_deterministic(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], radius, n, off, st_["bg"],
+                                       f["final_T"] if store_T else None, f["n_contrib"] if store_T else None,
+                                       T(st_["g"]), partial, grad, gsr.backward_opts("warp", 0, layout, store_T, ppt))
+        outs.append(N(grad))
+    out = st_["out"]
+    check_scaled(f"{name} deterministic", outs[0][:, :9], out["grad2d"], out["gscale"], out["gallow"])
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+    assert not np.isnan(N(partial)[:9 * nk]).any()

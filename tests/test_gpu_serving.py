@@ -47,3 +47,19 @@ def test_each_job_same_alone_and_in_the_mix(dev):
         np.testing.assert_allclose(lm, la, rtol=1e-5)
         pa, pm = ex1.final_params[j.job_id], ex.final_params[j.job_id]
         assert np.all(np.abs(pm - pa) <= 1e-5 * np.abs(pa) + 1e-3 * lr * j.steps)
+
+
+def test_deterministic_tier_gives_bitwise_equal_jobs_alone_and_in_the_mix(dev):
+    """With the atomic-free backward every step of a job is bit-identical
+    whatever runs beside it: final parameters are equal bit for bit."""
+    spec = [(20000, 3, 0.0, 160, 120), (30000, 3, 0.005, 200, 150), (25000, 3, 0.01, 160, 120)]
+    jobs = SV.make_jobs(spec, seed=3)
+    fps = sorted(j.footprint for j in jobs)
+    opts = gsr.backward_opts("warp", 0, 1, True, 2)
+    _, _, ex, sch = SV.run_serving(None, 3, fps[-1] + fps[-2] + 1, opts, 400.0, seed=3, device=dev, jobs=jobs,
+                                   deterministic=True)
+    for j in jobs:
+        alone = dataclasses.replace(j, state="waiting", done_steps=0, busy=False)
+        _, _, ex1, _ = SV.run_serving(None, 1, j.footprint, opts, 400.0, seed=3, device=dev, jobs=[alone],
+                                      deterministic=True)
+        np.testing.assert_array_equal(ex1.final_params[j.job_id], ex.final_params[j.job_id])
