@@ -220,7 +220,7 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("raster.cu", "gsr_internal.cuh"):
+    for f in ("raster.cu", "raster_common.cuh", "gsr_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2401_05345_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -270,7 +270,7 @@ def run_ours(args):
 
     # plain atomicAdd vs reduced tiers, backward kernel alone (untimed for the step)
     if args.profile:
-        best = gsr.backward_opts("hybrid", 12, 1, True, 2)
+        best = autotune.parse_opts_name(args.opts)
         tune_table, t_plain = {}, None
     else:
         tr = autotune.tune(vb, bg, R.dimg, reps=3, flush=flush)
@@ -320,9 +320,20 @@ def run_ours(args):
     bwd_ms = [b0.elapsed_time(b1) for (_, _, b0, b1) in ev]
     tot_ms = sum(step_ms)
     if args.profile:
+        tiers = []
+        if args.profile_tiers:
+            # one backward launch per autotune candidate, in this order, for a
+            # per-tier DRAM traffic capture
+            for o in autotune.default_candidates():
+                vb.backward(bg, R.dimg, o)
+                tiers.append(autotune.opts_name(o))
+            torch.cuda.synchronize()
         if rank == 0:
             print(json.dumps({"profile_run": True, "ms_per_step": tot_ms / args.steps,
-                              "backward_ms": statistics.mean(bwd_ms), "opts": best_name}), flush=True)
+                              "backward_ms": statistics.mean(bwd_ms), "opts": best_name,
+                              "kernel_hash": kernel_source_hash(),
+                              "backward_launches_before_tiers": 1 + args.warmup + args.steps,
+                              "tier_order": tiers}), flush=True)
         return 0
 
     # backward kernel alone: plain atomicAdd vs the reduced tiers
@@ -347,6 +358,24 @@ def run_ours(args):
         d1.synchronize()
         det_ts.append(d0.elapsed_time(d1))
     t_det = statistics.median(det_ts)
+    # binning: the hand-written sorts against the same binning through CUB
+    def time_bin(library):
+        sb = gsr.gsr_bin_scratch_bytes(vb.n, vb.W, vb.H, 16, 16, vb.key_capacity, library=library)
+        scr = torch.empty(sb, dtype=torch.uint8, device=dev)
+        ts = []
+        for r in range(reps + 1):
+            flush()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            gsr.gsr_bin_sort(vb.n, vb.W, vb.H, 16, 16, vb.splat2d, vb.radius, vb.key_capacity, scr, vb.point_list,
+                             vb.tile_ranges, None, stream, library=library)
+            a1.record(stream)
+            a1.synchronize()
+            if r:
+                ts.append(a0.elapsed_time(a1))
+        return statistics.median(ts)
+    t_bin_lib = time_bin(True)
+    t_bin_own = time_bin(False)
     sweep = {}
     for thr in (4, 8, 12, 16, 20, 24, 28, 32):
         sweep[str(thr)] = autotune.time_backward(
@@ -476,6 +505,8 @@ def run_ours(args):
                 "algorithmic_bytes_best": alg_bytes,
                 "hbm_gbs_best": alg_bytes / (t_best * 1e-3) / 1e9,
             },
+            "binning_ms": {"hand_written_sorts": t_bin_own, "cub_radix_sorts": t_bin_lib,
+                           "note": "same outputs; each includes its one host sync for the key count"},
             "l2_red_adds_per_s": red,
             "divergent_accumulation_ms": {"items": n_items, "records": rows,
                                           "by_distinct_destinations_per_warp": scat},
@@ -516,6 +547,9 @@ def main():
     ap.add_argument("--cpu-samples", type=int, default=4, help="oracle samples for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu)")
+    ap.add_argument("--opts", default="hybrid-thr16-lay1-ppt2", help="backward tier of a --profile run")
+    ap.add_argument("--profile-tiers", action="store_true",
+                    help="--profile: then one backward launch per autotune candidate")
     args = ap.parse_args()
     if args.warmup < 3 and not args.profile:
         ap.error("--warmup must be >= 3")

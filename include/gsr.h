@@ -155,25 +155,45 @@ int gsr_bin_scratch_bytes(int32_t n, int32_t width, int32_t height, int32_t tile
                           int32_t tile_h, int64_t key_capacity, size_t* bytes);
 
 /*
- * Tile binning: one key (tile_id << 32 | FP32 bits of depth) per (tile,
- * Gaussian) pair in each visible Gaussian's tile rectangle, emitted in
- * Gaussian order; stable LSD radix sort; per-tile [start, end) ranges.  This
+ * Tile binning: the entries (tile_id << 32 | FP32 bits of depth, Gaussian
+ * id) of every (tile, Gaussian) pair in each visible Gaussian's tile
+ * rectangle, in the order of a stable sort of the keys emitted in Gaussian
+ * order (tile, then depth, then id), and per-tile [start, end) ranges.  This
  * builds the "per-pixel list of primitives" that the gradient computation
  * iterates (Sec. III-A): all pixels of a tile share one depth-sorted list.
+ * Computed by hand-written sorts: a stable 3-pass LSD radix sort of the
+ * Gaussians' depth keys, then a counting sort that writes each tile's
+ * entries in that order (no key array is sorted).
  *   splat2d, radius: from gsr_preprocess.  scratch: scratch_bytes >=
  *   gsr_bin_scratch_bytes().  Outputs: point_list [key_capacity] (Gaussian
  *   ids, first *n_keys valid), tile_ranges [gx*gy*2] (uint32 start, end;
  *   0,0 for empty tiles), keys_out [key_capacity] (optional: sorted keys).
  *   n_keys: HOST pointer, receives the key count.
  * Synchronises `stream` once to read the key count.  Returns GSR_ECAPACITY
- * (with *n_keys set, nothing else written) when the count exceeds
- * key_capacity: the caller grows the buffers and calls again.
+ * (with *n_keys set, tile_ranges written, nothing else) when the count
+ * exceeds key_capacity: the caller grows the buffers and calls again.
+ * A tile grid with 65536 or more tiles per side is GSR_EINVAL.
  */
 int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                  const float* splat2d, const int32_t* radius, int64_t key_capacity,
                  void* scratch, size_t scratch_bytes, uint32_t* point_list,
                  uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,
                  gsr_stream_t stream);
+
+/*
+ * The same binning (same outputs, same arguments and errors) computed with
+ * the CUDA Toolkit's CUB radix sorts: the Gaussians sorted by depth, their
+ * tile ids emitted in that order, then a stable sort on the tile id.  Kept
+ * as the measured comparison for gsr_bin_sort; its scratch size comes from
+ * gsr_bin_scratch_bytes_library.
+ */
+int gsr_bin_scratch_bytes_library(int32_t n, int32_t width, int32_t height, int32_t tile_w,
+                                  int32_t tile_h, int64_t key_capacity, size_t* bytes);
+int gsr_bin_sort_library(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                         const float* splat2d, const int32_t* radius, int64_t key_capacity,
+                         void* scratch, size_t scratch_bytes, uint32_t* point_list,
+                         uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,
+                         gsr_stream_t stream);
 
 /*
  * Allocation-free binning.  The paper has no counterpart: this entry point

@@ -44,6 +44,15 @@ def opts_name(o) -> str:
         ("" if o.store_T else "-recompute")
 
 
+def parse_opts_name(name: str):
+    """Inverse of ``opts_name``: 'hybrid-thr16-lay1-ppt2[-recompute]'."""
+    parts = name.split("-")
+    mode = parts[0]
+    kv = {p[:3]: int(p[3:]) for p in parts[1:] if p[:3] in ("thr", "lay", "ppt")}
+    return gsr.backward_opts(mode, kv.get("thr", 0), kv.get("lay", 0), "recompute" not in parts,
+                             kv.get("ppt", 1))
+
+
 class L2Flusher:
     def __init__(self, device):
         self.buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)

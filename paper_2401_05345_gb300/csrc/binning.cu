@@ -1,0 +1,773 @@
+// Tile binning with hand-written sorts: the per-tile, depth-ordered lists of
+// splats that every pixel of a tile walks (Sec. III-A; the lists are the
+// 3DGS rasterizer's, Sec. II-C).
+//
+// 1. Depth order.  The Gaussians are put in (depth, id) order by a stable LSD
+//    radix sort of their 32-bit depth keys: three passes of 11, 11 and 10
+//    bits.  Each pass is reduce-then-scan: per-tile digit counts (for the
+//    first pass from the key-generation kernel, for the later ones added by
+//    the previous pass's scatter as it writes each key), a column scan of
+//    the [tile][digit] count matrix, and a scatter that ranks the tile's keys
+//    with warp match masks.  No block waits on another.
+// 2. Tile lists.  Walking the Gaussians in that order and appending each one
+//    to the lists of the tiles its rectangle covers gives every tile's list
+//    already in (depth, id) order, so the entries never go through a sort
+//    of their own: a counting sort over tile ids places them directly.  The
+//    entries, in depth order (tiles row-major inside a rectangle), are cut
+//    into equal slices, one per warp of the placement grid (a Gaussian may
+//    straddle two slices: it has one entry per tile, so order per tile is
+//    kept).  One kernel counts each block's entries per tile, a column scan
+//    over the blocks gives every (block, tile) pair its first slot (and the
+//    tile ranges), and a second pass writes the entries, 32 per round per
+//    warp, ranking equal tiles within a round by lane.
+#include "gsr_internal.cuh"
+
+namespace gsr {
+namespace {
+
+struct Geom {
+    int W, H, tw, th, gx, gy, twl, thl, tiles;
+};
+
+int log2_exact(int x) { int l = 0; while ((1 << l) < x) ++l; return l; }
+
+bool make_geom(int W, int H, int tw, int th, Geom& g) {
+    if (W <= 0 || H <= 0) return false;
+    if (!pow2_in(tw, 8, 32) || !pow2_in(th, 8, 32) || tw * th > 512) return false;
+    g.W = W; g.H = H; g.tw = tw; g.th = th;
+    g.gx = (W + tw - 1) / tw;
+    g.gy = (H + th - 1) / th;
+    if (g.gx >= 65536 || g.gy >= 65536) return false;  // tile coordinates are packed in 16 bits
+    if ((long long)g.gx * g.gy >= (1ll << 31)) return false;
+    g.twl = log2_exact(tw); g.thl = log2_exact(th);
+    g.tiles = g.gx * g.gy;
+    return true;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---- depth radix sort -------------------------------------------------------
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;  // keys per tile (block)
+constexpr int kRsB0 = 11, kRsB1 = 11, kRsB2 = 10;
+constexpr int kRsS1 = kRsB0, kRsS2 = kRsB0 + kRsB1;
+
+int rs_tiles(int n) { return (n + kRsTile - 1) / kRsTile; }
+
+// Exclusive scan of one value per thread over a 256-thread block (returns
+// the thread's prefix; *total receives the block sum).  s_wsum: 8 words.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_wsum, uint32_t* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_wsum[w] = incl;
+    __syncthreads();
+    uint32_t woff = 0, tot = 0;
+#pragma unroll
+    for (int q = 0; q < kRsWarps; ++q) {
+        const uint32_t x = s_wsum[q];
+        woff += q < w ? x : 0u;
+        tot += x;
+    }
+    __syncthreads();  // s_wsum may be reused by the caller
+    *total = tot;
+    return woff + incl - v;
+}
+
+// Depth keys (FP32 bits of the camera depth, positive, so their unsigned
+// order is the numeric order; culled Gaussians get the largest key) and ids;
+// per-tile counts of the first digit.
+__global__ void __launch_bounds__(kRsThreads)
+depth_keys_kernel(int n, const float* __restrict__ splat2d, const int* __restrict__ radius,
+                  uint32_t* __restrict__ keys, uint32_t* __restrict__ ids, uint32_t* __restrict__ counts0) {
+    constexpr int NB = 1 << kRsB0;
+    __shared__ uint32_t h[NB];
+    for (int i = threadIdx.x; i < NB; i += kRsThreads) h[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long first = (long long)blockIdx.x * kRsTile + w * 32 * kRsItems + lane;
+#pragma unroll 4
+    for (int it = 0; it < kRsItems; ++it) {
+        const long long i = first + 32 * it;
+        const bool valid = i < n;
+        uint32_t k = 0xffffffffu;
+        if (valid) {
+            k = radius[i] > 0 ? __float_as_uint(splat2d[(size_t)i * GSR_REC + 9]) : 0xffffffffu;
+            keys[i] = k;
+            ids[i] = (uint32_t)i;
+        }
+        const uint32_t d = k & (NB - 1);
+        const unsigned peers = __match_any_sync(kFull, d) & __ballot_sync(kFull, valid);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NB; i += kRsThreads) counts0[(size_t)blockIdx.x * NB + i] = h[i];
+}
+
+// In-place exclusive scan down the columns of a [rows][cols] matrix, with
+// the column totals.  Block: 32 columns x 32 row segments.  When ranges is
+// given, the last block to finish also scans the totals over the columns
+// (tile start offsets), writes the [start, end) ranges (0,0 for empty
+// columns) and the grand total.
+__global__ void __launch_bounds__(1024)
+colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restrict__ tot,
+               uint32_t* __restrict__ start, uint32_t* __restrict__ ranges, uint32_t* __restrict__ info) {
+    __shared__ uint32_t s_seg[32][33];
+    __shared__ bool s_last;
+    const int cx = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + cx;
+    const int per = (rows + 31) / 32;
+    const int r0 = seg * per, r1 = min(rows, r0 + per);
+    uint32_t sum = 0;
+    if (c < cols)
+#pragma unroll 4
+        for (int r = r0; r < r1; ++r) sum += m[(size_t)r * cols + c];
+    s_seg[seg][cx] = sum;
+    __syncthreads();
+    if (seg == 0) {
+        uint32_t run = 0;
+        for (int q = 0; q < 32; ++q) {
+            const uint32_t x = s_seg[q][cx];
+            s_seg[q][cx] = run;
+            run += x;
+        }
+        if (c < cols) tot[c] = run;
+    }
+    __syncthreads();
+    if (c < cols) {
+        uint32_t run = s_seg[seg][cx];
+#pragma unroll 4
+        for (int r = r0; r < r1; ++r) {
+            const size_t o = (size_t)r * cols + c;
+            const uint32_t x = m[o];
+            m[o] = run;
+            run += x;
+        }
+    }
+    if (!ranges) return;
+    // last block: exclusive scan of the column totals
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&info[2], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    uint32_t carry = 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < cols; base += 1024 * 4) {
+        const int c0 = base + threadIdx.x * 4;
+        uint32_t v[4], s = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = c0 + j < cols ? __ldcg(tot + c0 + j) : 0u;
+            s += v[j];
+        }
+        uint32_t incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_seg[0][w] = incl;
+        __syncthreads();
+        uint32_t woff = 0, btot = 0;
+        for (int q = 0; q < 32; ++q) {
+            const uint32_t x = s_seg[0][q];
+            woff += q < w ? x : 0u;
+            btot += x;
+        }
+        __syncthreads();
+        uint32_t run = carry + woff + incl - s;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (c0 + j < cols) {
+                start[c0 + j] = run;
+                ranges[2 * (size_t)(c0 + j)] = v[j] ? run : 0u;
+                ranges[2 * (size_t)(c0 + j) + 1] = v[j] ? run + v[j] : 0u;
+            }
+            run += v[j];
+        }
+        carry += btot;
+    }
+    if (threadIdx.x == 0) info[0] = carry;
+}
+
+// One scatter pass of the depth sort.  The tile's keys are ranked stably
+// (warp-striped: warp w holds keys w*512 .. w*512+511 of the tile, item i of
+// lane l is key 32 i + l of that run) with match masks per warp, per-warp
+// digit counts are scanned across the warps, and every key goes to
+//   (keys of smaller digits) + (keys of its digit in earlier tiles)
+//   + (its rank inside the tile).
+// With NEXT, each written key also adds one to its next digit's count in
+// the tile it lands in (the next pass's count matrix).
+template <int SHIFT, int BITS, int NSHIFT, int NBITS, bool NEXT>
+__global__ void __launch_bounds__(kRsThreads)
+radix_scatter_kernel(int n, const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* __restrict__ colpre,
+                     const uint32_t* __restrict__ tot, uint32_t* __restrict__ cnext, uint32_t* __restrict__ err) {
+    constexpr int NB = 1 << BITS;
+    constexpr int DPT = NB / kRsThreads;  // digits owned by each thread
+    __shared__ uint16_t s_w[kRsWarps][NB];
+    __shared__ uint32_t s_base[NB];
+    __shared__ uint32_t s_wsum[kRsWarps];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = tid; i < kRsWarps * NB / 2; i += kRsThreads) reinterpret_cast<uint32_t*>(&s_w[0][0])[i] = 0u;
+    const int tile = blockIdx.x;
+    const long long first = (long long)tile * kRsTile + w * 32 * kRsItems + lane;
+    uint32_t key[kRsItems], val[kRsItems], rank[kRsItems];
+#pragma unroll
+    for (int i = 0; i < kRsItems; ++i) {
+        const long long idx = first + 32 * i;
+        key[i] = idx < n ? kin[idx] : 0xffffffffu;
+        val[i] = idx < n ? vin[idx] : 0u;
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int i = 0; i < kRsItems; ++i) {
+        const bool valid = first + 32 * i < n;
+        const uint32_t d = (key[i] >> SHIFT) & (NB - 1);
+        const unsigned peers = __match_any_sync(kFull, d) & __ballot_sync(kFull, valid);
+        const uint32_t pre = s_w[w][d];
+        __syncwarp();
+        if (valid && lane == 31 - __clz(peers)) s_w[w][d] = (uint16_t)(pre + __popc(peers));
+        rank[i] = pre + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    // digits d = tid*DPT + j: global base and the warps' exclusive offsets
+    uint32_t hv[DPT], hs = 0;
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+        hv[j] = tot[tid * DPT + j];
+        hs += hv[j];
+    }
+    uint32_t all = 0;
+    uint32_t run = block_excl_scan(hs, s_wsum, &all);
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+        const int d = tid * DPT + j;
+        s_base[d] = run + colpre[(size_t)tile * NB + d];
+        run += hv[j];
+        uint32_t wr = 0;
+#pragma unroll
+        for (int q = 0; q < kRsWarps; ++q) {
+            const uint32_t c = s_w[q][d];
+            s_w[q][d] = (uint16_t)wr;
+            wr += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kRsItems; ++i) {
+        if (first + 32 * i < n) {
+            const uint32_t d = (key[i] >> SHIFT) & (NB - 1);
+            const uint32_t pos = s_base[d] + s_w[w][d] + rank[i];
+            if (pos >= (uint32_t)n) {  // inconsistent counts: never write outside the buffers
+                atomicOr(err, 1u);
+                continue;
+            }
+            kout[pos] = key[i];
+            vout[pos] = val[i];
+            if (NEXT) {
+                constexpr uint32_t NNB = 1u << NBITS;
+                atomicAdd(&cnext[(size_t)(pos / kRsTile) * NNB + ((key[i] >> NSHIFT) & (NNB - 1))], 1u);
+            }
+        }
+    }
+}
+
+// ---- tile counting sort -----------------------------------------------------
+constexpr int kPlaceWarps = 8;
+constexpr int kPlaceThreads = 32 * kPlaceWarps;
+constexpr int kMaxWindowTiles = 8192;  // tiles handled per placement window
+constexpr int kTargetSMs = 152;
+constexpr int kRectPer = 8;                            // Gaussians per thread of the rectangle pass
+constexpr int kRectBlock = kRsThreads * kRectPer;      // Gaussians per rectangle block
+constexpr int kRectShift = 11;                         // log2(kRectBlock)
+static_assert(kRectBlock == 1 << kRectShift, "rectangle block");
+// A block's entries stay below 2^16 (its per-tile counts are 16-bit).
+constexpr long long kMaxBlockEntries = 65000;
+
+int window_tiles(const Geom& g) { return g.tiles < kMaxWindowTiles ? g.tiles : kMaxWindowTiles; }
+
+// Shared memory of the placement kernel: a 32-bit base per tile and, per
+// warp, a 16-bit count per tile (packed two to a word).
+size_t place_smem(int tw) { return sizeof(uint32_t) * ((size_t)tw + (size_t)kPlaceWarps * ((tw + 1) / 2)); }
+
+// Number of placement blocks: about one per resident slot of a 152-SM part,
+// and enough that no block holds more than kMaxBlockEntries entries.  The
+// entries (in depth order, tiles row-major inside each rectangle) are split
+// evenly over the blocks' warps, so a block's work does not depend on how
+// large its splats are.
+int place_blocks(long long cap, const Geom& g) {
+    const size_t sm = place_smem(window_tiles(g)) + 1024;
+    int per_sm = (int)((size_t)(227 * 1024) / sm);
+    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    long long nb = (long long)kTargetSMs * per_sm;
+    const long long need = (cap + kMaxBlockEntries - 1) / kMaxBlockEntries;
+    return (int)(nb > need ? nb : need);
+}
+
+__device__ __forceinline__ void unpack_rect(uint2 r, int& x0, int& x1, int& y0, int& y1) {
+    x0 = (int)(r.x & 0xffffu); x1 = (int)(r.x >> 16);
+    y0 = (int)(r.y & 0xffffu); y1 = (int)(r.y >> 16);
+}
+
+__device__ __forceinline__ uint32_t rect_area(uint2 r) {
+    int x0, x1, y0, y1;
+    unpack_rect(r, x0, x1, y0, y1);
+    return (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+}
+
+// Rectangles of the depth-ordered Gaussians (packed 16-bit corners, empty
+// when culled) and the exclusive prefix of their areas inside each block of
+// 2048; the last block to finish turns the block sums into block offsets
+// and stores the entry total in info[4].
+__global__ void __launch_bounds__(kRsThreads)
+rects_kernel(int n, Geom g, const float* __restrict__ splat2d, const int* __restrict__ radius,
+             const uint32_t* __restrict__ order, uint2* __restrict__ rects, uint32_t* __restrict__ apre,
+             uint32_t* __restrict__ bsum, int nblk, uint32_t* __restrict__ info) {
+    __shared__ uint32_t s_wsum[kRsWarps];
+    __shared__ bool s_last;
+    const int k0 = blockIdx.x * kRectBlock + threadIdx.x * kRectPer;
+    uint32_t area[kRectPer], sum = 0;
+#pragma unroll
+    for (int i = 0; i < kRectPer; ++i) {
+        const int k = k0 + i;
+        int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        if (k < n) {
+            const uint32_t id = order[k];
+            const int r = radius[id];
+            if (r > 0) {
+                const float2 uv = *reinterpret_cast<const float2*>(splat2d + (size_t)id * GSR_REC);
+                tile_rect(uv.x, uv.y, r, g.gx, g.gy, g.twl, g.thl, x0, x1, y0, y1);
+                if (x1 <= x0 || y1 <= y0) x0 = x1 = y0 = y1 = 0;
+            }
+            rects[k] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
+        }
+        area[i] = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+        sum += area[i];
+    }
+    uint32_t btot;
+    uint32_t run = block_excl_scan(sum, s_wsum, &btot);
+#pragma unroll
+    for (int i = 0; i < kRectPer; ++i) {
+        if (k0 + i < n) apre[k0 + i] = run;
+        run += area[i];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = btot;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&info[3], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    uint32_t carry = 0;
+    for (int base = 0; base < nblk; base += kRsThreads * 4) {
+        const int c0 = base + threadIdx.x * 4;
+        uint32_t v[4], s4 = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = c0 + j < nblk ? __ldcg(bsum + c0 + j) : 0u;
+            s4 += v[j];
+        }
+        uint32_t all;
+        uint32_t r = carry + block_excl_scan(s4, s_wsum, &all);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (c0 + j < nblk) bsum[c0 + j] = r;
+            r += v[j];
+        }
+        carry += all;
+    }
+    if (threadIdx.x == 0) info[4] = carry;
+}
+
+// Entry prefix of depth-ordered Gaussian k (bsum already holds offsets).
+__device__ __forceinline__ uint32_t entry_prefix(const uint32_t* __restrict__ apre, const uint32_t* __restrict__ boff,
+                                                 int k) {
+    return boff[k >> kRectShift] + apre[k];
+}
+
+__device__ __forceinline__ uint32_t warp_entries(uint32_t total, int nwarps) {
+    const uint32_t ew = (uint32_t)(((unsigned long long)total + nwarps - 1) / nwarps);
+    return ew > 0 ? ew : 1u;
+}
+
+// For every warp j of the placement grid: the Gaussian that holds entry
+// j * Ew, its first entry (each boundary lies in exactly one rectangle).
+__global__ void __launch_bounds__(256)
+bounds_kernel(int n, int nwarps, const uint2* __restrict__ rects, const uint32_t* __restrict__ apre,
+              const uint32_t* __restrict__ boff, const uint32_t* __restrict__ info, uint32_t* __restrict__ wstart) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t area = rect_area(rects[k]);
+    if (area == 0) return;
+    const uint32_t ew = warp_entries(info[4], nwarps);
+    const uint32_t p = entry_prefix(apre, boff, k);
+    for (uint32_t j = (p + ew - 1) / ew; (unsigned long long)j * ew < (unsigned long long)p + area; ++j)
+        if (j < (uint32_t)nwarps) wstart[j] = (uint32_t)k;
+}
+
+// Per-warp staging of 32 consecutive depth-ordered Gaussians: their
+// rectangles, the exclusive prefix of their areas (entry e of the 32 belongs
+// to the last Gaussian whose prefix is <= e) and a multiplier that divides
+// by the rectangle width.
+struct WarpBatch {
+    uint32_t pre[33];
+    int x0[32], wd[32], y0[32];
+    uint32_t mul[32];
+    uint32_t id[32], dk[32];
+};
+
+// Fills the warp's batch (lane = Gaussian k, absent at k >= n); returns the
+// batch's entry count.
+__device__ __forceinline__ uint32_t stage_batch(WarpBatch& wb, int lane, bool present, uint2 pr, uint32_t id,
+                                                uint32_t dk) {
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    if (present) unpack_rect(pr, x0, x1, y0, y1);
+    const int wd = x1 - x0;
+    const uint32_t area = (uint32_t)wd * (uint32_t)(y1 - y0);
+    uint32_t incl = area;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    wb.pre[lane] = incl - area;
+    if (lane == 31) wb.pre[32] = incl;
+    wb.x0[lane] = x0;
+    wb.wd[lane] = wd;
+    wb.y0[lane] = y0;
+    // ceil(2^32 / wd) for wd >= 2: floor(e / wd) = umulhi(e, mul) exactly
+    // while e and wd are below 2^16 (then e * wd < 2^32)
+    wb.mul[lane] = wd > 1 ? (uint32_t)(0xffffffffu / (uint32_t)wd) + 1u : 0u;
+    wb.id[lane] = id;
+    wb.dk[lane] = dk;
+    __syncwarp();
+    return wb.pre[32];
+}
+
+// Tile (window-relative, or -1 outside the window) of entry e of the batch,
+// and the Gaussian (lane of the batch) it belongs to.
+__device__ __forceinline__ int entry_tile(const WarpBatch& wb, uint32_t e, const Geom& g, int t0, int tw, int& j) {
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (wb.pre[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    j = lo;
+    const uint32_t local = e - wb.pre[lo];
+    const uint32_t wd = (uint32_t)wb.wd[lo];
+    const uint32_t dy = wd == 1u ? local : (local < 65536u ? __umulhi(local, wb.mul[lo]) : local / wd);
+    const int t = (wb.y0[lo] + (int)dy) * g.gx + wb.x0[lo] + (int)(local - dy * wd) - t0;
+    return (unsigned)t < (unsigned)tw ? t : -1;
+}
+
+// Walks the entries [e0, e1) of warp j in depth order, 32 Gaussians at a
+// time, calling f(tile, gaussian lane) for each entry of the window (lanes
+// past the range call f with tile -1, so f may use warp-wide intrinsics).
+template <bool IDS, class F>
+__device__ __forceinline__ void walk_entries(WarpBatch& wb, int lane, int n, uint32_t e0, uint32_t e1, int k,
+                                             const uint2* __restrict__ rects, const uint32_t* __restrict__ order,
+                                             const uint32_t* __restrict__ dkeys, uint32_t pk, const Geom& g, int t0,
+                                             int tw, F&& f) {
+    while (pk < e1 && k < n) {
+        const int kk = k + lane;
+        const bool present = kk < n;
+        const uint32_t bt = stage_batch(wb, lane, present, present ? rects[kk] : make_uint2(0u, 0u),
+                                        IDS && present ? order[kk] : 0u, IDS && dkeys && present ? dkeys[kk] : 0u);
+        const uint32_t lo = e0 > pk ? e0 - pk : 0u;
+        const uint32_t hi = e1 - pk < bt ? e1 - pk : bt;
+        for (uint32_t base = lo; base < hi; base += 32) {
+            const uint32_t e = base + lane;
+            int j = 0, t = -1;
+            if (e < hi) t = entry_tile(wb, e, g, t0, tw, j);
+            f(t, j);
+        }
+        __syncwarp();
+        pk += bt;
+        k += 32;
+    }
+}
+
+// Counts, per placement block, the entries of every tile in the window
+// [t0, t0 + tw): m[b][t0 + t].
+__global__ void __launch_bounds__(kPlaceThreads)
+chunk_hist_kernel(int n, int nb, Geom g, int t0, int tw, const uint2* __restrict__ rects,
+                  const uint32_t* __restrict__ apre, const uint32_t* __restrict__ boff,
+                  const uint32_t* __restrict__ wstart, const uint32_t* __restrict__ info, uint32_t* __restrict__ m) {
+    extern __shared__ uint32_t h[];
+    __shared__ WarpBatch s_wb[kPlaceWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < tw; t += kPlaceThreads) h[t] = 0;
+    __syncthreads();
+    const int b = blockIdx.x;
+    const uint32_t total = info[4];
+    const int nwarps = nb * kPlaceWarps;
+    const uint32_t ew = warp_entries(total, nwarps);
+    const unsigned long long e0l = (unsigned long long)(b * kPlaceWarps + w) * ew;
+    if (e0l < total) {
+        const uint32_t e0 = (uint32_t)e0l;
+        const uint32_t e1 = total - e0 < ew ? total : e0 + ew;
+        const int k = (int)wstart[b * kPlaceWarps + w];
+        walk_entries<false>(s_wb[w], lane, n, e0, e1, k, rects, nullptr, nullptr, entry_prefix(apre, boff, k), g, t0,
+                            tw, [&](int t, int) {
+                                if (t >= 0) atomicAdd(&h[t], 1u);
+                            });
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tw; t += kPlaceThreads) m[(size_t)b * g.tiles + t0 + t] = h[t];
+}
+
+// Writes the entries of the tiles in the window: block b's entries of tile
+// t start at start[t] + m[b][t] (m already column-scanned); each warp owns a
+// consecutive slice of the block's entries, and its per-tile offsets come
+// from the warps before it.  Entries of one tile in the same round of 32
+// are ranked by lane with a match mask, so every tile receives its entries
+// in depth order.
+template <bool KEYS>
+__global__ void __launch_bounds__(kPlaceThreads)
+place_kernel(int n, int nb, Geom g, int t0, int tw, const uint32_t* __restrict__ order,
+             const uint32_t* __restrict__ dkeys, const uint2* __restrict__ rects, const uint32_t* __restrict__ apre,
+             const uint32_t* __restrict__ boff, const uint32_t* __restrict__ wstart,
+             const uint32_t* __restrict__ info, const uint32_t* __restrict__ m, const uint32_t* __restrict__ start,
+             uint32_t* __restrict__ point_list, uint64_t* __restrict__ keys_out) {
+    extern __shared__ uint32_t sm[];
+    __shared__ WarpBatch s_wb[kPlaceWarps];
+    const int tw2 = (tw + 1) / 2;
+    uint32_t* s_base = sm;
+    uint32_t* s_cnt = sm + tw;  // [kPlaceWarps][tw2] packed 16-bit counts
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = tid; i < kPlaceWarps * tw2; i += kPlaceThreads) s_cnt[i] = 0;
+    const int b = blockIdx.x;
+    const uint32_t total = info[4];
+    const uint32_t ew = warp_entries(total, nb * kPlaceWarps);
+    const unsigned long long e0l = (unsigned long long)(b * kPlaceWarps + w) * ew;
+    const bool mine = e0l < total;
+    const uint32_t e0 = mine ? (uint32_t)e0l : 0u;
+    const uint32_t e1 = !mine ? 0u : (total - e0 < ew ? total : e0 + ew);
+    const int k = mine ? (int)wstart[b * kPlaceWarps + w] : 0;
+    const uint32_t pk = mine ? entry_prefix(apre, boff, k) : 0u;
+    WarpBatch& wb = s_wb[w];
+    uint32_t* wc = s_cnt + (size_t)w * tw2;
+    __syncthreads();
+    // per-warp entry counts of each tile
+    if (mine)
+        walk_entries<false>(wb, lane, n, e0, e1, k, rects, nullptr, nullptr, pk, g, t0, tw, [&](int t, int) {
+            if (t >= 0) atomicAdd(&wc[t >> 1], (t & 1) ? 0x10000u : 1u);
+        });
+    __syncthreads();
+    // tile bases; per-warp exclusive offsets (two tiles per word)
+    for (int q = tid; q < tw2; q += kPlaceThreads) {
+        const int t = 2 * q;
+        const size_t mb = (size_t)b * g.tiles + t0;
+        s_base[t] = m[mb + t] + start[t0 + t];
+        if (t + 1 < tw) s_base[t + 1] = m[mb + t + 1] + start[t0 + t + 1];
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int v = 0; v < kPlaceWarps; ++v) {
+            const uint32_t x = s_cnt[(size_t)v * tw2 + q];
+            s_cnt[(size_t)v * tw2 + q] = lo | (hi << 16);
+            lo += x & 0xffffu;
+            hi += x >> 16;
+        }
+    }
+    __syncthreads();
+    if (!mine) return;
+    uint16_t* c16 = reinterpret_cast<uint16_t*>(wc);
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t key_total = info[0];
+    walk_entries<true>(wb, lane, n, e0, e1, k, rects, order, KEYS ? dkeys : nullptr, pk, g, t0, tw,
+                       [&](int t, int j) {
+        const unsigned peers = __match_any_sync(kFull, t >= 0 ? (uint32_t)t : 0xffffffffu);
+        uint32_t c = 0;
+        if (t >= 0) {
+            c = c16[t];
+            const uint32_t pos = s_base[t] + c + __popc(peers & lt);
+            if (pos < key_total) {  // always, unless the counts were inconsistent
+                point_list[pos] = wb.id[j];
+                if (KEYS) keys_out[pos] = ((uint64_t)(uint32_t)(t + t0) << 32) | (uint64_t)wb.dk[j];
+            }
+        }
+        __syncwarp();
+        if (t >= 0 && lane == 31 - __clz(peers)) c16[t] = (uint16_t)(c + __popc(peers));
+        __syncwarp();
+    });
+}
+
+// ---- scratch ------------------------------------------------------------------
+struct BinScratch {
+    uint32_t *ka, *va, *kb, *vb;   // [n] ping-pong keys / values of the depth sort
+    uint32_t *c0, *c1, *c2;        // [rs_tiles][digits] count matrices of the three passes
+    uint32_t *t0, *t1, *t2;        // digit totals
+    uint32_t* info;                // [8]: key total, sort error flag, finished colscan blocks,
+                                   //      finished rectangle blocks, entry total
+    uint2* rects;                  // [n] packed tile rectangles in depth order
+    uint32_t* apre;                // [n] entry prefix inside each rectangle block
+    uint32_t* bsum;                // [n / 2048] rectangle block sums, then offsets
+    uint32_t* wstart;              // [nb * warps] first Gaussian of each placement warp
+    uint32_t* m;                   // [nb][tiles] block x tile counts, then bases
+    uint32_t *ttot, *tstart;       // [tiles]
+    int nb;                        // placement blocks
+    size_t zero_bytes;             // c1 .. info are zeroed together
+    size_t total;
+};
+
+int rect_blocks(int n) { return (n + kRectBlock - 1) / kRectBlock; }
+
+void bin_layout(int n, const Geom& g, long long cap, char* base, BinScratch& s) {
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    const size_t rt = (size_t)(rs_tiles(n) > 0 ? rs_tiles(n) : 1);
+    s.nb = place_blocks(cap, g);
+    const size_t nb = (size_t)s.nb;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return base ? base + o : nullptr; };
+    s.ka = (uint32_t*)take(4 * nn);
+    s.va = (uint32_t*)take(4 * nn);
+    s.kb = (uint32_t*)take(4 * nn);
+    s.vb = (uint32_t*)take(4 * nn);
+    s.c0 = (uint32_t*)take(4 * rt * (1u << kRsB0));
+    s.t0 = (uint32_t*)take(4 * (1u << kRsB0));
+    s.t1 = (uint32_t*)take(4 * (1u << kRsB1));
+    s.t2 = (uint32_t*)take(4 * (1u << kRsB2));
+    const size_t z0 = off;
+    s.c1 = (uint32_t*)take(4 * rt * (1u << kRsB1));
+    s.c2 = (uint32_t*)take(4 * rt * (1u << kRsB2));
+    s.info = (uint32_t*)take(32);
+    s.zero_bytes = off - z0;
+    s.rects = (uint2*)take(8 * nn);
+    s.apre = (uint32_t*)take(4 * nn);
+    s.bsum = (uint32_t*)take(4 * (size_t)(rect_blocks(n) > 0 ? rect_blocks(n) : 1));
+    s.wstart = (uint32_t*)take(4 * nb * kPlaceWarps);
+    s.m = (uint32_t*)take(4 * nb * (size_t)g.tiles);
+    s.ttot = (uint32_t*)take(4 * (size_t)g.tiles);
+    s.tstart = (uint32_t*)take(4 * (size_t)g.tiles);
+    s.total = off;
+}
+
+int colscan(int rows, int cols, uint32_t* m, uint32_t* tot, uint32_t* start, uint32_t* ranges, uint32_t* info,
+            cudaStream_t st) {
+    colscan_kernel<<<(cols + 31) / 32, 1024, 0, st>>>(rows, cols, m, tot, start, ranges, info);
+    return check_launch();
+}
+
+int smem_optin(const void* fn, size_t bytes) {
+    if (bytes <= 48 * 1024) return GSR_OK;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e == cudaSuccess ? GSR_OK : cuda_fail(e);
+}
+
+}  // namespace
+}  // namespace gsr
+
+using namespace gsr;
+
+extern "C" int gsr_bin_scratch_bytes(int32_t n, int32_t width, int32_t height, int32_t tile_w,
+                                     int32_t tile_h, int64_t key_capacity, size_t* bytes) {
+    Geom g;
+    if (n < 0 || key_capacity < 0 || key_capacity >= 0xffffffffll || !bytes ||
+        !make_geom(width, height, tile_w, tile_h, g))
+        return GSR_EINVAL;
+    BinScratch s;
+    bin_layout(n, g, key_capacity, nullptr, s);
+    *bytes = s.total;
+    return GSR_OK;
+}
+
+extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                            const float* splat2d, const int32_t* radius, int64_t key_capacity,
+                            void* scratch, size_t scratch_bytes, uint32_t* point_list,
+                            uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,
+                            gsr_stream_t stream_) {
+    Geom g;
+    if (n < 0 || key_capacity < 0 || key_capacity >= 0xffffffffll || !n_keys ||
+        !make_geom(width, height, tile_w, tile_h, g))
+        return GSR_EINVAL;
+    if (!tile_ranges || !scratch || (n > 0 && (!splat2d || !radius)) || (key_capacity > 0 && !point_list))
+        return GSR_EINVAL;
+    if (!aligned16(splat2d) || !aligned16(scratch) || (keys_out && !aligned8(keys_out))) return GSR_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream_;
+    BinScratch s;
+    bin_layout(n, g, key_capacity, (char*)scratch, s);
+    if (scratch_bytes < s.total) return GSR_ESCRATCH;
+    *n_keys = 0;
+    int rc;
+    cudaError_t e;
+    if (n == 0) {
+        e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)g.tiles, st);
+        return e == cudaSuccess ? GSR_OK : cuda_fail(e);
+    }
+    e = cudaMemsetAsync(s.c1, 0, s.zero_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+
+    // 1. (depth, id) order: keys + first-digit counts, then three passes
+    const int rt = rs_tiles(n);
+    depth_keys_kernel<<<rt, kRsThreads, 0, st>>>(n, splat2d, radius, s.ka, s.va, s.c0);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    if ((rc = colscan(rt, 1 << kRsB0, s.c0, s.t0, nullptr, nullptr, nullptr, st)) != GSR_OK) return rc;
+    radix_scatter_kernel<0, kRsB0, kRsS1, kRsB1, true><<<rt, kRsThreads, 0, st>>>(n, s.ka, s.va, s.kb, s.vb, s.c0,
+                                                                                  s.t0, s.c1, s.info + 1);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    if ((rc = colscan(rt, 1 << kRsB1, s.c1, s.t1, nullptr, nullptr, nullptr, st)) != GSR_OK) return rc;
+    radix_scatter_kernel<kRsS1, kRsB1, kRsS2, kRsB2, true><<<rt, kRsThreads, 0, st>>>(n, s.kb, s.vb, s.ka, s.va,
+                                                                                      s.c1, s.t1, s.c2, s.info + 1);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    if ((rc = colscan(rt, 1 << kRsB2, s.c2, s.t2, nullptr, nullptr, nullptr, st)) != GSR_OK) return rc;
+    radix_scatter_kernel<kRsS2, kRsB2, 0, 1, false><<<rt, kRsThreads, 0, st>>>(n, s.ka, s.va, s.kb, s.vb, s.c2,
+                                                                               s.t2, nullptr, s.info + 1);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    const uint32_t* order = s.vb;
+    const uint32_t* dkeys = s.kb;
+
+    // 2. rectangles and entry prefixes in depth order, the first Gaussian of
+    //    every placement warp, per block x tile counts, column scan, tile
+    //    starts and ranges
+    const int nr = rect_blocks(n);
+    rects_kernel<<<nr, kRsThreads, 0, st>>>(n, g, splat2d, radius, order, s.rects, s.apre, s.bsum, nr, s.info);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    const int nwarps = s.nb * kPlaceWarps;
+    bounds_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, nwarps, s.rects, s.apre, s.bsum, s.info, s.wstart);
+    if ((rc = check_launch()) != GSR_OK) return rc;
+    const int tw = window_tiles(g);
+    const size_t hsm = sizeof(uint32_t) * (size_t)tw;
+    if ((rc = smem_optin((const void*)chunk_hist_kernel, hsm)) != GSR_OK) return rc;
+    for (int t0 = 0; t0 < g.tiles; t0 += tw) {
+        const int wt = g.tiles - t0 < tw ? g.tiles - t0 : tw;
+        chunk_hist_kernel<<<s.nb, kPlaceThreads, hsm, st>>>(n, s.nb, g, t0, wt, s.rects, s.apre, s.bsum, s.wstart,
+                                                            s.info, s.m);
+        if ((rc = check_launch()) != GSR_OK) return rc;
+    }
+    if ((rc = colscan(s.nb, g.tiles, s.m, s.ttot, s.tstart, tile_ranges, s.info, st)) != GSR_OK) return rc;
+    uint32_t info[5] = {0, 0, 0, 0, 0};
+    e = cudaMemcpyAsync(info, s.info, sizeof(info), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    // a sort pass found inconsistent counts, or the two entry totals differ (not expected)
+    if (info[1] || info[0] != info[4]) return GSR_ECUDA;
+    const uint32_t total = info[0];
+    *n_keys = (int64_t)total;
+    if ((long long)total > key_capacity) return GSR_ECAPACITY;
+    if (total == 0) return GSR_OK;
+
+    // 3. entries written in place
+    const size_t psm = place_smem(tw);
+    auto pk = keys_out ? place_kernel<true> : place_kernel<false>;
+    if ((rc = smem_optin((const void*)pk, psm)) != GSR_OK) return rc;
+    for (int t0 = 0; t0 < g.tiles; t0 += tw) {
+        const int wt = g.tiles - t0 < tw ? g.tiles - t0 : tw;
+        pk<<<s.nb, kPlaceThreads, psm, st>>>(n, s.nb, g, t0, wt, order, dkeys, s.rects, s.apre, s.bsum, s.wstart,
+                                             s.info, s.m, s.tstart, point_list, keys_out);
+        if ((rc = check_launch()) != GSR_OK) return rc;
+    }
+    return GSR_OK;
+}

@@ -1,4 +1,6 @@
-// Tile binning: duplicated (tile, depth) keys, stable radix sort, ranges.
+// Tile binning through the CUDA Toolkit's CUB radix sort: the comparison arm
+// of the hand-written binning (same outputs), and the allocation-free
+// variant, whose scratch is a static device array.
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
@@ -29,39 +31,7 @@ bool make_geom(int W, int H, int tw, int th, BinGeom& g) {
     return true;
 }
 
-// Scratch layout (each region 256-byte aligned).
-struct Scratch {
-    uint32_t* counts;      // n + 1: tiles touched, then exclusive offsets
-    uint64_t* keys_in;     // capacity
-    uint32_t* vals_in;     // capacity
-    uint64_t* keys_out;    // capacity
-    void* cub_tmp;
-    size_t cub_bytes;
-    size_t total;
-};
-
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-int layout(int n, long long cap, char* base, Scratch& s) {
-    size_t scan_bytes = 0, sort_bytes = 0;
-    cudaError_t e = cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, (uint32_t*)nullptr,
-                                                  (uint32_t*)nullptr, n + 1);
-    if (e != cudaSuccess) return cuda_fail(e);
-    e = cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, (uint64_t*)nullptr, (uint64_t*)nullptr,
-                                        (uint32_t*)nullptr, (uint32_t*)nullptr, (int)(cap > 0 ? cap : 1),
-                                        0, 64);
-    if (e != cudaSuccess) return cuda_fail(e);
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return base ? base + o : nullptr; };
-    s.counts = (uint32_t*)take(sizeof(uint32_t) * ((size_t)n + 1));
-    s.keys_in = (uint64_t*)take(sizeof(uint64_t) * (size_t)(cap > 0 ? cap : 1));
-    s.vals_in = (uint32_t*)take(sizeof(uint32_t) * (size_t)(cap > 0 ? cap : 1));
-    s.keys_out = (uint64_t*)take(sizeof(uint64_t) * (size_t)(cap > 0 ? cap : 1));
-    s.cub_bytes = scan_bytes > sort_bytes ? scan_bytes : sort_bytes;
-    s.cub_tmp = take(s.cub_bytes);
-    s.total = off;
-    return GSR_OK;
-}
 
 __global__ void count_kernel(int n, const float* __restrict__ splat2d, const int* __restrict__ radius,
                              BinGeom g, uint32_t* __restrict__ counts) {
@@ -263,7 +233,7 @@ __global__ void full_keys_kernel(long long nkeys, const uint32_t* __restrict__ t
 
 using namespace gsr;
 
-extern "C" int gsr_bin_scratch_bytes(int32_t n, int32_t width, int32_t height, int32_t tile_w,
+extern "C" int gsr_bin_scratch_bytes_library(int32_t n, int32_t width, int32_t height, int32_t tile_w,
                                      int32_t tile_h, int64_t key_capacity, size_t* bytes) {
     BinGeom g;
     if (n < 0 || key_capacity < 0 || key_capacity >= 0xffffffffll || !bytes ||
@@ -276,7 +246,7 @@ extern "C" int gsr_bin_scratch_bytes(int32_t n, int32_t width, int32_t height, i
     return GSR_OK;
 }
 
-extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+extern "C" int gsr_bin_sort_library(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                             const float* splat2d, const int32_t* radius, int64_t key_capacity,
                             void* scratch, size_t scratch_bytes, uint32_t* point_list,
                             uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,

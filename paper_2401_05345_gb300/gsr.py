@@ -90,6 +90,8 @@ def lib():
                                         POINTER(c_size_t)]
     L.gsr_bin_sort.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, c_int64, P, c_size_t,
                                P, P, P, POINTER(c_int64), P]
+    L.gsr_bin_scratch_bytes_library.argtypes = L.gsr_bin_scratch_bytes.argtypes
+    L.gsr_bin_sort_library.argtypes = L.gsr_bin_sort.argtypes
     L.gsr_bin_sort_static.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, c_int64, P, P, P,
                                       POINTER(c_int64), P]
     L.gsr_forward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P]
@@ -109,6 +111,7 @@ def lib():
     L.gsr_scatter_add9.argtypes = [c_int64, P, P, P, c_int32, c_int32, c_int32, P]
     L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
     for name in ("gsr_preprocess", "gsr_bin_scratch_bytes", "gsr_bin_sort", "gsr_bin_sort_static",
+                 "gsr_bin_scratch_bytes_library", "gsr_bin_sort_library",
                  "gsr_forward", "gsr_backward",
                  "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red",
                  "gsr_activate", "gsr_activate_backward", "gsr_scatter_add9", "gsr_entry_offsets_scratch_bytes",
@@ -156,22 +159,25 @@ def gsr_preprocess(n, sh_degree, mean, scale, quat, opacity, feat, cam, tile_w, 
                                                   _ptr(grad2d_to_zero), _stream(stream)))
 
 
-def gsr_bin_scratch_bytes(n, width, height, tile_w, tile_h, key_capacity) -> int:
+def gsr_bin_scratch_bytes(n, width, height, tile_w, tile_h, key_capacity, library=False) -> int:
+    name = "gsr_bin_scratch_bytes_library" if library else "gsr_bin_scratch_bytes"
     out = c_size_t(0)
-    _check("gsr_bin_scratch_bytes", lib().gsr_bin_scratch_bytes(n, width, height, tile_w, tile_h,
-                                                                key_capacity, ctypes.byref(out)))
+    _check(name, getattr(lib(), name)(n, width, height, tile_w, tile_h, key_capacity, ctypes.byref(out)))
     return int(out.value)
 
 
 def gsr_bin_sort(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity, scratch, point_list,
-                 tile_ranges, keys_out=None, stream=None):
-    """Returns (status, n_keys); status is GSR_OK or GSR_ECAPACITY."""
+                 tile_ranges, keys_out=None, stream=None, library=False):
+    """Returns (status, n_keys); status is GSR_OK or GSR_ECAPACITY.  With
+    library=True the same binning runs through CUB's radix sort
+    (gsr_bin_sort_library, the measured comparison)."""
+    name = "gsr_bin_sort_library" if library else "gsr_bin_sort"
     nk = c_int64(0)
-    st = lib().gsr_bin_sort(n, width, height, tile_w, tile_h, _ptr(splat2d), _ptr(radius), key_capacity,
-                            _ptr(scratch), scratch.numel() * scratch.element_size(), _ptr(point_list),
-                            _ptr(tile_ranges), _ptr(keys_out), ctypes.byref(nk), _stream(stream))
+    st = getattr(lib(), name)(n, width, height, tile_w, tile_h, _ptr(splat2d), _ptr(radius), key_capacity,
+                              _ptr(scratch), scratch.numel() * scratch.element_size(), _ptr(point_list),
+                              _ptr(tile_ranges), _ptr(keys_out), ctypes.byref(nk), _stream(stream))
     if st not in (GSR_OK, GSR_ECAPACITY):
-        _check("gsr_bin_sort", st)
+        _check(name, st)
     return st, int(nk.value)
 
 
