@@ -343,6 +343,9 @@ def run_ours(args):
     t_warp = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("warp", 0, lay, True, ppt), reps, flush)
     t_best = autotune.time_backward(vb, bg, R.dimg, best, reps, flush)
     t_block = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("block", 0, lay, True, ppt), reps, flush)
+    thr_c = int(best.threshold) if int(best.reduce_mode) in (gsr.REDUCE_HYBRID, gsr.REDUCE_CLUSTER) else 12
+    t_cluster = autotune.time_backward(vb, bg, R.dimg, gsr.backward_opts("cluster", thr_c, lay, True, ppt), reps,
+                                       flush)
     t_recompute = autotune.time_backward(
         vb, bg, R.dimg, gsr.backward_opts(int(best.reduce_mode), int(best.threshold), lay, False, ppt), reps, flush)
     # deterministic tier (no float atomics): backward + per-Gaussian reduction
@@ -491,6 +494,7 @@ def run_ours(args):
                          "ops_per_launch": ops, "launch_ms": bwd_avg_s * 1e3},
             "backward_raster": {
                 "ms_plain_atomicAdd": t_plain, "ms_warp": t_warp, "ms_block": t_block,
+                "ms_cluster_dsmem": t_cluster, "cluster_threshold": thr_c,
                 "ms_best": t_best, "best": best_name, "ms_best_recompute_T": t_recompute,
                 "ms_deterministic_no_atomics": t_det,
                 "speedup_best_vs_plain": t_plain / t_best,

@@ -80,12 +80,21 @@ typedef struct gsr_camera {
  *  BLOCK   warp partials (or, below the threshold, per-lane values) are
  *          added into the CTA's shared memory; one global red per
  *          (tile, splat, parameter) when the staged batch is retired.
+ *  CLUSTER 2 x 2 clusters of tile CTAs: warps at or above the threshold
+ *          reduce and add the 9 sums into a hash table spread over the
+ *          cluster's distributed shared memory (one owner CTA and slot per
+ *          splat id, 1024 slots per CTA; a splat that finds no free slot in
+ *          16 probes goes to L2 directly); after a cluster barrier each CTA
+ *          issues one global red per (cluster, splat, parameter).  Sparse
+ *          warps send per-lane atomics, as in HYBRID.  gsr_backward only
+ *          (gsr_backward_batched returns GSR_EINVAL).
  * threshold: 0 = every warp reduces, 33 = none does. */
 enum {
     GSR_REDUCE_PLAIN = 0,
     GSR_REDUCE_WARP = 1,
     GSR_REDUCE_HYBRID = 2,
-    GSR_REDUCE_BLOCK = 3
+    GSR_REDUCE_BLOCK = 3,
+    GSR_REDUCE_CLUSTER = 4
 };
 
 /* lane_layout: which pixels of a 16x16 tile share a warp.

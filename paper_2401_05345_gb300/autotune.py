@@ -20,8 +20,8 @@ L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
 
 
 def default_candidates(store_T=True):
-    """Tier x threshold x pixel-to-lane layout x pixels per thread (1: 8 warps
-    per 16x16 tile, 2: 4 warps)."""
+    """Tier (warp, hybrid, block, cluster) x threshold x pixel-to-lane layout
+    x pixels per thread (1: 8 warps per 16x16 tile, 2: 4 warps)."""
     c = []
     for ppt in (1, 2):
         for lay in (0, 1):
@@ -30,6 +30,8 @@ def default_candidates(store_T=True):
                 c.append(("hybrid", thr, lay, ppt))
             for thr in (0, 4, 8, 16):
                 c.append(("block", thr, lay, ppt))
+            for thr in (0, 8, 16):
+                c.append(("cluster", thr, lay, ppt))
     return [gsr.backward_opts(m, t, l, store_T, p) for (m, t, l, p) in c]
 
 

@@ -54,6 +54,34 @@ backward_kernel(BwdArgs p) {
     backward_tile<SH, MODE, STORE_T>(p, blockIdx.x, sm);
 }
 
+// Cluster tier: tiles (blockIdx.x, blockIdx.y) in 2 x 2 clusters (the grid is
+// rounded up to even sizes; CTAs past the image only take part in the
+// cluster's two barriers and its table).  Dynamic shared memory: key[cap],
+// val[cap][9] of this CTA's part of the cluster table.
+template <class SH, bool STORE_T>
+__global__ void __cluster_dims__(2, 2, 1) __launch_bounds__(SH::NT)
+backward_cluster_kernel(BwdArgs p, int cap) {
+    __shared__ BwdSmem<SH::B, kModeCluster> sm;
+    extern __shared__ uint32_t s_tab[];
+    uint32_t* key = s_tab;
+    float* val = reinterpret_cast<float*>(s_tab + cap);
+    for (int i = threadIdx.x; i < cap; i += SH::NT) key[i] = kSlotEmpty;
+    for (int i = threadIdx.x; i < cap * 9; i += SH::NT) val[i] = 0.0f;
+    ClusterTab ct;
+    ct.cap = cap;
+    ct.key_base = (uint32_t)__cvta_generic_to_shared(key);
+    ct.val_base = (uint32_t)__cvta_generic_to_shared(val);
+    cluster_sync_all();  // every part of the table is initialised
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    if (tx < p.g.gx && ty < p.g.gy) backward_tile<SH, kModeCluster, STORE_T>(p, ty * p.g.gx + tx, sm, DetSmem{}, &ct);
+    cluster_sync_all();  // every remote add into this CTA's part has landed
+    for (int i = threadIdx.x; i < cap * 9; i += SH::NT) {
+        const uint32_t id = key[i / 9];
+        const float v = val[i];
+        if (id != kSlotEmpty && v != 0.0f) red_add(p.grad2d + (size_t)id * GSR_REC + (i % 9), v);
+    }
+}
+
 // Counts of the backward traversal (no gradients written): per (warp, splat)
 // step the number of active lanes -> hist[0..32]; hist[33] = active pairs,
 // hist[34] = examined pairs (sum of n_contrib), hist[35] = warp steps with at
@@ -183,6 +211,26 @@ void launch_bwd_lay(int layout, bool store, int tiles, const BwdArgs& a, cudaStr
     }
 }
 
+// Cluster-table slots per CTA (40 bytes each).
+constexpr int kClusterSlots = 1024;
+
+template <int LAYOUT, int PPT, bool STORE_T>
+int launch_cluster(const BwdArgs& a, cudaStream_t s) {
+    using SH = Shape<16, 16, LAYOUT, PPT>;
+    constexpr size_t dyn = (size_t)kClusterSlots * 10 * sizeof(uint32_t);
+    auto k = backward_cluster_kernel<SH, STORE_T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const dim3 grid((unsigned)((a.g.gx + 1) / 2 * 2), (unsigned)((a.g.gy + 1) / 2 * 2));
+    k<<<grid, SH::NT, dyn, s>>>(a, kClusterSlots);
+    return check_launch();
+}
+
+template <int LAYOUT, int PPT>
+int launch_cluster_store(bool store, const BwdArgs& a, cudaStream_t s) {
+    return store ? launch_cluster<LAYOUT, PPT, true>(a, s) : launch_cluster<LAYOUT, PPT, false>(a, s);
+}
+
 template <int MODE>
 void launch_bwd_mode(int ppt, int layout, bool store, int tiles, const BwdArgs& a, cudaStream_t s) {
     if (ppt == 2) launch_bwd_lay<MODE, 2>(layout, store, tiles, a, s);
@@ -193,7 +241,7 @@ void launch_bwd_mode(int ppt, int layout, bool store, int tiles, const BwdArgs& 
 
 // Options check shared with the batched entry point.
 int check_bwd_opts(const gsr_backward_opts& o) {
-    if (o.reduce_mode < GSR_REDUCE_PLAIN || o.reduce_mode > GSR_REDUCE_BLOCK) return GSR_EINVAL;
+    if (o.reduce_mode < GSR_REDUCE_PLAIN || o.reduce_mode > GSR_REDUCE_CLUSTER) return GSR_EINVAL;
     if (o.threshold < 0 || o.threshold > 33 || (o.lane_layout != 0 && o.lane_layout != 1)) return GSR_EINVAL;
     if (o.store_T != 0 && o.store_T != 1) return GSR_EINVAL;
     if (o.pixels_per_thread < 0 || o.pixels_per_thread > 2) return GSR_EINVAL;
@@ -253,7 +301,10 @@ extern "C" int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32
         case GSR_REDUCE_PLAIN: launch_bwd_lay<GSR_REDUCE_PLAIN, 1>(o.lane_layout, st, tiles, a, s); break;
         case GSR_REDUCE_WARP: launch_bwd_mode<GSR_REDUCE_WARP>(ppt, o.lane_layout, st, tiles, a, s); break;
         case GSR_REDUCE_HYBRID: launch_bwd_mode<GSR_REDUCE_HYBRID>(ppt, o.lane_layout, st, tiles, a, s); break;
-        default: launch_bwd_mode<GSR_REDUCE_BLOCK>(ppt, o.lane_layout, st, tiles, a, s); break;
+        case GSR_REDUCE_BLOCK: launch_bwd_mode<GSR_REDUCE_BLOCK>(ppt, o.lane_layout, st, tiles, a, s); break;
+        default:
+            if (ppt == 2) return o.lane_layout ? launch_cluster_store<1, 2>(st, a, s) : launch_cluster_store<0, 2>(st, a, s);
+            return o.lane_layout ? launch_cluster_store<1, 1>(st, a, s) : launch_cluster_store<0, 1>(st, a, s);
     }
     return check_launch();
 }

@@ -149,6 +149,7 @@ extern "C" int gsr_backward_batched(int32_t n_views, const gsr_view* views, cons
     if (opts) o = *opts;
     if (n_views <= 0 || n_views > 256 || n_items < 0 || !views || !counter || (n_items > 0 && !items)) return GSR_EINVAL;
     if (check_bwd_opts(o) != GSR_OK || ctas_per_sm < 0) return GSR_EINVAL;
+    if (o.reduce_mode == GSR_REDUCE_CLUSTER) return GSR_EINVAL;  // single-view launches only
     cudaStream_t s = (cudaStream_t)stream_;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return cuda_fail(e);

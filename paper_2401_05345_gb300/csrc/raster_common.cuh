@@ -193,6 +193,66 @@ struct DetSmem {
     uint32_t* slot;     // [B] entry slot of staged entry k
 };
 
+// Cluster tier: a 2 x 2 cluster of tile CTAs pre-reduces its warps' splat
+// gradients in a hash table spread over the four CTAs' shared memory
+// (distributed shared memory); every splat id has one owner CTA and one slot
+// there, and each CTA flushes its part with one global red per (cluster,
+// splat, parameter) once the whole cluster is done.
+constexpr int kModeCluster = 5;
+constexpr uint32_t kSlotEmpty = 0xffffffffu;
+constexpr int kClusterProbe = 16;  // slots tried before falling back to a global red
+
+struct ClusterTab {
+    uint32_t key_base;  // shared::cta addresses of this CTA's key[cap] (every
+    uint32_t val_base;  // CTA of the cluster has them at the same offsets) and val[cap][9]
+    int cap;            // slots per CTA (a power of two)
+};
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Address, in the cluster's shared window, of shared::cta address `la` of
+// CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_map(uint32_t la, uint32_t rank) {
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(rank));
+    return ra;
+}
+
+__device__ __forceinline__ uint32_t dsm_cas(uint32_t addr, uint32_t cmp, uint32_t val) {
+    uint32_t old;
+    asm volatile("atom.shared::cluster.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "r"(addr), "r"(cmp), "r"(val)
+                 : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void dsm_red_add(uint32_t addr, float v) {
+    asm volatile("red.shared::cluster.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+// Every thread of every CTA of the cluster: writes before it are visible to
+// the cluster after it.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Slot of splat `id` in the cluster table (claimed if new), as (owner CTA,
+// slot), or -1 when kClusterProbe slots are taken by other ids.
+__device__ __forceinline__ int cluster_slot(const ClusterTab& ct, uint32_t id, uint32_t& owner) {
+    const uint32_t h = id * 0x9E3779B1u;
+    owner = h >> 30;
+    uint32_t s = (h >> 8) & (uint32_t)(ct.cap - 1);
+    for (int pr = 0; pr < kClusterProbe; ++pr) {
+        const uint32_t old = dsm_cas(cluster_map(ct.key_base + 4u * s, owner), kSlotEmpty, id);
+        if (old == kSlotEmpty || old == id) return (int)s;
+        s = (s + 1u) & (uint32_t)(ct.cap - 1);
+    }
+    return -1;
+}
+
 // Slot of the (tile, Gaussian) entry in the per-Gaussian layout: the
 // Gaussian's first slot plus the tile's row-major rank inside its rectangle
 // (the order binning emits the entries in).
@@ -243,7 +303,8 @@ __device__ __forceinline__ void pair_grads(const SplatEval& e, float4 a, float4 
 // it; shared storage is reused across calls.
 template <class SH, int MODE, bool STORE_T>
 __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, BwdSmem<SH::B, MODE>& sm,
-                                              DetSmem det = DetSmem{nullptr, nullptr, nullptr}) {
+                                              DetSmem det = DetSmem{nullptr, nullptr, nullptr},
+                                              const ClusterTab* ct = nullptr) {
     constexpr int B = SH::B, NT = SH::NT;
     constexpr int PPT = B / NT;
     static_assert(MODE != GSR_REDUCE_PLAIN || PPT == 1, "the plain tier keeps one pixel per thread");
@@ -371,7 +432,18 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                     const bool dense = (MODE == GSR_REDUCE_WARP) || (__popc(m) >= p.threshold);
                     if (dense) {
                         const float z = reduce9(v, lane);
-                        if (rparam < 9) {
+                        if (MODE == kModeCluster) {
+                            uint32_t owner = 0;
+                            int slot = -1;
+                            if (lane == 0) slot = cluster_slot(*ct, sm.id[k], owner);
+                            slot = __shfl_sync(kFull, slot, 0);
+                            owner = __shfl_sync(kFull, owner, 0);
+                            if (rparam < 9) {
+                                if (slot >= 0)
+                                    dsm_red_add(cluster_map(ct->val_base + 4u * (uint32_t)(slot * 9 + rparam), owner), z);
+                                else red_add(rec + rparam, z);
+                            }
+                        } else if (rparam < 9) {
                             if (MODE == GSR_REDUCE_BLOCK) atomicAdd(&sm.acc[k * 9 + rparam], z);
                             else red_add(rec + rparam, z);
                         }

@@ -18,8 +18,9 @@ LIB_PATH = os.path.join(_HERE, "libgsr.so")
 GSR_OK, GSR_EINVAL, GSR_ECAPACITY, GSR_ECUDA, GSR_ETIMEOUT, GSR_ESCRATCH, GSR_ELIMIT = 0, -1, -2, -3, -4, -5, -6
 STATIC_BIN_MAX_GAUSSIANS, STATIC_BIN_MAX_KEYS = 1 << 20, 1 << 22
 GSR_REC = 12
-REDUCE_PLAIN, REDUCE_WARP, REDUCE_HYBRID, REDUCE_BLOCK = 0, 1, 2, 3
-REDUCE_NAMES = {"plain": REDUCE_PLAIN, "warp": REDUCE_WARP, "hybrid": REDUCE_HYBRID, "block": REDUCE_BLOCK}
+REDUCE_PLAIN, REDUCE_WARP, REDUCE_HYBRID, REDUCE_BLOCK, REDUCE_CLUSTER = 0, 1, 2, 3, 4
+REDUCE_NAMES = {"plain": REDUCE_PLAIN, "warp": REDUCE_WARP, "hybrid": REDUCE_HYBRID, "block": REDUCE_BLOCK,
+                "cluster": REDUCE_CLUSTER}
 
 
 class GsrError(RuntimeError):

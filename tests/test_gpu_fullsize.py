@@ -19,7 +19,7 @@ from paper_2401_05345_gb300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 TIERS = [("plain", 0, 1, 1), ("warp", 0, 1, 1), ("hybrid", 12, 1, 1), ("hybrid", 8, 0, 1), ("block", 0, 1, 1),
-         ("hybrid", 12, 1, 2), ("warp", 0, 0, 2), ("block", 0, 1, 2)]
+         ("hybrid", 12, 1, 2), ("warp", 0, 0, 2), ("block", 0, 1, 2), ("cluster", 12, 1, 2), ("cluster", 0, 0, 1)]
 BG = (0.0, 0.0, 0.0)
 
 

@@ -212,7 +212,8 @@ def test_forward_matches_oracle(dev, orc, name, bg):
 
 TIERS = [("plain", 0, 0, 1), ("warp", 0, 0, 1), ("warp", 0, 1, 1), ("hybrid", 8, 0, 1), ("hybrid", 16, 1, 1),
          ("hybrid", 33, 0, 1), ("block", 0, 0, 1), ("block", 12, 1, 1),
-         ("warp", 0, 0, 2), ("hybrid", 8, 1, 2), ("hybrid", 33, 1, 2), ("block", 0, 1, 2), ("block", 12, 0, 2)]
+         ("warp", 0, 0, 2), ("hybrid", 8, 1, 2), ("hybrid", 33, 1, 2), ("block", 0, 1, 2), ("block", 12, 0, 2),
+         ("cluster", 0, 0, 1), ("cluster", 12, 1, 1), ("cluster", 0, 1, 2), ("cluster", 8, 0, 2)]
 
 
 @pytest.mark.parametrize("store_T", [True, False])
