@@ -533,9 +533,10 @@ def run_ours(args):
     return 0
 
 
-# Kernels of libgsr launched per step: preprocess, tile count, exclusive scan
-# (2 CUB kernels), duplicate, radix sort (CUB: 1 histogram + 6 onesweep passes
-# for a 45-bit key), ranges, forward, L1 loss, backward, backward projection.
+# Kernels of libgsr launched per step: preprocess; binning (depth keys, three
+# column scans and three radix scatter passes, rectangles, slice bounds,
+# block x tile counts, column scan + ranges, placement); forward, L1 loss,
+# backward, backward projection.
 LAUNCHES_PER_STEP = 17
 
 
