@@ -1,4 +1,5 @@
-"""ctypes wrapper of the FP64 CPU oracle (``gsr_oracle.c``).
+"""ctypes wrapper of the FP64 CPU oracle (``gsr_oracle.c``: the splat
+rasterizer; ``cube_oracle.c``: cube-map texture sampling and its gradient).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, the smoke check and the
 benchmark's CPU-baseline leg.  It shares no code with the CUDA library or its
@@ -15,6 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gsr_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "cube_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -22,10 +24,10 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc: -O2, no FMA contraction, no fast-math, so
     x86 and Arm hosts evaluate the same IEEE operations."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                               "-fPIC", "-shared", "-o", tmp] + _SRCS + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -42,6 +44,13 @@ def _load():
     if _lib is not None:
         return _lib
     lib = ctypes.CDLL(build())
+    F = POINTER(c_float)
+    lib.orc_cube_taps.argtypes = [c_longlong, F, c_int, POINTER(c_int), POINTER(c_longlong), POINTER(c_double)]
+    lib.orc_cube_taps.restype = None
+    lib.orc_cube_forward.argtypes = [c_longlong, F, c_int, F, POINTER(c_double), POINTER(c_double)]
+    lib.orc_cube_forward.restype = None
+    lib.orc_cube_backward.argtypes = [c_longlong, F, F, c_int, POINTER(c_double), POINTER(c_double)]
+    lib.orc_cube_backward.restype = None
     D = POINTER(c_double)
     I = POINTER(c_int)
     U32 = POINTER(c_uint32)
@@ -246,3 +255,48 @@ def scatter_add9(idx, vals, rows):
     out = np.zeros((rows, 9))
     np.add.at(out, np.asarray(idx, np.int64), np.asarray(vals, np.float64))
     return out
+
+
+# ----------------------------------------------------------------------------
+# cube-map texture sampling (cube_oracle.c)
+# ----------------------------------------------------------------------------
+def _f32(a):
+    return np.ascontiguousarray(a, np.float32)
+
+
+def cube_taps(dirs, R):
+    """Per direction [n,3] (FP32): face (-1 = no sample), linear tap texels
+    [n,4] (face*R*R + row*R + column) and tap weights [n,4] (FP64)."""
+    lib = _load()
+    d = _f32(dirs).reshape(-1, 3)
+    n = len(d)
+    face = np.zeros(max(n, 1), np.int32)
+    texel = np.zeros((max(n, 1), 4), np.int64)
+    w = np.zeros((max(n, 1), 4), np.float64)
+    lib.orc_cube_taps(n, _p(d, c_float), R, _p(face, c_int), _p(texel, c_longlong), _p(w))
+    return face[:n], texel[:n], w[:n]
+
+
+def cube_forward(dirs, R, tex):
+    """Bilinear cube-map samples [n,3] (FP64) and their scales (sum of the
+    absolute terms).  tex: [6,R,R,4] FP32."""
+    lib = _load()
+    d = _f32(dirs).reshape(-1, 3)
+    t = _f32(tex)
+    assert t.shape == (6, R, R, 4)
+    n = len(d)
+    out = np.zeros((max(n, 1), 3))
+    sc = np.zeros((max(n, 1), 3))
+    lib.orc_cube_forward(n, _p(d, c_float), R, _p(t, c_float), _p(out), _p(sc))
+    return out[:n], sc[:n]
+
+
+def cube_backward(dirs, dL, R):
+    """Texture gradient [6,R,R,3] (FP64) of sum(dL * sample) and its scale."""
+    lib = _load()
+    d = _f32(dirs).reshape(-1, 3)
+    g = _f32(dL).reshape(-1, 3)
+    grad = np.zeros((6, R, R, 3))
+    sc = np.zeros((6, R, R, 3))
+    lib.orc_cube_backward(len(d), _p(d, c_float), _p(g, c_float), R, _p(grad), _p(sc))
+    return grad, sc

@@ -225,3 +225,45 @@ def batched_workload(seed=0, sizes=(50_000, 200_000, 600_000, 1_200_000), views=
         cam = sphere_cameras(rng, 1, (0.0, 0.0, 0.0), 4.0, [(w, h)])[0]
         jobs.append((s, cam))
     return scenes, jobs
+
+
+def cubemap_workload(seed=0, width=1024, height=1024, R=128, bumps=48):
+    """Inputs of the cube-map texture workload (learning an environment map
+    from images of a reflective object, the NvDiffRec workload): an
+    orthographic view of a mirror sphere filling 90 % of the shorter image
+    side, its normals perturbed by seeded bumps (mesh detail), and per pixel
+    the reflection of the view ray (0, 0, -1) about the normal, FP32 [H,W,3]
+    (zero outside the sphere: no sample).  Also a U[0,1] cube map [6,R,R,4]
+    (fourth channel 0) and an L1-type upstream gradient [H,W,3] in {-1,+1}."""
+    rng = np.random.default_rng(seed + 4242)
+    ys, xs = np.mgrid[0:height, 0:width].astype(np.float64)
+    rad = 0.45 * min(width, height)
+    px = (xs + 0.5 - width / 2.0) / rad
+    py = (ys + 0.5 - height / 2.0) / rad
+    r2 = px * px + py * py
+    inside = r2 < 1.0
+    nz = np.sqrt(np.clip(1.0 - r2, 0.0, 1.0))
+    n = np.stack([px, -py, nz], -1)
+    # bumps: gradient of a sum of Gaussians over the image plane, added to the normal's tangent part
+    c = rng.uniform(-0.9, 0.9, size=(bumps, 2))
+    s = rng.uniform(0.05, 0.2, size=bumps)
+    a = rng.uniform(-0.15, 0.15, size=bumps)
+    gx = np.zeros_like(px)
+    gy = np.zeros_like(py)
+    for k in range(bumps):
+        dx, dy = px - c[k, 0], py - c[k, 1]
+        e = a[k] * np.exp(-(dx * dx + dy * dy) / (2 * s[k] * s[k])) / (s[k] * s[k])
+        gx -= e * dx
+        gy -= e * dy
+    n[..., 0] -= gx
+    n[..., 1] += gy
+    n /= np.linalg.norm(n, axis=-1, keepdims=True)
+    v = np.array([0.0, 0.0, -1.0])
+    vn = n @ v
+    r = v[None, None, :] - 2.0 * vn[..., None] * n
+    r /= np.linalg.norm(r, axis=-1, keepdims=True)
+    dirs = np.where(inside[..., None], r, 0.0).astype(np.float32)
+    tex = rng.uniform(0.0, 1.0, size=(6, R, R, 4)).astype(np.float32)
+    tex[..., 3] = 0.0
+    dL = np.where(rng.uniform(size=(height, width, 3)) < 0.5, -1.0, 1.0).astype(np.float32)
+    return dirs, tex, dL

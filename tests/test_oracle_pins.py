@@ -532,3 +532,142 @@ def test_scatter_add_definition_by_brute_force(orc):
         for q in range(9):
             ref[d, q] += vals[i, q]
     np.testing.assert_allclose(got, ref, rtol=1e-14, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# cube-map texture sampling and its gradient (cube_oracle.c)
+# ----------------------------------------------------------------------------
+
+def _dirs(rng, n):
+    d = rng.normal(size=(n, 3)).astype(np.float32)
+    return d
+
+
+def test_cube_face_is_the_major_axis(orc):
+    """Face = axis of the largest |component| (ties: x, then y), positive for
+    components >= 0: brute force over random and tied directions; all-zero
+    directions (either sign) have no sample."""
+    rng = np.random.default_rng(0)
+    d = _dirs(rng, 4000)
+    d[:200, 1] = d[:200, 0]                      # |x| == |y|
+    d[200:400, 2] = -d[200:400, 1]               # |y| == |z|
+    d[400:450] = [[0.0, -0.0, 0.0]] * 50         # no sample
+    d[450:500] = [[-0.0, 0.0, 0.0]] * 50
+    d[450:500, 0] = np.float32(-0.0)
+    d[450:500, 2] = np.float32(0.0)
+    face, texel, w = orc.cube_taps(d, 16)
+    a = np.abs(d)
+    for i, v in enumerate(d):
+        if not (a[i].max() > 0):
+            assert face[i] == -1
+            continue
+        if a[i, 0] >= a[i, 1] and a[i, 0] >= a[i, 2]:
+            ax = 0
+        elif a[i, 1] >= a[i, 2]:
+            ax = 1
+        else:
+            ax = 2
+        pos = not np.signbit(v[ax]) or v[ax] == 0.0
+        assert face[i] == 2 * ax + (0 if pos else 1), (i, v, face[i])
+
+
+def test_cube_axis_directions_hit_the_face_centre(orc):
+    """Along each axis (s, t) = (1/2, 1/2): u = v = R/2 - 1/2, so the four
+    centre texels of the face get 1/4 each."""
+    R = 8
+    d = np.float32([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]]) * 3.0
+    face, texel, w = orc.cube_taps(d, R)
+    for f in range(6):
+        assert face[f] == f
+        cols = sorted({int(t % R) for t in texel[f]})
+        rows = sorted({int(t // R % R) for t in texel[f]})
+        assert cols == [R // 2 - 1, R // 2] and rows == [R // 2 - 1, R // 2]
+        np.testing.assert_allclose(w[f], 0.25, rtol=0, atol=0)
+
+
+def test_cube_coordinates_are_the_projection_onto_the_face(orc):
+    """On every face the texel coordinates are the central projection of d
+    onto the face: sampling a texture that stores each texel's own column and
+    row returns (u, v) = (s R - 1/2, t R - 1/2) with s - 1/2 and t - 1/2
+    equal to +-1/2 times the two minor components over the major one, each
+    coordinate on a different minor axis.  (Which sign each face uses is the
+    OpenGL convention and is not pinned here.)"""
+    R = 64
+    tex = np.zeros((6, R, R, 4), np.float32)
+    tex[..., 0] = np.arange(R, dtype=np.float32)[None, None, :]
+    tex[..., 1] = np.arange(R, dtype=np.float32)[None, :, None]
+    rng = np.random.default_rng(1)
+    for f in range(6):
+        ax, sgn = f // 2, (1.0 if f % 2 == 0 else -1.0)
+        minor = [a for a in range(3) if a != ax]
+        d = rng.uniform(-0.9, 0.9, size=(300, 3))
+        d[:, ax] = sgn
+        d = d.astype(np.float32)
+        out, _ = orc.cube_forward(d, R, tex)
+        face, _, _ = orc.cube_taps(d, R)
+        assert np.all(face == f)
+        s = (out[:, 0] + 0.5) / R - 0.5
+        t = (out[:, 1] + 0.5) / R - 0.5
+        ratios = d[:, minor].astype(np.float64) / np.abs(d[:, [ax]].astype(np.float64))
+        for coord in (s, t):
+            coef, *_ = np.linalg.lstsq(ratios, coord, rcond=None)
+            assert sorted(np.round(np.abs(coef), 6)) == [0.0, 0.5], (f, coef)
+        cs, *_ = np.linalg.lstsq(ratios, s, rcond=None)
+        ct, *_ = np.linalg.lstsq(ratios, t, rcond=None)
+        assert np.argmax(np.abs(cs)) != np.argmax(np.abs(ct))
+
+
+def test_cube_constant_texture_samples_the_constant(orc):
+    """Bilinear weights sum to 1, also where taps are clamped at face edges."""
+    R = 5
+    tex = np.full((6, R, R, 4), 0.375, np.float32)
+    tex[..., 1] = 2.0
+    tex[..., 2] = -1.5
+    rng = np.random.default_rng(2)
+    d = _dirs(rng, 3000)
+    d[:100] = np.float32([1, 0.999, -0.9999])      # near corners: clamped taps
+    out, _ = orc.cube_forward(d, R, tex)
+    np.testing.assert_allclose(out, np.broadcast_to([0.375, 2.0, -1.5], out.shape), rtol=1e-15, atol=1e-15)
+
+
+def test_cube_worked_example(orc):
+    """d = (1, 0.25, -0.5), R = 4: face +x, s = (0.5 + 1)/2 = 0.75, t =
+    (-0.25 + 1)/2 = 0.375, u = 2.5, v = 1.0: taps (2,1), (3,1) with 1/2 each,
+    (2,2), (3,2) with 0."""
+    face, texel, w = orc.cube_taps(np.float32([[1.0, 0.25, -0.5]]), 4)
+    assert face[0] == 0
+    assert [(int(t % 4), int(t // 4 % 4)) for t in texel[0]] == [(2, 1), (3, 1), (2, 2), (3, 2)]
+    np.testing.assert_array_equal(w[0], [0.5, 0.5, 0.0, 0.0])
+
+
+def test_cube_backward_is_the_derivative_of_the_forward(orc):
+    """The sample is linear in the texture, so the central difference of
+    L = sum(dL * sample) in one texel channel is exact (up to FP64 rounding)
+    and must equal the backward's gradient of that texel channel."""
+    R = 6
+    rng = np.random.default_rng(3)
+    d = _dirs(rng, 500)
+    d[:20] = 0.0
+    dL = rng.normal(size=(500, 3)).astype(np.float32)
+    tex = (rng.integers(0, 64, size=(6, R, R, 4)) / 64.0).astype(np.float32)  # +-0.5 stays exact
+    grad, _ = orc.cube_backward(d, dL, R)
+    for _ in range(40):
+        f, j, i, c = rng.integers(6), rng.integers(R), rng.integers(R), rng.integers(3)
+        tp, tm = tex.copy(), tex.copy()
+        tp[f, j, i, c] += 0.5
+        tm[f, j, i, c] -= 0.5
+        lp = float((orc.cube_forward(d, R, tp)[0] * dL).sum())
+        lm = float((orc.cube_forward(d, R, tm)[0] * dL).sum())
+        assert abs((lp - lm) - grad[f, j, i, c]) <= 1e-12 * (1 + abs(grad[f, j, i, c])), (f, j, i, c)
+
+
+def test_cube_gradient_sum_rule(orc):
+    """Weights sum to 1 per sample, so the texture gradient summed over all
+    texels equals the upstream gradient summed over the samples."""
+    rng = np.random.default_rng(4)
+    d = _dirs(rng, 2000)
+    d[::7] = 0.0
+    dL = rng.normal(size=(2000, 3)).astype(np.float32)
+    grad, _ = orc.cube_backward(d, dL, 9)
+    act = np.abs(d).max(1) > 0
+    np.testing.assert_allclose(grad.reshape(-1, 3).sum(0), dL[act].astype(np.float64).sum(0), rtol=1e-12)
