@@ -426,6 +426,49 @@ def run_ours(args):
             row[name] = statistics.median(ts)
         scat[str(distinct)] = row
 
+    # cube-map texture workload (environment-map learning, Sec. VI): forward
+    # sample and the texture-gradient accumulation tiers, L2 flushed before
+    # each; two mip levels of the cube map (moderate and heavy contention)
+    from paper_2401_05345_gb300 import scenes as S
+    tex_results = {}
+    for TR in (128, 32):
+        dirs_np, tex_np, dlt_np = S.cubemap_workload(0, R=TR)
+        TH, TW = dirs_np.shape[:2]
+        dirs_t = torch.from_numpy(dirs_np).to(dev)
+        tex_t = torch.from_numpy(tex_np).to(dev)
+        dlt_t = torch.from_numpy(dlt_np).to(dev)
+        tout = torch.zeros((TH, TW, 3), device=dev)
+        tgrad = torch.zeros((6, TR, TR, 4), device=dev)
+        n_tex_px = int((np.abs(dirs_np).max(-1) > 0).sum())
+
+        def time_tex(fn, r=5, tgrad=tgrad):
+            ts = []
+            for i in range(r + 1):
+                tgrad.zero_()
+                flush()
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                fn()
+                a1.record(stream)
+                a1.synchronize()
+                if i:
+                    ts.append(a0.elapsed_time(a1))
+            return statistics.median(ts)
+        tex_ms = {"forward": time_tex(lambda: gsr.gsr_cube_forward(TW, TH, dirs_t, TR, tex_t, tout))}
+        for name, thr in (("plain", 0), ("plain_v4", 0), ("serial", 0), ("serial", 2), ("serial", 8),
+                          ("sorted", 0), ("block", 0)):
+            tex_ms[f"backward_{name}_thr{thr}"] = time_tex(
+                lambda name=name, thr=thr: gsr.gsr_cube_backward(TW, TH, dirs_t, dlt_t, TR, tgrad, name, thr))
+        tex_best = min((v, k) for k, v in tex_ms.items() if k.startswith("backward"))
+        tex_results[f"R{TR}"] = {
+            "workload": f"mirror sphere {TW}x{TH}, {n_tex_px} sampled pixels, cube map 6x{TR}x{TR} (RGB + pad), "
+                        f"{4 * n_tex_px / (6 * TR * TR):.1f} taps per texel",
+            "ms": tex_ms, "best": tex_best[1],
+            "updates_per_s_plain": 12 * n_tex_px / (tex_ms["backward_plain_thr0"] / 1e3),
+            "updates_per_s_best": 12 * n_tex_px / (tex_best[0] / 1e3),
+            "speedup_best_vs_plain": tex_ms["backward_plain_thr0"] / tex_best[0],
+            "plain_frac_of_l2_distinct_red": (12 * n_tex_px / (tex_ms["backward_plain_thr0"] / 1e3)) / red["distinct"]}
+
     # end to end through host buffers: H2D of the step's inputs, D2H of the loss
     host_in = [t.detach().cpu().pin_memory() for t in sc.tensors()] + [target.cpu().pin_memory()]
     dev_in = sc.tensors() + [target]
@@ -511,6 +554,7 @@ def run_ours(args):
             },
             "binning_ms": {"hand_written_sorts": t_bin_own, "cub_radix_sorts": t_bin_lib,
                            "note": "same outputs; each includes its one host sync for the key count"},
+            "texture_gradient": tex_results,
             "l2_red_adds_per_s": red,
             "divergent_accumulation_ms": {"items": n_items, "records": rows,
                                           "by_distinct_destinations_per_warp": scat},

@@ -130,6 +130,43 @@ typedef struct gsr_view {
     int32_t reserved;
 } gsr_view;
 
+/*
+ * Cube-map texture workload (the NvDiffRec workload of Sec. VI: learning an
+ * environment map from images).  Each pixel with a non-zero direction
+ * samples the cube map bilinearly; the backward adds w_k * dL/dout to the
+ * gradient of each of the pixel's 4 texels.  The lanes of a warp update
+ * different but overlapping texels, the divergent case of Sec. V-A1.
+ * Conventions (OpenGL cube maps): face = major axis of the direction (ties:
+ * x, then y; positive for components >= 0), faces +x -x +y -y +z -z = 0..5;
+ * (sc, tc, ma): +x (-z, -y, |x|), -x (z, -y, |x|), +y (x, z, |y|),
+ * -y (x, -z, |y|), +z (x, -y, |z|), -z (-x, -y, |z|); s = (sc/ma + 1)/2,
+ * t = (tc/ma + 1)/2; u = s R - 1/2, v = t R - 1/2 evaluated in FP32 with one
+ * rounding per operation; taps floor(u) + {0,1} x floor(v) + {0,1} clamped to
+ * the face; weights (1-fu)(1-fv), fu(1-fv), (1-fu)fv, fu fv.
+ * Layouts: dirs, out, dL_dout [height][width][3] float; tex and grad_tex
+ * [6][R][R][4] float (16-byte aligned; channel 3 unused, its gradient stays
+ * untouched).  grad_tex accumulates.  6 R^2 < 2^31.
+ */
+enum {
+    GSR_TEX_PLAIN = 0,     /* 3 scalar atomicAdd per tap (the baseline) */
+    GSR_TEX_PLAIN_V4 = 1,  /* one red.global.add.v4.f32 per tap */
+    GSR_TEX_SERIAL = 2,    /* per tap: lanes on the same texel (match mask) of
+                              at least `threshold` lanes are summed by their
+                              lowest lane, which pulls each peer in turn and
+                              issues one v4 red (SW-S, Sec. V-A1); smaller
+                              groups issue per-lane v4 reds */
+    GSR_TEX_SORTED = 3,    /* per tap: the warp's (texel, lane) pairs are
+                              sorted, summed per run, one v4 red per run */
+    GSR_TEX_BLOCK = 4      /* per 16x16-pixel CTA: a 1024-slot shared-memory
+                              table (8 probes, then a direct red), flushed
+                              with one v4 red per texel at the end */
+};
+int gsr_cube_forward(int32_t width, int32_t height, const float* dirs, int32_t R, const float* tex,
+                     float* out, gsr_stream_t stream);
+/* threshold: 0..33, used by GSR_TEX_SERIAL. */
+int gsr_cube_backward(int32_t width, int32_t height, const float* dirs, const float* dL_dout, int32_t R,
+                      float* grad_tex, int32_t method, int32_t threshold, gsr_stream_t stream);
+
 const char* gsr_status_string(int status);
 /* Text of the last CUDA error seen by the library in this thread. */
 const char* gsr_last_cuda_error(void);

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsr.so")
-SOURCES = ["project.cu", "binning.cu", "binsort.cu", "raster.cu", "raster_batched.cu", "scatter.cu", "misc.cu"]
+SOURCES = ["project.cu", "binning.cu", "binsort.cu", "raster.cu", "raster_batched.cu", "scatter.cu", "texture.cu", "misc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -102,4 +102,29 @@ __device__ __forceinline__ void red_add(float* addr, float v) {
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(v) : "memory");
 }
 
+// One vector red of four floats (addr 16-byte aligned).
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+// Bitonic sort of the warp's (key, src) pairs in ascending (key, src) order;
+// lane L ends with the L-th pair.
+__device__ __forceinline__ void warp_sort_pairs(uint32_t& key, uint32_t& src, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint32_t ok = __shfl_xor_sync(kFull, key, j);
+            const uint32_t os = __shfl_xor_sync(kFull, src, j);
+            const bool take_min = (((lane & k) == 0) == ((lane & j) == 0));
+            const bool other_smaller = (ok < key) || (ok == key && os < src);
+            if (take_min == other_smaller) {
+                key = ok;
+                src = os;
+            }
+        }
+    }
+}
+
 }  // namespace gsr

@@ -72,22 +72,7 @@ scatter9_kernel(long long n, const uint32_t* __restrict__ idx, const float* __re
     }
     // METHOD 2: bitonic sort of (destination, source lane) over the warp
     uint32_t key = d, src = (uint32_t)lane;
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const uint32_t ok = __shfl_xor_sync(kFull, key, j);
-            const uint32_t os = __shfl_xor_sync(kFull, src, j);
-            const bool up = ((lane & k) == 0);
-            const bool lower = ((lane & j) == 0);
-            const bool take_min = (up == lower);
-            const bool other_smaller = (ok < key) || (ok == key && os < src);
-            if (take_min == other_smaller) {
-                key = ok;
-                src = os;
-            }
-        }
-    }
+    warp_sort_pairs(key, src, lane);
     float y[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) y[q] = __shfl_sync(kFull, x[q], (int)src);

@@ -111,12 +111,14 @@ def lib():
                                              POINTER(c_float), P, P, P, P, P, POINTER(BackwardOpts), P]
     L.gsr_scatter_add9.argtypes = [c_int64, P, P, P, c_int32, c_int32, c_int32, P]
     L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
+    L.gsr_cube_forward.argtypes = [c_int32, c_int32, P, c_int32, P, P, P]
+    L.gsr_cube_backward.argtypes = [c_int32, c_int32, P, P, c_int32, P, c_int32, c_int32, P]
     for name in ("gsr_preprocess", "gsr_bin_scratch_bytes", "gsr_bin_sort", "gsr_bin_sort_static",
                  "gsr_bin_scratch_bytes_library", "gsr_bin_sort_library",
                  "gsr_forward", "gsr_backward",
                  "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red",
                  "gsr_activate", "gsr_activate_backward", "gsr_scatter_add9", "gsr_entry_offsets_scratch_bytes",
-                 "gsr_entry_offsets", "gsr_backward_deterministic"):
+                 "gsr_entry_offsets", "gsr_backward_deterministic", "gsr_cube_forward", "gsr_cube_backward"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -285,3 +287,17 @@ def gsr_bench_red(pattern, blocks, iters, buffer, stream=None) -> int:
     _check("gsr_bench_red", lib().gsr_bench_red(pattern, blocks, iters, _ptr(buffer), buffer.numel(),
                                                 ctypes.byref(adds), _stream(stream)))
     return int(adds.value)
+
+
+TEX_METHODS = {"plain": 0, "plain_v4": 1, "serial": 2, "sorted": 3, "block": 4}
+
+
+def gsr_cube_forward(width, height, dirs, R, tex, out, stream=None):
+    _check("gsr_cube_forward", lib().gsr_cube_forward(width, height, _ptr(dirs), R, _ptr(tex), _ptr(out),
+                                                      _stream(stream)))
+
+
+def gsr_cube_backward(width, height, dirs, dL_dout, R, grad_tex, method="sorted", threshold=0, stream=None):
+    m = TEX_METHODS[method] if isinstance(method, str) else int(method)
+    _check("gsr_cube_backward", lib().gsr_cube_backward(width, height, _ptr(dirs), _ptr(dL_dout), R, _ptr(grad_tex),
+                                                        m, threshold, _stream(stream)))
