@@ -417,81 +417,100 @@ bounds_kernel(int n, int nwarps, const uint2* __restrict__ rects, const uint32_t
 }
 
 // Per-warp staging of 32 consecutive depth-ordered Gaussians: their
-// rectangles, the exclusive prefix of their areas (entry e of the 32 belongs
-// to the last Gaussian whose prefix is <= e) and a multiplier that divides
-// by the rectangle width.
+// rectangles, the exclusive prefixes of their entry counts (areas) and of
+// their row counts (rectangle heights), ids and depth keys.  Work is handed
+// to lanes one rectangle row at a time: row unit u of the batch belongs to
+// the last Gaussian whose row prefix is <= u.
 struct WarpBatch {
-    uint32_t pre[33];
+    uint32_t pre[32];    // entries before Gaussian j in the batch
+    uint32_t rpre[33];   // rows before Gaussian j; rpre[32] = rows of the batch
     int x0[32], wd[32], y0[32];
-    uint32_t mul[32];
     uint32_t id[32], dk[32];
 };
 
 // Fills the warp's batch (lane = Gaussian k, absent at k >= n); returns the
-// batch's entry count.
+// batch's entry count (and its row count in *rows).
 __device__ __forceinline__ uint32_t stage_batch(WarpBatch& wb, int lane, bool present, uint2 pr, uint32_t id,
-                                                uint32_t dk) {
+                                                uint32_t dk, uint32_t* rows) {
     int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
     if (present) unpack_rect(pr, x0, x1, y0, y1);
     const int wd = x1 - x0;
-    const uint32_t area = (uint32_t)wd * (uint32_t)(y1 - y0);
-    uint32_t incl = area;
+    const uint32_t ht = wd > 0 ? (uint32_t)(y1 - y0) : 0u;
+    const uint32_t area = (uint32_t)wd * ht;
+    uint32_t inc = area, rinc = ht;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
+        const uint32_t t = __shfl_up_sync(kFull, inc, o);
+        const uint32_t r = __shfl_up_sync(kFull, rinc, o);
+        if (lane >= o) {
+            inc += t;
+            rinc += r;
+        }
     }
-    wb.pre[lane] = incl - area;
-    if (lane == 31) wb.pre[32] = incl;
+    wb.pre[lane] = inc - area;
+    wb.rpre[lane] = rinc - ht;
+    if (lane == 31) wb.rpre[32] = rinc;
     wb.x0[lane] = x0;
     wb.wd[lane] = wd;
     wb.y0[lane] = y0;
-    // ceil(2^32 / wd) for wd >= 2: floor(e / wd) = umulhi(e, mul) exactly
-    // while e and wd are below 2^16 (then e * wd < 2^32)
-    wb.mul[lane] = wd > 1 ? (uint32_t)(0xffffffffu / (uint32_t)wd) + 1u : 0u;
     wb.id[lane] = id;
     wb.dk[lane] = dk;
-    __syncwarp();
-    return wb.pre[32];
+    *rows = __shfl_sync(kFull, rinc, 31);
+    return __shfl_sync(kFull, inc, 31);
 }
 
-// Tile (window-relative, or -1 outside the window) of entry e of the batch,
-// and the Gaussian (lane of the batch) it belongs to.
-__device__ __forceinline__ int entry_tile(const WarpBatch& wb, uint32_t e, const Geom& g, int t0, int tw, int& j) {
+// One rectangle row handed to a lane: tiles row_t0 + x for x in [xs, xe)
+// (window-relative tile ids), of Gaussian lane j of the batch, tile row y.
+struct RowWork {
+    int j, y, row_t0, xs, xe;
+};
+
+// Row unit u of the batch, clipped to the warp's entries [e0, e1) (pk =
+// global index of the batch's first entry).  Returns false when nothing of
+// the row lies in the range.
+__device__ __forceinline__ bool row_unit(const WarpBatch& wb, uint32_t u, uint32_t pk, uint32_t e0, uint32_t e1,
+                                         const Geom& g, int t0, RowWork& r) {
     int lo = 0, hi = 31;
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         const int mid = (lo + hi + 1) >> 1;
-        if (wb.pre[mid] <= e) lo = mid; else hi = mid - 1;
+        if (wb.rpre[mid] <= u) lo = mid; else hi = mid - 1;
     }
-    j = lo;
-    const uint32_t local = e - wb.pre[lo];
-    const uint32_t wd = (uint32_t)wb.wd[lo];
-    const uint32_t dy = wd == 1u ? local : (local < 65536u ? __umulhi(local, wb.mul[lo]) : local / wd);
-    const int t = (wb.y0[lo] + (int)dy) * g.gx + wb.x0[lo] + (int)(local - dy * wd) - t0;
-    return (unsigned)t < (unsigned)tw ? t : -1;
+    const int ri = (int)(u - wb.rpre[lo]);
+    const int wd = wb.wd[lo];
+    const uint32_t gp = pk + wb.pre[lo] + (uint32_t)(ri * wd);  // global index of the row's first entry
+    const int xs = e0 > gp ? (int)(e0 - gp) : 0;
+    const int xe = e1 - gp < (uint32_t)wd ? (int)(e1 - gp) : wd;
+    if (gp >= e1 || xe <= xs) return false;
+    r.j = lo;
+    r.y = wb.y0[lo] + ri;
+    r.row_t0 = r.y * g.gx + wb.x0[lo] - t0;
+    r.xs = xs;
+    r.xe = xe;
+    return true;
 }
 
-// Walks the entries [e0, e1) of warp j in depth order, 32 Gaussians at a
-// time, calling f(tile, gaussian lane) for each entry of the window (lanes
-// past the range call f with tile -1, so f may use warp-wide intrinsics).
+// Walks the entries [e0, e1) of one warp in depth order, 32 Gaussians at a
+// time and 32 rectangle rows per round: f(ok, row) on every lane of every
+// round (ok false when the lane has no row), so f may use warp intrinsics.
 template <bool IDS, class F>
-__device__ __forceinline__ void walk_entries(WarpBatch& wb, int lane, int n, uint32_t e0, uint32_t e1, int k,
-                                             const uint2* __restrict__ rects, const uint32_t* __restrict__ order,
-                                             const uint32_t* __restrict__ dkeys, uint32_t pk, const Geom& g, int t0,
-                                             int tw, F&& f) {
+__device__ __forceinline__ void walk_rows(WarpBatch& wb, int lane, int n, uint32_t e0, uint32_t e1, int k,
+                                          const uint2* __restrict__ rects, const uint32_t* __restrict__ order,
+                                          const uint32_t* __restrict__ dkeys, uint32_t pk, const Geom& g, int t0,
+                                          F&& f) {
     while (pk < e1 && k < n) {
         const int kk = k + lane;
         const bool present = kk < n;
+        uint32_t br;
         const uint32_t bt = stage_batch(wb, lane, present, present ? rects[kk] : make_uint2(0u, 0u),
-                                        IDS && present ? order[kk] : 0u, IDS && dkeys && present ? dkeys[kk] : 0u);
-        const uint32_t lo = e0 > pk ? e0 - pk : 0u;
-        const uint32_t hi = e1 - pk < bt ? e1 - pk : bt;
-        for (uint32_t base = lo; base < hi; base += 32) {
-            const uint32_t e = base + lane;
-            int j = 0, t = -1;
-            if (e < hi) t = entry_tile(wb, e, g, t0, tw, j);
-            f(t, j);
+                                        IDS && present ? order[kk] : 0u, IDS && dkeys && present ? dkeys[kk] : 0u,
+                                        &br);
+        __syncwarp();
+        for (uint32_t base = 0; base < br; base += 32) {
+            const uint32_t u = base + lane;
+            RowWork r;
+            const bool ok = u < br && row_unit(wb, u, pk, e0, e1, g, t0, r);
+            f(ok, r);
         }
         __syncwarp();
         pk += bt;
@@ -519,10 +538,14 @@ chunk_hist_kernel(int n, int nb, Geom g, int t0, int tw, const uint2* __restrict
         const uint32_t e0 = (uint32_t)e0l;
         const uint32_t e1 = total - e0 < ew ? total : e0 + ew;
         const int k = (int)wstart[b * kPlaceWarps + w];
-        walk_entries<false>(s_wb[w], lane, n, e0, e1, k, rects, nullptr, nullptr, entry_prefix(apre, boff, k), g, t0,
-                            tw, [&](int t, int) {
-                                if (t >= 0) atomicAdd(&h[t], 1u);
-                            });
+        walk_rows<false>(s_wb[w], lane, n, e0, e1, k, rects, nullptr, nullptr, entry_prefix(apre, boff, k), g, t0,
+                         [&](bool ok, const RowWork& r) {
+                             if (!ok) return;
+                             for (int x = r.xs; x < r.xe; ++x) {
+                                 const int t = r.row_t0 + x;
+                                 if ((unsigned)t < (unsigned)tw) atomicAdd(&h[t], 1u);
+                             }
+                         });
     }
     __syncthreads();
     for (int t = threadIdx.x; t < tw; t += kPlaceThreads) m[(size_t)b * g.tiles + t0 + t] = h[t];
@@ -562,8 +585,12 @@ place_kernel(int n, int nb, Geom g, int t0, int tw, const uint32_t* __restrict__
     __syncthreads();
     // per-warp entry counts of each tile
     if (mine)
-        walk_entries<false>(wb, lane, n, e0, e1, k, rects, nullptr, nullptr, pk, g, t0, tw, [&](int t, int) {
-            if (t >= 0) atomicAdd(&wc[t >> 1], (t & 1) ? 0x10000u : 1u);
+        walk_rows<false>(wb, lane, n, e0, e1, k, rects, nullptr, nullptr, pk, g, t0, [&](bool ok, const RowWork& r) {
+            if (!ok) return;
+            for (int x = r.xs; x < r.xe; ++x) {
+                const int t = r.row_t0 + x;
+                if ((unsigned)t < (unsigned)tw) atomicAdd(&wc[t >> 1], (t & 1) ? 0x10000u : 1u);
+            }
         });
     __syncthreads();
     // tile bases; per-warp exclusive offsets (two tiles per word)
@@ -586,21 +613,32 @@ place_kernel(int n, int nb, Geom g, int t0, int tw, const uint32_t* __restrict__
     uint16_t* c16 = reinterpret_cast<uint16_t*>(wc);
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t key_total = info[0];
-    walk_entries<true>(wb, lane, n, e0, e1, k, rects, order, KEYS ? dkeys : nullptr, pk, g, t0, tw,
-                       [&](int t, int j) {
-        const unsigned peers = __match_any_sync(kFull, t >= 0 ? (uint32_t)t : 0xffffffffu);
-        uint32_t c = 0;
-        if (t >= 0) {
-            c = c16[t];
-            const uint32_t pos = s_base[t] + c + __popc(peers & lt);
-            if (pos < key_total) {  // always, unless the counts were inconsistent
-                point_list[pos] = wb.id[j];
-                if (KEYS) keys_out[pos] = ((uint64_t)(uint32_t)(t + t0) << 32) | (uint64_t)wb.dk[j];
+    walk_rows<true>(wb, lane, n, e0, e1, k, rects, order, KEYS ? dkeys : nullptr, pk, g, t0,
+                    [&](bool ok, const RowWork& r) {
+        // rows of the same tile row in one round share tiles: they take
+        // turns in lane order (lane order is depth order); rows of
+        // different tile rows never share a tile
+        const unsigned peers = __match_any_sync(kFull, ok ? (uint32_t)r.y : 0xffffffffu);
+        const int rank = __popc(peers & lt);
+        const int turns = __reduce_max_sync(kFull, ok ? __popc(peers) : 0);
+        const uint32_t id = ok ? wb.id[r.j] : 0u;
+        const uint64_t dk = KEYS && ok ? (uint64_t)wb.dk[r.j] : 0ull;
+        for (int turn = 0; turn < turns; ++turn) {
+            if (ok && rank == turn) {
+                for (int x = r.xs; x < r.xe; ++x) {
+                    const int t = r.row_t0 + x;
+                    if ((unsigned)t >= (unsigned)tw) continue;
+                    const uint32_t c = c16[t];
+                    const uint32_t pos = s_base[t] + c;
+                    if (pos < key_total) {  // always, unless the counts were inconsistent
+                        point_list[pos] = id;
+                        if (KEYS) keys_out[pos] = ((uint64_t)(uint32_t)(t + t0) << 32) | dk;
+                    }
+                    c16[t] = (uint16_t)(c + 1);
+                }
             }
+            __syncwarp();
         }
-        __syncwarp();
-        if (t >= 0 && lane == 31 - __clz(peers)) c16[t] = (uint16_t)(c + __popc(peers));
-        __syncwarp();
     });
 }
 
