@@ -50,11 +50,18 @@ struct Shape {
 };
 
 // Bitmask of the warps of a tile (origin ox, oy) whose pixel block can hold
-// a pixel where this splat reaches alpha >= 1/255: the bounding box of the
-// ellipse sigma <= ln(255 o) (half-widths sqrt(2 L C / det), sqrt(2 L A /
-// det) for the conic [[A,B],[B,C]]), with L enlarged by 1% + 0.01 and the box
-// by 2% + 0.05 px, so FP32 rounding of sigma or alpha can never let a culled
-// pair pass the alpha test: culling removes only pairs every kernel skips.
+// a pixel where this splat reaches alpha >= 1/255, i.e. sigma <= ln(255 o).
+// Two tests, both conservative: the bounding box of that ellipse
+// (half-widths sqrt(2 L C / det), sqrt(2 L A / det) for the conic
+// [[A,B],[B,C]]; box enlarged by 2% + 0.05 px), then the exact minimum of
+// sigma over the warp's block (enlarged by 0.05 px): sigma is a convex
+// quadratic, so when the centre lies outside the block the minimum is on an
+// edge whose side the centre is on, at the clamped stationary point of that
+// edge.  L is enlarged by 1% + 0.01 and the minimum is compared with
+// L + 1e-5 (A X^2 + C Y^2 + 2 |B| X Y) (X, Y the block's extents from the
+// centre), far above the FP32 rounding of either evaluation of sigma, so a
+// culled pair can never pass the alpha test: culling removes only pairs
+// every kernel skips.
 template <class SH>
 __device__ __forceinline__ unsigned warp_cull_mask(float u, float v, float A, float B, float C, float o, int ox,
                                                    int oy) {
@@ -67,14 +74,34 @@ __device__ __forceinline__ unsigned warp_cull_mask(float u, float v, float A, fl
     const float ex = sqrtf(2.0f * L * C / det) * 1.02f + 0.05f;
     const float ey = sqrtf(2.0f * L * A / det) * 1.02f + 0.05f;
     unsigned m = 0u;
-#pragma unroll
+#pragma unroll 1
     for (int w = 0; w < NW; ++w) {
         int x0, y0;
         SH::warp_origin(w, x0, y0);
         x0 += ox;
         y0 += oy;
-        const bool hit = (u + ex >= (float)x0) && (u - ex <= (float)(x0 + SH::BX - 1)) &&
-                         (v + ey >= (float)y0) && (v - ey <= (float)(y0 + SH::BY - 1));
+        bool hit = (u + ex >= (float)x0) && (u - ex <= (float)(x0 + SH::BX - 1)) &&
+                   (v + ey >= (float)y0) && (v - ey <= (float)(y0 + SH::BY - 1));
+        if (hit) {
+            const float dxa = (float)x0 - 0.05f - u, dxb = (float)(x0 + SH::BX - 1) + 0.05f - u;
+            const float dya = (float)y0 - 0.05f - v, dyb = (float)(y0 + SH::BY - 1) + 0.05f - v;
+            if (dxa > 0.0f || dxb < 0.0f || dya > 0.0f || dyb < 0.0f) {  // centre outside the block
+                float smin = 3.0e38f;
+                if (dxa > 0.0f || dxb < 0.0f) {
+                    const float X = dxa > 0.0f ? dxa : dxb;
+                    const float Y = fminf(fmaxf(-B * X / C, dya), dyb);
+                    smin = fminf(smin, 0.5f * (A * X * X + C * Y * Y) + B * X * Y);
+                }
+                if (dya > 0.0f || dyb < 0.0f) {
+                    const float Y = dya > 0.0f ? dya : dyb;
+                    const float X = fminf(fmaxf(-B * Y / A, dxa), dxb);
+                    smin = fminf(smin, 0.5f * (A * X * X + C * Y * Y) + B * X * Y);
+                }
+                const float xm = fmaxf(fabsf(dxa), fabsf(dxb)), ym = fmaxf(fabsf(dya), fabsf(dyb));
+                const float tol = 1e-5f * (A * xm * xm + C * ym * ym + 2.0f * fabsf(B) * xm * ym);
+                hit = smin <= L + tol;
+            }
+        }
         m |= hit ? (1u << w) : 0u;
     }
     return m;
