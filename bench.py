@@ -287,8 +287,8 @@ def run_ours(args):
     units = 9 * p_active
 
     def step_once(on_backward=None):
-        grads.mean.zero_(); grads.scale.zero_(); grads.quat.zero_(); grads.opacity.zero_(); grads.feat.zero_()
-        R.step(sc, target, bg, grads, on_backward=on_backward)
+        # one view per step: the 3D gradients are written, not accumulated
+        R.step(sc, target, bg, grads, on_backward=on_backward, accumulate=False)
 
     for _ in range(args.warmup):
         step_once()

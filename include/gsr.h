@@ -406,6 +406,17 @@ int gsr_backward_project(int32_t n, int32_t sh_degree, const float* mean, const 
                          const gsr_camera* cam, const int32_t* radius, const float* grad2d,
                          float* dmean, float* dscale, float* dquat, float* dopacity,
                          float* dfeat, gsr_stream_t stream);
+/*
+ * The same, but the outputs are written instead of accumulated: every
+ * element of every Gaussian's gradients is stored (zero for Gaussians with
+ * radius 0), so a single-view step needs neither a zero fill nor a read of
+ * the previous values.
+ */
+int gsr_backward_project_store(int32_t n, int32_t sh_degree, const float* mean, const float* scale,
+                               const float* quat, const float* opacity, const float* feat,
+                               const gsr_camera* cam, const int32_t* radius, const float* grad2d,
+                               float* dmean, float* dscale, float* dquat, float* dopacity,
+                               float* dfeat, gsr_stream_t stream);
 
 /*
  * L1 photometric loss of Sec. II-B (difference to the reference image):

@@ -135,6 +135,34 @@ __device__ __forceinline__ void stage_rows_add_out(float* __restrict__ g, int ro
     for (int f = f0 + threadIdx.x; f < total; f += CH) g[f] += s[srow<NF>(f)];
 }
 
+// Writes the staged rows back: g += s (ACC) or g = s.
+template <int NF, int CH, bool VEC, bool ACC>
+__device__ __forceinline__ void stage_rows_out(float* __restrict__ g, int rows, const float* s) {
+    if (ACC) {
+        stage_rows_add_out<NF, CH, VEC>(g, rows, s);
+        return;
+    }
+    const int total = rows * NF;
+    int f0 = 0;
+    if (VEC) {
+        float4* g4 = reinterpret_cast<float4*>(g);
+        const int n4 = total >> 2;
+        for (int t = threadIdx.x; t < n4; t += CH) {
+            const int f = 4 * t;
+            g4[t] = make_float4(s[srow<NF>(f)], s[srow<NF>(f + 1)], s[srow<NF>(f + 2)], s[srow<NF>(f + 3)]);
+        }
+        f0 = n4 << 2;
+    }
+    for (int f = f0 + threadIdx.x; f < total; f += CH) g[f] = s[srow<NF>(f)];
+}
+
+// out += v (ACC) or out = v.
+template <bool ACC>
+__device__ __forceinline__ void put(float& out, float v) {
+    if (ACC) out += v;
+    else out = v;
+}
+
 constexpr int kChunk = 128;  // Gaussians per CTA of the projection kernels
 
 // Forward quantities of one Gaussian, kept for the backward projection.
@@ -271,7 +299,9 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
     rec[2] = make_float4(rgb[2], P.p[2], 0.f, 0.f);
 }
 
-template <int DEG, bool VEC>
+// ACC: gradients are added to the outputs; otherwise every output element of
+// every Gaussian is written (zero for culled Gaussians).
+template <int DEG, bool VEC, bool ACC>
 __global__ void __launch_bounds__(kChunk)
 backproject_kernel(int n, const float* __restrict__ mean, const float* __restrict__ scale,
                    const float* __restrict__ quat, const float* __restrict__ feat, Cam k,
@@ -298,7 +328,9 @@ backproject_kernel(int n, const float* __restrict__ mean, const float* __restric
     // colour: SH basis along the viewing direction, clamp at 0
     if constexpr (DEG < 0) {
         if (valid)
-            for (int ch = 0; ch < 3; ++ch) dfeat[3 * (size_t)i + ch] += gcol[ch];
+            for (int ch = 0; ch < 3; ++ch) put<ACC>(dfeat[3 * (size_t)i + ch], gcol[ch]);
+        else if (!ACC && i < n)
+            for (int ch = 0; ch < 3; ++ch) dfeat[3 * (size_t)i + ch] = 0.f;
     } else {
         stage_rows_in<NF, kChunk, VEC>(feat + (size_t)base * NF, rows, s_f);
         __syncthreads();
@@ -337,15 +369,21 @@ backproject_kernel(int n, const float* __restrict__ mean, const float* __restric
             for (int j = 0; j < NF; ++j) f[j] = 0.f;
         }
         __syncthreads();
-        stage_rows_add_out<NF, kChunk, VEC>(dfeat + (size_t)base * NF, rows, s_f);
+        stage_rows_out<NF, kChunk, VEC, ACC>(dfeat + (size_t)base * NF, rows, s_f);
     }
-    if (!valid) return;
     Proj P;
     const float* m = mean + 3 * (size_t)i;
     const float* s = scale + 3 * (size_t)i;
-    if (!project(k, m, s, quat + 4 * (size_t)i, P)) return;
+    if (!valid || !project(k, m, s, quat + 4 * (size_t)i, P)) {
+        if (!ACC && i < n) {  // the outputs of a culled Gaussian are zero
+            dopacity[i] = 0.f;
+            for (int j = 0; j < 3; ++j) dmean[3 * (size_t)i + j] = dscale[3 * (size_t)i + j] = 0.f;
+            for (int j = 0; j < 4; ++j) dquat[4 * (size_t)i + j] = 0.f;
+        }
+        return;
+    }
     const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, go = gb.y;
-    dopacity[i] += go;
+    put<ACC>(dopacity[i], go);
 
     // conic (A,B,C) = inverse of [[a,b],[b,c]]
     const float a = P.a, b = P.b, c = P.c;
@@ -386,7 +424,7 @@ backproject_kernel(int n, const float* __restrict__ mean, const float* __restric
             acc += dMij * P.R[3 * ii + j];
             dR[3 * ii + j] = dMij * s[j];
         }
-        ds[j] += acc;
+        put<ACC>(ds[j], acc);
     }
     // R(q) with q normalised, then through the normalisation
     const float w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
@@ -397,7 +435,7 @@ backproject_kernel(int n, const float* __restrict__ mean, const float* __restric
     dq[3] = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] + x * dR[6] + y * dR[7]);
     float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
     float* dqo = dquat + 4 * (size_t)i;
-    for (int j = 0; j < 4; ++j) dqo[j] += (dq[j] - P.qn[j] * qd) * P.qinv;
+    for (int j = 0; j < 4; ++j) put<ACC>(dqo[j], (dq[j] - P.qn[j] * qd) * P.qinv);
 
     // T = J W: dL/dJ = dT W^T (only J00, J02, J11, J12 are non-zero)
     float dJ00 = dT[0] * k.R[0] + dT[1] * k.R[1] + dT[2] * k.R[2];
@@ -415,7 +453,7 @@ backproject_kernel(int n, const float* __restrict__ mean, const float* __restric
                 dJ02 * dJ02_dz + dJ12 * dJ12_dz;
     float* dmo = dmean + 3 * (size_t)i;
     for (int j = 0; j < 3; ++j)
-        dmo[j] += dm[j] + k.R[j] * dp0 + k.R[3 + j] * dp1 + k.R[6 + j] * dp2;
+        put<ACC>(dmo[j], dm[j] + k.R[j] * dp0 + k.R[3 + j] * dp1 + k.R[6 + j] * dp2);
 }
 
 bool tiles_ok(int tw, int th) { return pow2_in(tw, 8, 32) && pow2_in(th, 8, 32) && tw * th <= 512; }
@@ -461,12 +499,11 @@ extern "C" int gsr_preprocess(int32_t n, int32_t sh_degree, const float* mean, c
     return check_launch();
 }
 
-extern "C" int gsr_backward_project(int32_t n, int32_t sh_degree, const float* mean, const float* scale,
-                                    const float* quat, const float* opacity, const float* feat,
-                                    const gsr_camera* cam, const int32_t* radius, const float* grad2d,
-                                    float* dmean, float* dscale, float* dquat, float* dopacity,
-                                    float* dfeat, gsr_stream_t stream) {
-    (void)opacity;
+template <bool ACC>
+int backward_project_impl(int32_t n, int32_t sh_degree, const float* mean, const float* scale, const float* quat,
+                          const float* feat, const gsr_camera* cam, const int32_t* radius, const float* grad2d,
+                          float* dmean, float* dscale, float* dquat, float* dopacity, float* dfeat,
+                          gsr_stream_t stream) {
     if (n < 0 || sh_degree < -1 || sh_degree > 3 || !cam) return GSR_EINVAL;
     if (n == 0) return GSR_OK;
     if (!mean || !scale || !quat || !feat || !radius || !grad2d || !dmean || !dscale || !dquat ||
@@ -477,14 +514,14 @@ extern "C" int gsr_backward_project(int32_t n, int32_t sh_degree, const float* m
     const int blocks = (n + 127) / 128;
     cudaStream_t st = (cudaStream_t)stream;
     const bool vec = aligned16(feat) && aligned16(dfeat);
-#define GSR_BP(D)                                                                                            \
-    do {                                                                                                     \
-        if (vec) backproject_kernel<D, true><<<blocks, kChunk, 0, st>>>(n, mean, scale, quat, feat, k, radius,  \
-                                                                     grad2d, dmean, dscale, dquat, dopacity, \
-                                                                     dfeat);                                 \
-        else backproject_kernel<D, false><<<blocks, kChunk, 0, st>>>(n, mean, scale, quat, feat, k, radius,    \
-                                                                  grad2d, dmean, dscale, dquat, dopacity,   \
-                                                                  dfeat);                                   \
+#define GSR_BP(D)                                                                                                  \
+    do {                                                                                                           \
+        if (vec) backproject_kernel<D, true, ACC><<<blocks, kChunk, 0, st>>>(n, mean, scale, quat, feat, k, radius, \
+                                                                           grad2d, dmean, dscale, dquat,            \
+                                                                           dopacity, dfeat);                        \
+        else backproject_kernel<D, false, ACC><<<blocks, kChunk, 0, st>>>(n, mean, scale, quat, feat, k, radius,   \
+                                                                        grad2d, dmean, dscale, dquat, dopacity,    \
+                                                                        dfeat);                                    \
     } while (0)
     switch (sh_degree) {
         case -1: GSR_BP(-1); break;
@@ -495,4 +532,24 @@ extern "C" int gsr_backward_project(int32_t n, int32_t sh_degree, const float* m
     }
 #undef GSR_BP
     return check_launch();
+}
+
+extern "C" int gsr_backward_project(int32_t n, int32_t sh_degree, const float* mean, const float* scale,
+                                    const float* quat, const float* opacity, const float* feat,
+                                    const gsr_camera* cam, const int32_t* radius, const float* grad2d,
+                                    float* dmean, float* dscale, float* dquat, float* dopacity,
+                                    float* dfeat, gsr_stream_t stream) {
+    (void)opacity;
+    return backward_project_impl<true>(n, sh_degree, mean, scale, quat, feat, cam, radius, grad2d, dmean, dscale,
+                                       dquat, dopacity, dfeat, stream);
+}
+
+extern "C" int gsr_backward_project_store(int32_t n, int32_t sh_degree, const float* mean, const float* scale,
+                                          const float* quat, const float* opacity, const float* feat,
+                                          const gsr_camera* cam, const int32_t* radius, const float* grad2d,
+                                          float* dmean, float* dscale, float* dquat, float* dopacity,
+                                          float* dfeat, gsr_stream_t stream) {
+    (void)opacity;
+    return backward_project_impl<false>(n, sh_degree, mean, scale, quat, feat, cam, radius, grad2d, dmean, dscale,
+                                        dquat, dopacity, dfeat, stream);
 }

@@ -101,6 +101,7 @@ def lib():
     L.gsr_backward_stats.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, P, c_int32, P, P]
     L.gsr_backward_project.argtypes = [c_int32, c_int32, P, P, P, P, P, POINTER(Camera), P, P, P, P, P,
                                        P, P, P]
+    L.gsr_backward_project_store.argtypes = L.gsr_backward_project.argtypes
     L.gsr_l1_loss.argtypes = [c_int64, P, P, P, P, P]
     L.gsr_activate.argtypes = [c_int64, P, P, P, P, P]
     L.gsr_activate_backward.argtypes = [c_int64, P, P, P, P, P, P, P]
@@ -118,7 +119,8 @@ def lib():
                  "gsr_forward", "gsr_backward",
                  "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red",
                  "gsr_activate", "gsr_activate_backward", "gsr_scatter_add9", "gsr_entry_offsets_scratch_bytes",
-                 "gsr_entry_offsets", "gsr_backward_deterministic", "gsr_cube_forward", "gsr_cube_backward"):
+                 "gsr_entry_offsets", "gsr_backward_deterministic", "gsr_cube_forward", "gsr_cube_backward",
+                 "gsr_backward_project_store"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -244,9 +246,12 @@ def gsr_backward_stats(width, height, tile_w, tile_h, tile_ranges, point_list, s
 
 
 def gsr_backward_project(n, sh_degree, mean, scale, quat, opacity, feat, cam, radius, grad2d, dmean,
-                         dscale, dquat, dopacity, dfeat, stream=None):
+                         dscale, dquat, dopacity, dfeat, stream=None, accumulate=True):
+    """accumulate=False calls gsr_backward_project_store (outputs written,
+    zero for culled Gaussians)."""
     c = cam if isinstance(cam, Camera) else camera(cam)
-    _check("gsr_backward_project", lib().gsr_backward_project(
+    name = "gsr_backward_project" if accumulate else "gsr_backward_project_store"
+    _check(name, getattr(lib(), name)(
         n, sh_degree, _ptr(mean), _ptr(scale), _ptr(quat), _ptr(opacity), _ptr(feat), ctypes.byref(c),
         _ptr(radius), _ptr(grad2d), _ptr(dmean), _ptr(dscale), _ptr(dquat), _ptr(dopacity), _ptr(dfeat),
         _stream(stream)))

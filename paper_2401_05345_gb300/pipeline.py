@@ -132,10 +132,12 @@ class ViewBuffers:
                                        self.splat2d, self.radius, self.n, self._det_offsets, bg, self.final_T,
                                        self.n_contrib, dL_dimage, self._det_partial, self.grad2d, opts, stream)
 
-    def backward_project(self, sc: SceneTensors, grads: SceneTensors, stream=None):
+    def backward_project(self, sc: SceneTensors, grads: SceneTensors, stream=None, accumulate=True):
+        """3D gradients of this view: added to ``grads``, or (accumulate=False)
+        written over them."""
         gsr.gsr_backward_project(self.n, sc.sh_degree, sc.mean, sc.scale, sc.quat, sc.opacity, sc.feat,
                                  self.c_cam, self.radius, self.grad2d, grads.mean, grads.scale, grads.quat,
-                                 grads.opacity, grads.feat, stream)
+                                 grads.opacity, grads.feat, stream, accumulate)
 
 
 class Renderer:
@@ -152,10 +154,11 @@ class Renderer:
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
 
     def step(self, sc: SceneTensors, target: torch.Tensor, bg, grads: SceneTensors, stream=None,
-             on_backward=None):
-        """Runs the whole path; ``grads`` accumulates the 3D gradients.
-        Returns the device scalar L1 loss.  ``on_backward(begin: bool)`` is
-        called around the backward launch (event recording by benchmarks)."""
+             on_backward=None, accumulate=True):
+        """Runs the whole path; ``grads`` accumulates the 3D gradients (or,
+        with accumulate=False, receives them: no zeroing needed).  Returns the
+        device scalar L1 loss.  ``on_backward(begin: bool)`` is called around
+        the backward launch (event recording by benchmarks)."""
         vb = self.vb
         self.loss.zero_()
         vb.preprocess(sc, zero_grad=True, stream=stream)
@@ -170,5 +173,5 @@ class Renderer:
             vb.backward(bg, self.dimg, self.opts, stream)
         if on_backward:
             on_backward(False)
-        vb.backward_project(sc, grads, stream)
+        vb.backward_project(sc, grads, stream, accumulate)
         return self.loss

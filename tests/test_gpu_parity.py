@@ -286,6 +286,28 @@ def test_backward_project_matches_oracle(dev, orc, name):
     assert np.all(N(dm)[st_["radius"] == 0] == 0)
 
 
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_backward_project_store_overwrites(dev, orc, name):
+    """The store variant writes every output (old contents irrelevant): equal
+    to the accumulating call on zeroed buffers, zero for culled Gaussians."""
+    st_ = oracle_stage(orc, name, (0.3, 0.7, 0.1))
+    scene, cam = st_["scene"], st_["cam"]
+    n = scene.n
+    g12 = np.zeros((n, 12), np.float32)
+    g12[:, :9] = st_["out"]["grad2d"].astype(np.float32)
+    k = scene.feat.reshape(n, -1).shape[1]
+    args = (n, scene.sh_degree, T(scene.mean), T(scene.scale), T(scene.quat), T(scene.opacity),
+            T(scene.feat.reshape(n, -1)), cam, T(st_["radius"]), T(g12))
+    acc = [torch.zeros((n, c), device=dev) for c in (3, 3, 4)] + [torch.zeros(n, device=dev),
+                                                                 torch.zeros((n, k), device=dev)]
+    sto = [torch.full_like(t, 7.25) for t in acc]
+    gsr.gsr_backward_project(*args, *acc)
+    gsr.gsr_backward_project(*args, *sto, accumulate=False)
+    for a, b in zip(acc, sto):
+        np.testing.assert_array_equal(N(a), N(b))
+    assert np.all(N(sto[4])[st_["radius"] == 0] == 0.0)
+
+
 # ----------------------------------------------------------------------------
 # edge cases
 # ----------------------------------------------------------------------------
