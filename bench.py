@@ -287,8 +287,9 @@ def run_ours(args):
     units = 9 * p_active
 
     def step_once(on_backward=None):
-        # one view per step: the 3D gradients are written, not accumulated
-        R.step(sc, target, bg, grads, on_backward=on_backward, accumulate=False)
+        # one view per step: the 3D gradients are written, not accumulated;
+        # binning does not wait for its key count (checked after the steps)
+        R.step(sc, target, bg, grads, on_backward=on_backward, accumulate=False, sync_bin=False)
 
     for _ in range(args.warmup):
         step_once()
@@ -316,6 +317,8 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop() if not args.profile else None
+    if not vb.check_bin():  # the key buffers come from the first (synchronous) pass
+        raise SystemExit("binning capacity changed between steps")
     step_ms = [e0.elapsed_time(e1) for (e0, e1, _, _) in ev]
     bwd_ms = [b0.elapsed_time(b1) for (_, _, b0, b1) in ev]
     tot_ms = sum(step_ms)
@@ -494,6 +497,8 @@ def run_ours(args):
         return ms
     e2e_ms = e2e_run(False)
     e2e_scene_ms = e2e_run(True)
+    if not vb.check_bin():
+        raise SystemExit("binning capacity changed between steps")
     h2d = target_host.numel() * target_host.element_size()
     h2d_scene = h2d + sum(t.numel() * t.element_size() for t in scene_host)
 

@@ -216,8 +216,8 @@ int gsr_bin_scratch_bytes(int32_t n, int32_t width, int32_t height, int32_t tile
  *   0,0 for empty tiles), keys_out [key_capacity] (optional: sorted keys).
  *   n_keys: HOST pointer, receives the key count.
  * Synchronises `stream` once to read the key count.  Returns GSR_ECAPACITY
- * (with *n_keys set, tile_ranges written, nothing else) when the count
- * exceeds key_capacity: the caller grows the buffers and calls again.
+ * (with *n_keys set, every tile range empty, nothing else written) when the
+ * count exceeds key_capacity: the caller grows the buffers and calls again.
  * A tile grid with 65536 or more tiles per side is GSR_EINVAL.
  */
 int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
@@ -225,6 +225,22 @@ int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32
                  void* scratch, size_t scratch_bytes, uint32_t* point_list,
                  uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,
                  gsr_stream_t stream);
+
+/*
+ * gsr_bin_sort without the host synchronisation: everything is queued on
+ * `stream`, and count_dev (DEVICE pointer, 2 x uint32) receives the key count
+ * and a status: 0 ok; 1 more keys than key_capacity (then every tile range
+ * is empty and point_list / keys_out are not written, so later kernels of
+ * the step see empty lists); 2 inconsistent internal counts (not expected).
+ * The caller reads count_dev after the step (e.g. with the loss) and, on
+ * status 1, grows the buffers and redoes the step.  Makes the whole step
+ * capturable in a CUDA graph.  Returns GSR_OK or an argument error.
+ */
+int gsr_bin_sort_async(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                       const float* splat2d, const int32_t* radius, int64_t key_capacity,
+                       void* scratch, size_t scratch_bytes, uint32_t* point_list,
+                       uint32_t* tile_ranges, uint64_t* keys_out, uint32_t* count_dev,
+                       gsr_stream_t stream);
 
 /*
  * The same binning (same outputs, same arguments and errors) computed with

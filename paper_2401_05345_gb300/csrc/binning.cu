@@ -114,10 +114,13 @@ depth_keys_kernel(int n, const float* __restrict__ splat2d, const int* __restric
 // the column totals.  Block: 32 columns x 32 row segments.  When ranges is
 // given, the last block to finish also scans the totals over the columns
 // (tile start offsets), writes the [start, end) ranges (0,0 for empty
-// columns) and the grand total.
+// columns) and the grand total (info[0], and count_out[0] with a status in
+// count_out[1]: 0 ok, 1 more than cap, 2 inconsistent counts; all ranges
+// empty unless 0).
 __global__ void __launch_bounds__(1024)
 colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restrict__ tot,
-               uint32_t* __restrict__ start, uint32_t* __restrict__ ranges, uint32_t* __restrict__ info) {
+               uint32_t* __restrict__ start, uint32_t* __restrict__ ranges, uint32_t* __restrict__ info,
+               uint32_t cap, uint32_t* __restrict__ count_out) {
     __shared__ uint32_t s_seg[32][33];
     __shared__ bool s_last;
     const int cx = threadIdx.x & 31, seg = threadIdx.x >> 5;
@@ -195,7 +198,21 @@ colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restric
         }
         carry += btot;
     }
-    if (threadIdx.x == 0) info[0] = carry;
+    // more keys than the caller's capacity (or inconsistent counts): every
+    // range empty, so nothing downstream reads the lists
+    const uint32_t status = (info[1] || carry != __ldcg(info + 4)) ? 2u : (carry > cap ? 1u : 0u);
+    if (status)
+        for (int c = threadIdx.x; c < cols; c += 1024) {
+            ranges[2 * (size_t)c] = 0u;
+            ranges[2 * (size_t)c + 1] = 0u;
+        }
+    if (threadIdx.x == 0) {
+        info[0] = carry;
+        if (count_out) {
+            count_out[0] = carry;
+            count_out[1] = status;
+        }
+    }
 }
 
 // One scatter pass of the depth sort.  The tile's keys are ranked stably
@@ -559,13 +576,15 @@ chunk_hist_kernel(int n, int nb, Geom g, int t0, int tw, const uint2* __restrict
 // in depth order.
 template <bool KEYS>
 __global__ void __launch_bounds__(kPlaceThreads)
-place_kernel(int n, int nb, Geom g, int t0, int tw, const uint32_t* __restrict__ order,
+place_kernel(int n, int nb, Geom g, int t0, int tw, uint32_t cap, const uint32_t* __restrict__ order,
              const uint32_t* __restrict__ dkeys, const uint2* __restrict__ rects, const uint32_t* __restrict__ apre,
              const uint32_t* __restrict__ boff, const uint32_t* __restrict__ wstart,
              const uint32_t* __restrict__ info, const uint32_t* __restrict__ m, const uint32_t* __restrict__ start,
              uint32_t* __restrict__ point_list, uint64_t* __restrict__ keys_out) {
     extern __shared__ uint32_t sm[];
     __shared__ WarpBatch s_wb[kPlaceWarps];
+    // over capacity or inconsistent counts: nothing is placed (the ranges are empty)
+    if (info[0] > cap || info[1] || info[0] != info[4]) return;
     const int tw2 = (tw + 1) / 2;
     uint32_t* s_base = sm;
     uint32_t* s_cnt = sm + tw;  // [kPlaceWarps][tw2] packed 16-bit counts
@@ -693,8 +712,8 @@ void bin_layout(int n, const Geom& g, long long cap, char* base, BinScratch& s) 
 }
 
 int colscan(int rows, int cols, uint32_t* m, uint32_t* tot, uint32_t* start, uint32_t* ranges, uint32_t* info,
-            cudaStream_t st) {
-    colscan_kernel<<<(cols + 31) / 32, 1024, 0, st>>>(rows, cols, m, tot, start, ranges, info);
+            cudaStream_t st, uint32_t cap = 0xffffffffu, uint32_t* count_out = nullptr) {
+    colscan_kernel<<<(cols + 31) / 32, 1024, 0, st>>>(rows, cols, m, tot, start, ranges, info, cap, count_out);
     return check_launch();
 }
 
@@ -721,13 +740,17 @@ extern "C" int gsr_bin_scratch_bytes(int32_t n, int32_t width, int32_t height, i
     return GSR_OK;
 }
 
-extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
-                            const float* splat2d, const int32_t* radius, int64_t key_capacity,
-                            void* scratch, size_t scratch_bytes, uint32_t* point_list,
-                            uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,
-                            gsr_stream_t stream_) {
+namespace gsr {
+namespace {
+
+// count_dev == nullptr: synchronous (reads the key count, *n_keys);
+// otherwise the count and status go to count_dev and nothing waits.
+int bin_sort_impl(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h, const float* splat2d,
+                  const int32_t* radius, int64_t key_capacity, void* scratch, size_t scratch_bytes,
+                  uint32_t* point_list, uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,
+                  uint32_t* count_dev, gsr_stream_t stream_) {
     Geom g;
-    if (n < 0 || key_capacity < 0 || key_capacity >= 0xffffffffll || !n_keys ||
+    if (n < 0 || key_capacity < 0 || key_capacity >= 0xffffffffll || (!n_keys && !count_dev) ||
         !make_geom(width, height, tile_w, tile_h, g))
         return GSR_EINVAL;
     if (!tile_ranges || !scratch || (n > 0 && (!splat2d || !radius)) || (key_capacity > 0 && !point_list))
@@ -737,11 +760,12 @@ extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t ti
     BinScratch s;
     bin_layout(n, g, key_capacity, (char*)scratch, s);
     if (scratch_bytes < s.total) return GSR_ESCRATCH;
-    *n_keys = 0;
+    if (n_keys) *n_keys = 0;
     int rc;
     cudaError_t e;
     if (n == 0) {
         e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)g.tiles, st);
+        if (e == cudaSuccess && count_dev) e = cudaMemsetAsync(count_dev, 0, 2 * sizeof(uint32_t), st);
         return e == cudaSuccess ? GSR_OK : cuda_fail(e);
     }
     e = cudaMemsetAsync(s.c1, 0, s.zero_bytes, st);
@@ -784,7 +808,21 @@ extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t ti
                                                             s.info, s.m);
         if ((rc = check_launch()) != GSR_OK) return rc;
     }
-    if ((rc = colscan(s.nb, g.tiles, s.m, s.ttot, s.tstart, tile_ranges, s.info, st)) != GSR_OK) return rc;
+    const uint32_t cap = (uint32_t)key_capacity;
+    if ((rc = colscan(s.nb, g.tiles, s.m, s.ttot, s.tstart, tile_ranges, s.info, st, cap, count_dev)) != GSR_OK)
+        return rc;
+    if (count_dev) {  // placement checks the count on the device
+        const size_t psm = place_smem(tw);
+        auto pk = keys_out ? place_kernel<true> : place_kernel<false>;
+        if ((rc = smem_optin((const void*)pk, psm)) != GSR_OK) return rc;
+        for (int t0 = 0; t0 < g.tiles; t0 += tw) {
+            const int wt = g.tiles - t0 < tw ? g.tiles - t0 : tw;
+            pk<<<s.nb, kPlaceThreads, psm, st>>>(n, s.nb, g, t0, wt, cap, order, dkeys, s.rects, s.apre, s.bsum,
+                                                 s.wstart, s.info, s.m, s.tstart, point_list, keys_out);
+            if ((rc = check_launch()) != GSR_OK) return rc;
+        }
+        return GSR_OK;
+    }
     uint32_t info[5] = {0, 0, 0, 0, 0};
     e = cudaMemcpyAsync(info, s.info, sizeof(info), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -803,9 +841,32 @@ extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t ti
     if ((rc = smem_optin((const void*)pk, psm)) != GSR_OK) return rc;
     for (int t0 = 0; t0 < g.tiles; t0 += tw) {
         const int wt = g.tiles - t0 < tw ? g.tiles - t0 : tw;
-        pk<<<s.nb, kPlaceThreads, psm, st>>>(n, s.nb, g, t0, wt, order, dkeys, s.rects, s.apre, s.bsum, s.wstart,
-                                             s.info, s.m, s.tstart, point_list, keys_out);
+        pk<<<s.nb, kPlaceThreads, psm, st>>>(n, s.nb, g, t0, wt, cap, order, dkeys, s.rects, s.apre, s.bsum,
+                                             s.wstart, s.info, s.m, s.tstart, point_list, keys_out);
         if ((rc = check_launch()) != GSR_OK) return rc;
     }
     return GSR_OK;
+}
+
+}  // namespace
+}  // namespace gsr
+
+extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                            const float* splat2d, const int32_t* radius, int64_t key_capacity,
+                            void* scratch, size_t scratch_bytes, uint32_t* point_list,
+                            uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,
+                            gsr_stream_t stream) {
+    if (!n_keys) return GSR_EINVAL;
+    return bin_sort_impl(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity, scratch, scratch_bytes,
+                         point_list, tile_ranges, keys_out, n_keys, nullptr, stream);
+}
+
+extern "C" int gsr_bin_sort_async(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                                  const float* splat2d, const int32_t* radius, int64_t key_capacity,
+                                  void* scratch, size_t scratch_bytes, uint32_t* point_list,
+                                  uint32_t* tile_ranges, uint64_t* keys_out, uint32_t* count_dev,
+                                  gsr_stream_t stream) {
+    if (!count_dev) return GSR_EINVAL;
+    return bin_sort_impl(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity, scratch, scratch_bytes,
+                         point_list, tile_ranges, keys_out, nullptr, count_dev, stream);
 }

@@ -93,6 +93,8 @@ def lib():
                                P, P, P, POINTER(c_int64), P]
     L.gsr_bin_scratch_bytes_library.argtypes = L.gsr_bin_scratch_bytes.argtypes
     L.gsr_bin_sort_library.argtypes = L.gsr_bin_sort.argtypes
+    L.gsr_bin_sort_async.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, c_int64, P, c_size_t,
+                                     P, P, P, P, P]
     L.gsr_bin_sort_static.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, c_int64, P, P, P,
                                       POINTER(c_int64), P]
     L.gsr_forward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P]
@@ -120,7 +122,7 @@ def lib():
                  "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red",
                  "gsr_activate", "gsr_activate_backward", "gsr_scatter_add9", "gsr_entry_offsets_scratch_bytes",
                  "gsr_entry_offsets", "gsr_backward_deterministic", "gsr_cube_forward", "gsr_cube_backward",
-                 "gsr_backward_project_store"):
+                 "gsr_backward_project_store", "gsr_bin_sort_async"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -184,6 +186,16 @@ def gsr_bin_sort(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity
     if st not in (GSR_OK, GSR_ECAPACITY):
         _check(name, st)
     return st, int(nk.value)
+
+
+def gsr_bin_sort_async(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity, scratch, point_list,
+                       tile_ranges, count_dev, keys_out=None, stream=None):
+    """Binning without a host sync; count_dev (int32 [2] on the device)
+    receives (key count, status 0 ok / 1 over capacity / 2 inconsistent)."""
+    _check("gsr_bin_sort_async", lib().gsr_bin_sort_async(
+        n, width, height, tile_w, tile_h, _ptr(splat2d), _ptr(radius), key_capacity, _ptr(scratch),
+        scratch.numel() * scratch.element_size(), _ptr(point_list), _ptr(tile_ranges), _ptr(keys_out),
+        _ptr(count_dev), _stream(stream)))
 
 
 def gsr_bin_sort_static(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity, point_list,

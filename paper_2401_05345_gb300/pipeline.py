@@ -109,6 +109,31 @@ class ViewBuffers:
                 raise RuntimeError("keys_out smaller than the key count %d" % nk)
             self._alloc_keys(int(nk * 1.25) + 1024)
 
+    def bin_async(self, stream=None):
+        """Binning without a host sync into the current buffers; the key count
+        and status land in ``self.bin_count`` (device int32 [2]).  Check them
+        after the step with ``check_bin``."""
+        if self.scratch is None:
+            sb = gsr.gsr_bin_scratch_bytes(self.n, self.W, self.H, self.tw, self.th, self.key_capacity)
+            self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
+        if getattr(self, "bin_count", None) is None:
+            self.bin_count = torch.zeros(2, dtype=torch.int32, device=self.device)
+        gsr.gsr_bin_sort_async(self.n, self.W, self.H, self.tw, self.th, self.splat2d, self.radius,
+                               self.key_capacity, self.scratch, self.point_list, self.tile_ranges, self.bin_count,
+                               None, stream)
+
+    def check_bin(self) -> bool:
+        """After an asynchronous binning (and a sync): True if the lists were
+        complete; otherwise the key buffers are grown for the next attempt."""
+        cnt, status = (int(x) for x in self.bin_count.cpu())
+        self.n_keys = cnt
+        if status == 0:
+            return True
+        if status == 2:
+            raise RuntimeError("inconsistent binning counts")
+        self._alloc_keys(int(cnt * 1.25) + 1024)
+        return False
+
     def forward(self, bg, stream=None):
         gsr.gsr_forward(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
                         bg, self.image, self.final_T, self.n_contrib, stream)
@@ -154,15 +179,21 @@ class Renderer:
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
 
     def step(self, sc: SceneTensors, target: torch.Tensor, bg, grads: SceneTensors, stream=None,
-             on_backward=None, accumulate=True):
+             on_backward=None, accumulate=True, sync_bin=True):
         """Runs the whole path; ``grads`` accumulates the 3D gradients (or,
         with accumulate=False, receives them: no zeroing needed).  Returns the
         device scalar L1 loss.  ``on_backward(begin: bool)`` is called around
-        the backward launch (event recording by benchmarks)."""
+        the backward launch (event recording by benchmarks).  sync_bin=False
+        bins without waiting for the key count: nothing in the step waits on
+        the host, and ``self.vb.check_bin()`` must be called after the step
+        (if it returns False the step has to be redone)."""
         vb = self.vb
         self.loss.zero_()
         vb.preprocess(sc, zero_grad=True, stream=stream)
-        vb.bin(stream)
+        if sync_bin:
+            vb.bin(stream)
+        else:
+            vb.bin_async(stream)
         vb.forward(bg, stream)
         gsr.gsr_l1_loss(vb.image.numel(), vb.image, target, self.dimg, self.loss, stream)
         if on_backward:

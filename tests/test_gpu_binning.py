@@ -151,3 +151,73 @@ def test_repeated_calls_reuse_scratch(dev, orc):
         assert st == gsr.GSR_OK and nk == len(pl_ref)
         np.testing.assert_array_equal(pl.cpu().numpy()[:nk].view(np.uint32), pl_ref)
         np.testing.assert_array_equal(ranges.cpu().numpy().view(np.uint32), ranges_ref)
+
+
+@pytest.mark.parametrize("case", CASES[:6], ids=lambda c: c[0])
+def test_async_binning_matches_sync(dev, case):
+    name, seed, n, W, H, (tw, th), levels, culled, big = case
+    rec, radius = records(seed, n, W, H, levels, culled, big=big)
+    nk, pl, ranges, keys = run_bin(dev, rec, radius, W, H, tw, th)
+    cap = max(nk, 1)
+    sb = gsr.gsr_bin_scratch_bytes(n, W, H, tw, th, cap)
+    scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
+    gx, gy = (W + tw - 1) // tw, (H + th - 1) // th
+    apl = torch.zeros(cap, dtype=torch.int32, device=dev)
+    arg = torch.full((gx * gy, 2), -1, dtype=torch.int32, device=dev)
+    akeys = torch.zeros(cap, dtype=torch.int64, device=dev)
+    cnt = torch.full((2,), -1, dtype=torch.int32, device=dev)
+    gsr.gsr_bin_sort_async(n, W, H, tw, th, torch.from_numpy(rec).to(dev), torch.from_numpy(radius).to(dev), cap,
+                           scratch, apl, arg, cnt, akeys)
+    torch.cuda.synchronize()
+    assert cnt.cpu().tolist() == [nk, 0]
+    np.testing.assert_array_equal(apl.cpu().numpy()[:nk].view(np.uint32), pl)
+    np.testing.assert_array_equal(arg.cpu().numpy().view(np.uint32), ranges)
+    np.testing.assert_array_equal(akeys.cpu().numpy()[:nk].view(np.uint64), keys)
+
+
+def test_async_binning_over_capacity_leaves_empty_lists(dev):
+    W, H = 300, 200
+    rec, radius = records(21, 9000, W, H, 3)
+    nk = run_bin(dev, rec, radius, W, H, 16, 16)[0]
+    cap = nk - 5
+    n = len(radius)
+    sb = gsr.gsr_bin_scratch_bytes(n, W, H, 16, 16, cap)
+    scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
+    pl = torch.full((cap,), -3, dtype=torch.int32, device=dev)
+    ranges = torch.full((19 * 13, 2), 7, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(2, dtype=torch.int32, device=dev)
+    gsr.gsr_bin_sort_async(n, W, H, 16, 16, torch.from_numpy(rec).to(dev), torch.from_numpy(radius).to(dev), cap,
+                           scratch, pl, ranges, cnt)
+    torch.cuda.synchronize()
+    assert cnt.cpu().tolist() == [nk, 1]
+    assert np.all(ranges.cpu().numpy() == 0)
+    assert np.all(pl.cpu().numpy() == -3)
+
+
+def test_renderer_step_with_async_binning(dev):
+    """A whole step with asynchronous binning equals the synchronous one, and
+    an undersized key buffer is reported and grown by check_bin."""
+    from paper_2401_05345_gb300 import pipeline
+    from paper_2401_05345_gb300 import scenes as S
+    scene, cam = S.tiny_workload(4)
+    sc = pipeline.SceneTensors.from_scene(scene, dev)
+    target = torch.from_numpy(S.target_image(4, cam.width, cam.height)).to(dev)
+    out = []
+    for sync in (True, False):
+        R = pipeline.Renderer(scene.n, cam, dev, key_capacity=64)
+        grads = sc.zeros_like_params()
+        if not sync:
+            R.step(sc, target, (0.1, 0.2, 0.3), grads, sync_bin=False)
+            torch.cuda.synchronize()
+            assert not R.vb.check_bin()      # 64 keys are too few: reported, buffers grown
+            grads = sc.zeros_like_params()
+            R.step(sc, target, (0.1, 0.2, 0.3), grads, sync_bin=False)
+            torch.cuda.synchronize()
+            assert R.vb.check_bin()
+        else:
+            R.step(sc, target, (0.1, 0.2, 0.3), grads)
+        torch.cuda.synchronize()
+        out.append((R.vb.image.cpu().numpy(), [t.cpu().numpy() for t in grads.tensors()]))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    for a, b in zip(out[0][1], out[1][1]):  # float atomics: only the summation order differs
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max() + 1e-7
