@@ -43,7 +43,7 @@ __device__ __forceinline__ void tile_rect(float u, float v, int r, int gx, int g
 // alpha = min(0.99, o G).  Returns false when the splat is skipped
 // (sigma < 0 or alpha < 1/255).
 struct SplatEval {
-    float dx, dy, sigma, G, alpha;
+    float dx, dy, dxx, dyy, dxy, sigma, G, alpha;
     bool capped;
 };
 
@@ -51,8 +51,11 @@ __device__ __forceinline__ bool eval_splat(float u, float v, float A, float B, f
                                            float px, float py, SplatEval& e) {
     e.dx = __fsub_rn(u, px);
     e.dy = __fsub_rn(v, py);
-    float q = __fmaf_rn(C, __fmul_rn(e.dy, e.dy), __fmul_rn(A, __fmul_rn(e.dx, e.dx)));
-    e.sigma = __fmaf_rn(0.5f, q, __fmul_rn(B, __fmul_rn(e.dx, e.dy)));
+    e.dxx = __fmul_rn(e.dx, e.dx);
+    e.dyy = __fmul_rn(e.dy, e.dy);
+    e.dxy = __fmul_rn(e.dx, e.dy);
+    float q = __fmaf_rn(C, e.dyy, __fmul_rn(A, e.dxx));
+    e.sigma = __fmaf_rn(0.5f, q, __fmul_rn(B, e.dxy));
     if (e.sigma < 0.0f) return false;
     e.G = __expf(-e.sigma);
     float oG = __fmul_rn(o, e.G);

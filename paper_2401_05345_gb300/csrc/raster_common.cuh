@@ -61,7 +61,9 @@ struct Shape {
 // L + 1e-5 (A X^2 + C Y^2 + 2 |B| X Y) (X, Y the block's extents from the
 // centre), far above the FP32 rounding of either evaluation of sigma, so a
 // culled pair can never pass the alpha test: culling removes only pairs
-// every kernel skips.
+// every kernel skips.  The reciprocals and square roots are the hardware
+// approximations (a few ulp): far inside those margins, and an inexact
+// stationary point moves sigma only at second order.
 template <class SH>
 __device__ __forceinline__ unsigned warp_cull_mask(float u, float v, float A, float B, float C, float o, int ox,
                                                    int oy) {
@@ -71,8 +73,11 @@ __device__ __forceinline__ unsigned warp_cull_mask(float u, float v, float A, fl
     const float det = A * C - B * B;
     if (!(det > 0.0f) || !(A > 0.0f) || !(C > 0.0f)) return ALL;
     const float L = __logf(o * 255.0f) * 1.01f + 0.01f;
-    const float ex = sqrtf(2.0f * L * C / det) * 1.02f + 0.05f;
-    const float ey = sqrtf(2.0f * L * A / det) * 1.02f + 0.05f;
+    const float iA = __fdividef(1.0f, A), iC = __fdividef(1.0f, C);
+    const float t = __fdividef(2.0f * L, det);  // > 0
+    const float tx = t * C, ty = t * A;
+    const float ex = tx * rsqrtf(tx) * 1.02f + 0.05f;
+    const float ey = ty * rsqrtf(ty) * 1.02f + 0.05f;
     unsigned m = 0u;
 #pragma unroll 1
     for (int w = 0; w < NW; ++w) {
@@ -89,12 +94,12 @@ __device__ __forceinline__ unsigned warp_cull_mask(float u, float v, float A, fl
                 float smin = 3.0e38f;
                 if (dxa > 0.0f || dxb < 0.0f) {
                     const float X = dxa > 0.0f ? dxa : dxb;
-                    const float Y = fminf(fmaxf(-B * X / C, dya), dyb);
+                    const float Y = fminf(fmaxf(-B * X * iC, dya), dyb);
                     smin = fminf(smin, 0.5f * (A * X * X + C * Y * Y) + B * X * Y);
                 }
                 if (dya > 0.0f || dyb < 0.0f) {
                     const float Y = dya > 0.0f ? dya : dyb;
-                    const float X = fminf(fmaxf(-B * Y / A, dxa), dxb);
+                    const float X = fminf(fmaxf(-B * Y * iA, dxa), dxb);
                     smin = fminf(smin, 0.5f * (A * X * X + C * Y * Y) + B * X * Y);
                 }
                 const float xm = fmaxf(fabsf(dxa), fabsf(dxb)), ym = fmaxf(fabsf(dya), fabsf(dyb));
@@ -301,28 +306,36 @@ struct BwdSmem {
     int maxlast;
 };
 
-// Gradients of one active (pixel, splat) pair, walking back to front: T
-// holds T_{j+1} on entry and T_j on exit; S accumulates
-// sum_{k>j} (c_k . g) alpha_k T_k + T_final (bg . g).
+// Gradients of one active (pixel, splat) pair, walking back to front, added
+// to v[0..9): T holds T_{j+1} on entry and T_j on exit; S accumulates
+// sum_{k>j} (c_k . g) alpha_k T_k + T_final (bg . g).  With
+// dL/dalpha = T_j (c_j . g) - S / (1 - alpha_j):  dL/dc = alpha T_j g,
+// dL/do = G dL/dalpha, dL/dsigma = -o G dL/dalpha (both 0 where alpha is
+// capped), and through sigma = (A dx^2 + C dy^2)/2 + B dx dy:
+// dL/d(u, v) = (A dx + B dy, B dx + C dy) dL/dsigma,
+// dL/d(A, B, C) = (dx^2/2, dx dy, dy^2/2) dL/dsigma.  Every output is one
+// fused multiply-add into its running sum.
 __device__ __forceinline__ void pair_grads(const SplatEval& e, float4 a, float4 b, float cb, float g0, float g1,
                                            float g2, float& T, float& S, float* v) {
     const float inv = __frcp_rn(1.0f - e.alpha);
     const float Tj = T * inv;
-    const float cg = b.z * g0 + b.w * g1 + cb * g2;
-    const float dal = Tj * cg - S * inv;
+    const float cg = fmaf(b.z, g0, fmaf(b.w, g1, cb * g2));
+    const float dal = fmaf(Tj, cg, -S * inv);
     const float w = e.alpha * Tj;
     S = fmaf(cg, w, S);
     T = Tj;
-    v[6] = w * g0;
-    v[7] = w * g1;
-    v[8] = w * g2;
-    const float dsig = e.capped ? 0.0f : -b.y * e.G * dal;
-    v[5] = e.capped ? 0.0f : e.G * dal;
-    v[0] = (a.z * e.dx + a.w * e.dy) * dsig;
-    v[1] = (a.w * e.dx + b.x * e.dy) * dsig;
-    v[2] = 0.5f * e.dx * e.dx * dsig;
-    v[3] = e.dx * e.dy * dsig;
-    v[4] = 0.5f * e.dy * e.dy * dsig;
+    v[6] = fmaf(w, g0, v[6]);
+    v[7] = fmaf(w, g1, v[7]);
+    v[8] = fmaf(w, g2, v[8]);
+    const float dop = e.capped ? 0.0f : e.G * dal;
+    v[5] += dop;
+    const float dsig = -b.y * dop;
+    const float hd = 0.5f * dsig;
+    v[0] = fmaf(fmaf(a.z, e.dx, a.w * e.dy), dsig, v[0]);
+    v[1] = fmaf(fmaf(a.w, e.dx, b.x * e.dy), dsig, v[1]);
+    v[2] = fmaf(e.dxx, hd, v[2]);
+    v[3] = fmaf(e.dxy, dsig, v[3]);
+    v[4] = fmaf(e.dyy, hd, v[4]);
 }
 
 // Backward of one tile: the gradient-computation step (Sec. III-A) for the
@@ -434,12 +447,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                 for (int q = 0; q < PPT; ++q) {
                     SplatEval e;
                     const bool act = (pos < last[q]) && eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, fpx[q], fpy[q], e);
-                    if (act) {
-                        float vq[9];
-                        pair_grads(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], vq);
-#pragma unroll
-                        for (int i = 0; i < 9; ++i) v[i] += vq[i];
-                    }
+                    if (act) pair_grads(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
                     any |= act;
                 }
                 float* rec = grad + (size_t)sm.id[k] * GSR_REC;
