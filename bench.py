@@ -295,6 +295,23 @@ def run_ours(args):
         step_once()
     torch.cuda.synchronize()
 
+    # the step as one CUDA graph (pipeline.StepGraph); the backward is timed
+    # by external events recorded inside the graph on every replay.  Without
+    # external events (or with --stream-launches) the steps are launched
+    # kernel by kernel.
+    graph, gev = None, None
+    if not args.stream_launches:
+        try:
+            gev = (torch.cuda.Event(enable_timing=True, external=True),
+                   torch.cuda.Event(enable_timing=True, external=True))
+        except TypeError:
+            gev = None
+    if gev is not None:
+        graph = pipeline.StepGraph(R, sc, target, bg, grads, accumulate=False, backward_events=gev)
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+
     # timed region: K steps, L2 flushed (untimed) before each
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -306,12 +323,19 @@ def run_ours(args):
     if not args.profile:
         clocks.start()
     wall0 = time.perf_counter()
+    graph_bwd_ms = []
     for k in range(args.steps):
         flush()
         e0, e1, b0, b1 = ev[k]
         e0.record(stream)
-        step_once(lambda begin, b0=b0, b1=b1: (b0 if begin else b1).record(stream))
-        e1.record(stream)
+        if graph is not None:
+            graph.replay()
+            e1.record(stream)
+            e1.synchronize()  # the graph's backward events are re-recorded by the next replay
+            graph_bwd_ms.append(gev[0].elapsed_time(gev[1]))
+        else:
+            step_once(lambda begin, b0=b0, b1=b1: (b0 if begin else b1).record(stream))
+            e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if world > 1:
@@ -320,7 +344,7 @@ def run_ours(args):
     if not vb.check_bin():  # the key buffers come from the first (synchronous) pass
         raise SystemExit("binning capacity changed between steps")
     step_ms = [e0.elapsed_time(e1) for (e0, e1, _, _) in ev]
-    bwd_ms = [b0.elapsed_time(b1) for (_, _, b0, b1) in ev]
+    bwd_ms = graph_bwd_ms if graph is not None else [b0.elapsed_time(b1) for (_, _, b0, b1) in ev]
     tot_ms = sum(step_ms)
     if args.profile:
         tiers = []
@@ -481,6 +505,10 @@ def run_ours(args):
     target_host = target.cpu().pin_memory()
     scene_host = [t.detach().cpu().pin_memory() for t in sc.tensors()]
 
+    # the step graph is captured again here: the measurements above may have
+    # regrown the view's buffers
+    e2e_graph = pipeline.StepGraph(R, sc, target, bg, grads, accumulate=False) if graph is not None else None
+
     def e2e_run(with_scene):
         ms = []
         torch.cuda.synchronize()
@@ -490,7 +518,10 @@ def run_ours(args):
                 for d, hsrc in zip(sc.tensors(), scene_host):
                     d.copy_(hsrc, non_blocking=True)
             target.copy_(target_host, non_blocking=True)
-            step_once()
+            if e2e_graph is not None:
+                e2e_graph.replay()
+            else:
+                step_once()
             loss_host.copy_(R.loss, non_blocking=True)
             torch.cuda.current_stream().synchronize()
             ms.append(1e3 * (time.perf_counter() - t0))
@@ -545,7 +576,9 @@ def run_ours(args):
             "data": "synthetic (seeded generator standing in for the paper's captured scenes)",
             "config": {"workload": desc, "parallelism": f"replicas x{world}",
                        "l2": "flushed before every timed step (256 MiB write, outside the step events)",
-                       "backward_opts": best_name, "bg": list(bg)},
+                       "backward_opts": best_name, "bg": list(bg),
+                       "launch": "one CUDA graph per step (pipeline.StepGraph)" if graph is not None
+                                 else "kernel by kernel on one stream"},
             "roofline": {"bound": "alu", "kernel": f"backward_kernel ({best_name})",
                          "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "T fp32-ops/s",
                          "frac": achieved / peak_ops, "traffic": traffic,
@@ -618,6 +651,8 @@ def main():
     ap.add_argument("--cpu-samples", type=int, default=4, help="oracle samples for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu)")
+    ap.add_argument("--stream-launches", action="store_true",
+                    help="launch the steps kernel by kernel instead of replaying one CUDA graph")
     ap.add_argument("--opts", default="hybrid-thr16-lay1-ppt2", help="backward tier of a --profile run")
     ap.add_argument("--profile-tiers", action="store_true",
                     help="--profile: then one backward launch per autotune candidate")

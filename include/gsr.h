@@ -376,8 +376,12 @@ int gsr_entry_offsets(int32_t n, int32_t width, int32_t height, int32_t tile_w, 
  * order and written to the entry's slot of `partial`; a second kernel sums
  * each Gaussian's entries in slot order into grad2d (accumulated).
  *   radius: from gsr_preprocess; entry_offsets: from gsr_entry_offsets (n+1);
- *   partial: device float [entry_offsets[n] * 9] scratch; other arguments as
- *   gsr_backward.  opts: lane_layout, store_T, pixels_per_thread are used
+ *   partial: device float [partial_entries * 9] scratch.  When
+ *   entry_offsets[n] (a device value: the view's entry count) exceeds
+ *   partial_entries, both kernels return without writing anything and
+ *   grad2d keeps its values: size partial by the key capacity of the
+ *   binning, so that a step whose binning fitted always fits.  Other
+ *   arguments as gsr_backward.  opts: lane_layout, store_T, pixels_per_thread are used
  *   (reduce_mode and threshold are ignored: every active warp reduces).  The
  *   bits of the result depend on lane_layout and pixels_per_thread (they fix
  *   the summation order), not on scheduling.
@@ -387,7 +391,8 @@ int gsr_backward_deterministic(int32_t width, int32_t height, int32_t tile_w, in
                                const float* splat2d, const int32_t* radius, int32_t n,
                                const uint32_t* entry_offsets, const float* bg, const float* final_T,
                                const int32_t* n_contrib, const float* dL_dimage, float* partial,
-                               float* grad2d, const gsr_backward_opts* opts, gsr_stream_t stream);
+                               int64_t partial_entries, float* grad2d, const gsr_backward_opts* opts,
+                               gsr_stream_t stream);
 
 /*
  * Traversal statistics of gsr_backward (nothing else is written): walks the

@@ -152,6 +152,7 @@ template <class SH, bool STORE_T>
 __global__ void __launch_bounds__(SH::NT)
 backward_det_kernel(BwdArgs p) {
     __shared__ BwdSmem<SH::B, kModeDet> sm;
+    if (p.entry_off[p.n] > p.partial_cap) return;  // partial too small: nothing is written
     extern __shared__ float s_dyn[];
     DetSmem det;
     det.part = s_dyn;
@@ -162,9 +163,9 @@ backward_det_kernel(BwdArgs p) {
 
 // grad2d[i] += sum of Gaussian i's entry partials, in slot (tile) order.
 __global__ void entries_reduce_kernel(int n, const uint32_t* __restrict__ off, const float* __restrict__ partial,
-                                      float* __restrict__ grad2d) {
+                                      uint32_t cap, float* __restrict__ grad2d) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || off[n] > cap) return;
     const uint32_t e0 = off[i], e1 = off[i + 1];
     if (e0 == e1) return;
     float acc[9];
@@ -336,12 +337,14 @@ extern "C" int gsr_backward_deterministic(int32_t width, int32_t height, int32_t
                                           const float* splat2d, const int32_t* radius, int32_t n,
                                           const uint32_t* entry_offsets, const float* bg, const float* final_T,
                                           const int32_t* n_contrib, const float* dL_dimage, float* partial,
-                                          float* grad2d, const gsr_backward_opts* opts, gsr_stream_t stream_) {
+                                          int64_t partial_entries, float* grad2d, const gsr_backward_opts* opts,
+                                          gsr_stream_t stream_) {
     gsr_backward_opts o = {GSR_REDUCE_WARP, 0, 1, 1, 2, {0, 0, 0}};
     if (opts) o = *opts;
     if (width <= 0 || height <= 0 || n < 0 || !tile_ranges || !splat2d || !bg || !dL_dimage || !grad2d)
         return GSR_EINVAL;
     if (n > 0 && (!radius || !entry_offsets || !partial || !point_list)) return GSR_EINVAL;
+    if (partial_entries < 0) return GSR_EINVAL;
     if (!aligned16(splat2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
     if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
     if ((o.lane_layout != 0 && o.lane_layout != 1) || (o.store_T != 0 && o.store_T != 1)) return GSR_EINVAL;
@@ -361,6 +364,8 @@ extern "C" int gsr_backward_deterministic(int32_t width, int32_t height, int32_t
     a.radius = radius;
     a.entry_off = entry_offsets;
     a.partial = partial;
+    a.n = n;
+    a.partial_cap = partial_entries > 0xffffffffll ? 0xffffffffu : (uint32_t)partial_entries;
     const int tiles = a.g.gx * a.g.gy;
     cudaStream_t s = (cudaStream_t)stream_;
     const bool st = o.store_T != 0;
@@ -370,6 +375,6 @@ extern "C" int gsr_backward_deterministic(int32_t width, int32_t height, int32_t
     else
         rc = o.lane_layout ? launch_det_store<1, 1>(st, tiles, a, s) : launch_det_store<0, 1>(st, tiles, a, s);
     if (rc != GSR_OK) return rc;
-    entries_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, entry_offsets, partial, grad2d);
+    entries_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, entry_offsets, partial, a.partial_cap, grad2d);
     return check_launch();
 }

@@ -212,6 +212,8 @@ struct BwdArgs {
     const int* radius;
     const uint32_t* entry_off;
     float* partial;
+    int n;                // Gaussians (entry_off has n + 1 values)
+    uint32_t partial_cap; // entries partial holds
 };
 
 // Deterministic tier: per-warp partial sums are combined in warp order and

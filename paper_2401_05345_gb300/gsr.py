@@ -111,7 +111,7 @@ def lib():
     L.gsr_entry_offsets_scratch_bytes.argtypes = [c_int32, POINTER(c_size_t)]
     L.gsr_entry_offsets.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, P, c_size_t, P, P]
     L.gsr_backward_deterministic.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, P, c_int32, P,
-                                             POINTER(c_float), P, P, P, P, P, POINTER(BackwardOpts), P]
+                                             POINTER(c_float), P, P, P, P, c_int64, P, POINTER(BackwardOpts), P]
     L.gsr_scatter_add9.argtypes = [c_int64, P, P, P, c_int32, c_int32, c_int32, P]
     L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
     L.gsr_cube_forward.argtypes = [c_int32, c_int32, P, c_int32, P, P, P]
@@ -242,11 +242,12 @@ def gsr_entry_offsets(n, width, height, tile_w, tile_h, splat2d, radius, scratch
 def gsr_backward_deterministic(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, radius, n,
                                entry_offsets, bg, final_T, n_contrib, dL_dimage, partial, grad2d, opts=None,
                                stream=None):
+    """partial: float tensor; its size / 9 is the entry capacity passed on."""
     o = opts if opts is not None else backward_opts("warp", 0, 1, True, 2)
     _check("gsr_backward_deterministic", lib().gsr_backward_deterministic(
         width, height, tile_w, tile_h, _ptr(tile_ranges), _ptr(point_list), _ptr(splat2d), _ptr(radius), n,
-        _ptr(entry_offsets), _f3(bg), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage), _ptr(partial), _ptr(grad2d),
-        ctypes.byref(o), _stream(stream)))
+        _ptr(entry_offsets), _f3(bg), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage), _ptr(partial),
+        partial.numel() // 9, _ptr(grad2d), ctypes.byref(o), _stream(stream)))
 
 
 def gsr_backward_stats(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, n_contrib, hist,

@@ -144,10 +144,13 @@ class ViewBuffers:
 
     def backward_deterministic(self, bg, dL_dimage, opts=None, stream=None):
         """Backward without float atomics (bit-identical run to run); keeps
-        its per-entry partial buffer between calls."""
-        nk = max(self.n_keys, 1)
+        its per-entry partial buffer between calls, sized by the key capacity
+        so that every binning that fits the key buffers fits it too (also
+        when the key count is not known on the host: asynchronous binning,
+        graph replays)."""
+        nk = max(self.n_keys, self.key_capacity, 1)
         if getattr(self, "_det_partial", None) is None or self._det_partial.numel() < 9 * nk:
-            self._det_partial = torch.empty(9 * nk + 1024, dtype=torch.float32, device=self.device)
+            self._det_partial = torch.empty(9 * nk, dtype=torch.float32, device=self.device)
             self._det_offsets = torch.empty(self.n + 1, dtype=torch.int32, device=self.device)
             self._det_scratch = torch.empty(gsr.gsr_entry_offsets_scratch_bytes(self.n), dtype=torch.uint8,
                                             device=self.device)
@@ -206,3 +209,56 @@ class Renderer:
             on_backward(False)
         vb.backward_project(sc, grads, stream, accumulate)
         return self.loss
+
+
+class StepGraph:
+    """One view's training step (``Renderer.step`` with asynchronous binning)
+    captured once in a CUDA graph and replayed.  The step's 17 kernel
+    launches, the loss reset and the gradient zeroing go to the GPU as one
+    graph launch, so no launch gap separates the short binning kernels.
+
+    The graph keeps the device addresses it was captured with: new inputs
+    are copied into the same ``target`` tensor (and scene tensors) before a
+    replay, and ``loss`` / ``grads`` are overwritten by each replay.  The key
+    capacity is fixed at capture: after replays, ``ok()`` (one device read)
+    reports whether the binning fitted; if not, the key buffers have been
+    grown and the step must be captured again.
+
+    ``backward_events``: optional (begin, end) ``torch.cuda.Event``s created
+    with ``enable_timing=True, external=True``; they are recorded around the
+    backward launch inside the graph on every replay."""
+
+    def __init__(self, renderer: "Renderer", sc: SceneTensors, target: torch.Tensor, bg, grads: SceneTensors,
+                 accumulate=False, backward_events=None):
+        self.renderer = renderer
+        dev = renderer.vb.device
+        side = torch.cuda.Stream(device=dev)
+        for attempt in range(2):  # a second pass after check_bin grew the key buffers
+            side.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.stream(side):  # lazy allocations and first launches happen outside the capture
+                renderer.step(sc, target, bg, grads, accumulate=accumulate, sync_bin=False)
+            torch.cuda.current_stream(dev).wait_stream(side)
+            torch.cuda.synchronize(dev)
+            if renderer.vb.check_bin():
+                break
+        else:
+            raise RuntimeError("binning did not fit the grown key buffers")
+        hook = None
+        if backward_events is not None:
+            b0, b1 = backward_events
+            hook = lambda begin: (b0 if begin else b1).record()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            renderer.step(sc, target, bg, grads, on_backward=hook, accumulate=accumulate, sync_bin=False)
+        self.loss = renderer.loss
+
+    def replay(self) -> torch.Tensor:
+        """Runs the captured step on the current stream; returns the device
+        scalar loss (valid once the stream reaches it)."""
+        self.graph.replay()
+        return self.loss
+
+    def ok(self) -> bool:
+        """After replays and a sync: True if every replay's binning fitted the
+        key buffers."""
+        return self.renderer.vb.check_bin()

@@ -430,4 +430,24 @@ def test_deterministic_backward_matches_oracle_and_repeats_bitwise(dev, orc, nam
     check_scaled(f"{name} deterministic", outs[0][:, :9], out["grad2d"], out["gscale"], out["gallow"])
     np.testing.assert_array_equal(outs[0], outs[1])
     np.testing.assert_array_equal(outs[0], outs[2])
+
+
+def test_deterministic_backward_leaves_everything_when_partial_is_too_small(dev, orc):
+    """A partial buffer one entry short of the view's entry count: neither
+    kernel writes (grad2d keeps its values, partial its contents)."""
+    st_ = oracle_stage(orc, "tiny", (0.3, 0.7, 0.1))
+    cam = st_["cam"]
+    f = gpu_forward(dev, st_)
+    n = len(st_["rec"])
+    radius = T(st_["radius"])
+    off = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+    scr = torch.empty(gsr.gsr_entry_offsets_scratch_bytes(n), dtype=torch.uint8, device=dev)
+    gsr.gsr_entry_offsets(n, cam.width, cam.height, 16, 16, f["splat"], radius, scr, off)
+    nk = int(off[n])
+    partial = torch.full((9 * (nk - 1),), 7.0, device=dev)
+    grad = torch.full((n, 12), 3.0, device=dev)
+    gsr.gsr_backward_deterministic(cam.width, cam.height, 16, 16, f["ranges"], f["pl"], f["splat"], radius, n, off,
+                                   st_["bg"], f["final_T"], f["n_contrib"], T(st_["g"]), partial, grad)
+    torch.cuda.synchronize()
+    assert bool((grad == 3.0).all()) and bool((partial == 7.0).all())
     assert not np.isnan(N(partial)[:9 * nk]).any()
