@@ -240,6 +240,53 @@ def traffic_from_profile(kernel_hash, opts_name, n_pairs):
     return float(e["dram_bytes_per_launch"])
 
 
+def ingest_traffic(csv_path):
+    """Writes profiles/backward_traffic.json from the ncu CSV of a
+    ``--profile --profile-tiers`` run captured with
+    ``--metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum -k regex:backward_kernel``:
+    the last launches of the capture are the tier launches, one per autotune
+    candidate in order (the cluster tier's own kernel does not match)."""
+    import csv
+
+    from paper_2401_05345_gb300 import autotune, gsr
+    launches = {}
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(f) if r]
+    hdr = next(i for i, r in enumerate(rows) if r[0] == "ID")
+    cols = rows[hdr]
+    for r in rows[hdr + 1:]:
+        if len(r) != len(cols):
+            continue
+        d = dict(zip(cols, r))
+        if "backward_kernel" not in d["Kernel Name"]:
+            continue
+        v = float(d["Metric Value"].replace(",", ""))
+        unit = d["Metric Unit"].lower()
+        scale = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "ns": 1e-3, "nsecond": 1e-3,
+                 "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}.get(unit, 1.0)
+        launches.setdefault(int(d["ID"]), {})[d["Metric Name"]] = v * scale
+    # the cluster tier's kernel (backward_cluster_kernel) is not in the capture
+    names = [autotune.opts_name(o) for o in autotune.default_candidates() if o.reduce_mode != gsr.REDUCE_CLUSTER]
+    ids = sorted(launches)
+    if len(ids) < len(names):
+        raise SystemExit(f"{len(ids)} backward launches in {csv_path}, {len(names)} tiers expected")
+    kh = kernel_source_hash()
+    out = {"kernel_hash": kh,
+           "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                     "--clock-control none -k regex:backward_kernel (cold L2 per launch) of "
+                     "bench.py --profile --profile-tiers; see profiles/backward_tiers_single_view_500k.md"}
+    for name, i in zip(names, ids[-len(names):]):
+        m = launches[i]
+        rd, wr = m["dram__bytes_read.sum"], m["dram__bytes_write.sum"]
+        out[name] = {"kernel_hash": kh, "dram_bytes_per_launch": rd + wr, "dram_read": rd, "dram_write": wr,
+                     "ncu_us": m["gpu__time_duration.sum"]}
+    path = os.path.join(ROOT, "profiles", "backward_traffic.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(f"wrote {path}: {len(names)} tiers, kernel hash {kh}")
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -359,7 +406,6 @@ def run_ours(args):
             print(json.dumps({"profile_run": True, "ms_per_step": tot_ms / args.steps,
                               "backward_ms": statistics.mean(bwd_ms), "opts": best_name,
                               "kernel_hash": kernel_source_hash(),
-                              "backward_launches_before_tiers": 1 + args.warmup + args.steps,
                               "tier_order": tiers}), flush=True)
         return 0
 
@@ -656,7 +702,11 @@ def main():
     ap.add_argument("--opts", default="hybrid-thr16-lay1-ppt2", help="backward tier of a --profile run")
     ap.add_argument("--profile-tiers", action="store_true",
                     help="--profile: then one backward launch per autotune candidate")
+    ap.add_argument("--ingest-traffic", metavar="CSV",
+                    help="write profiles/backward_traffic.json from the ncu CSV of a --profile-tiers capture")
     args = ap.parse_args()
+    if args.ingest_traffic:
+        return ingest_traffic(args.ingest_traffic)
     if args.warmup < 3 and not args.profile:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -242,11 +242,24 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
     constexpr int NF = 3 * K;
     __shared__ float s_f[DEG < 0 ? 1 : kChunk * (NF + 1)];
     const int base = blockIdx.x * kChunk;
+    const int i = base + threadIdx.x;
+    // this Gaussian's inputs are requested before the feature staging, so
+    // their latency overlaps it
+    float mv[3] = {0.f, 0.f, 0.f}, sv[3] = {0.f, 0.f, 0.f}, qv[4] = {1.f, 0.f, 0.f, 0.f}, op = 0.f;
+    if (i < n) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            mv[j] = mean[3 * (size_t)i + j];
+            sv[j] = scale[3 * (size_t)i + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) qv[j] = quat[4 * (size_t)i + j];
+        op = opacity[i];
+    }
     if constexpr (DEG >= 0) {
         stage_rows_in<NF, kChunk, VEC>(feat + (size_t)base * NF, min(kChunk, n - base), s_f);
         __syncthreads();
     }
-    const int i = base + threadIdx.x;
     if (i >= n) return;
     float4* rec = reinterpret_cast<float4*>(splat2d + (size_t)i * GSR_REC);
     if (gzero) {
@@ -255,7 +268,7 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
     }
     Proj P;
     int r = 0;
-    bool ok = project(k, mean + 3 * (size_t)i, scale + 3 * (size_t)i, quat + 4 * (size_t)i, P);
+    bool ok = project(k, mv, sv, qv, P);
     if (ok) {
         float mid = 0.5f * (P.a + P.c);
         float disc = fmaxf(kLambdaFloor, mid * mid - P.det);
@@ -276,8 +289,7 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
     if constexpr (DEG < 0) {
         for (int ch = 0; ch < 3; ++ch) rgb[ch] = feat[3 * (size_t)i + ch];
     } else {
-        const float* m = mean + 3 * (size_t)i;
-        float dx = m[0] - k.campos[0], dy = m[1] - k.campos[1], dz = m[2] - k.campos[2];
+        float dx = mv[0] - k.campos[0], dy = mv[1] - k.campos[1], dz = mv[2] - k.campos[2];
         float il = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
         float Y[16];
         sh_basis(DEG, dx * il, dy * il, dz * il, Y);
@@ -295,14 +307,16 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
     }
     radius[i] = r;
     rec[0] = make_float4(P.u, P.v, P.c * idet, -P.b * idet);
-    rec[1] = make_float4(P.a * idet, opacity[i], rgb[0], rgb[1]);
+    rec[1] = make_float4(P.a * idet, op, rgb[0], rgb[1]);
     rec[2] = make_float4(rgb[2], P.p[2], 0.f, 0.f);
 }
 
 // ACC: gradients are added to the outputs; otherwise every output element of
 // every Gaussian is written (zero for culled Gaussians).
+// Six CTAs per SM (at most 80 registers): the kernel is bound by memory
+// latency, so resident warps matter more than registers.
 template <int DEG, bool VEC, bool ACC>
-__global__ void __launch_bounds__(kChunk)
+__global__ void __launch_bounds__(kChunk, 6)
 backproject_kernel(int n, const float* __restrict__ mean, const float* __restrict__ scale,
                    const float* __restrict__ quat, const float* __restrict__ feat, Cam k,
                    const int* __restrict__ radius, const float* __restrict__ grad2d,
@@ -317,11 +331,21 @@ backproject_kernel(int n, const float* __restrict__ mean, const float* __restric
     const bool valid = i < n && radius[i] > 0;
     float dm[3] = {0.f, 0.f, 0.f};
     float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, gc = ga;
+    // this Gaussian's inputs are requested before the feature staging, so
+    // their latency overlaps it
+    float mv[3] = {0.f, 0.f, 0.f}, sv[3] = {0.f, 0.f, 0.f}, qv[4] = {1.f, 0.f, 0.f, 0.f};
     if (valid) {
         const float4* g4 = reinterpret_cast<const float4*>(grad2d + (size_t)i * GSR_REC);
         ga = g4[0];
         gb = g4[1];
         gc = g4[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            mv[j] = mean[3 * (size_t)i + j];
+            sv[j] = scale[3 * (size_t)i + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) qv[j] = quat[4 * (size_t)i + j];
     }
     float gcol[3] = {gb.z, gb.w, gc.x};
 
@@ -336,8 +360,7 @@ backproject_kernel(int n, const float* __restrict__ mean, const float* __restric
         __syncthreads();
         float* f = s_f + threadIdx.x * (NF + 1);
         if (valid) {
-            const float* m = mean + 3 * (size_t)i;
-            float dx = m[0] - k.campos[0], dy = m[1] - k.campos[1], dz = m[2] - k.campos[2];
+            float dx = mv[0] - k.campos[0], dy = mv[1] - k.campos[1], dz = mv[2] - k.campos[2];
             float len = sqrtf(dx * dx + dy * dy + dz * dz);
             float il = 1.0f / len;
             float x = dx * il, y = dy * il, z = dz * il;
@@ -372,9 +395,8 @@ backproject_kernel(int n, const float* __restrict__ mean, const float* __restric
         stage_rows_out<NF, kChunk, VEC, ACC>(dfeat + (size_t)base * NF, rows, s_f);
     }
     Proj P;
-    const float* m = mean + 3 * (size_t)i;
-    const float* s = scale + 3 * (size_t)i;
-    if (!valid || !project(k, m, s, quat + 4 * (size_t)i, P)) {
+    const float* s = sv;
+    if (!valid || !project(k, mv, sv, qv, P)) {
         if (!ACC && i < n) {  // the outputs of a culled Gaussian are zero
             dopacity[i] = 0.f;
             for (int j = 0; j < 3; ++j) dmean[3 * (size_t)i + j] = dscale[3 * (size_t)i + j] = 0.f;
