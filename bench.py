@@ -680,9 +680,9 @@ def run_ours(args):
 
 # Kernels of libgsr launched per step: preprocess; binning (depth keys, three
 # column scans and three radix scatter passes, rectangles, slice bounds,
-# block x tile counts, column scan + ranges, placement); forward, L1 loss,
-# backward, backward projection.
-LAUNCHES_PER_STEP = 17
+# block x tile counts, column scan + ranges, placement); tile order; forward,
+# L1 loss, backward, backward projection.
+LAUNCHES_PER_STEP = 18
 
 
 def main():

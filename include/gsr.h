@@ -289,6 +289,23 @@ int gsr_bin_sort_static(int32_t n, int32_t width, int32_t height, int32_t tile_w
                         int64_t* n_keys, gsr_stream_t stream);
 
 /*
+ * Tile order of the blend kernels: a permutation of the tile ids, longest
+ * lists first.  Each tile of a view takes one CTA of the forward and backward
+ * kernels, and a CTA's time follows its list length (0 to several thousand
+ * entries).  Launching the longest first is the longest-processing-time-first
+ * rule of list scheduling; without it the launch ends in a tail of long tiles
+ * that started late.  The paper has no counterpart (it launches one thread
+ * per pixel and does not discuss scheduling).  Lists are bucketed by length
+ * (powers of two, each split in four); tiles of one bucket come in no
+ * particular order.  No result depends on the order except the float
+ * summation order of the atomic backward tiers, which is not fixed anyway.
+ *   tile_ranges: [tiles][2] from binning; order: device uint32 [tiles] (out).
+ *   One CTA; asynchronous on `stream`.
+ */
+int gsr_tile_order(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                   const uint32_t* tile_ranges, uint32_t* order, gsr_stream_t stream);
+
+/*
  * Forward blend: for each pixel, front to back over its tile's list:
  * sigma = A dx^2/2 + B dx dy + C dy^2/2 with (dx,dy) = (u,v) - pixel, skip if
  * sigma < 0; alpha = min(0.99, o exp(-sigma)), skip if alpha < 1/255; stop
@@ -297,12 +314,15 @@ int gsr_bin_sort_static(int32_t n, int32_t width, int32_t height, int32_t tile_w
  * per-pixel lists the gradient step walks).
  *   bg: HOST pointer to 3 floats.  Outputs: image [3,H,W]; final_T [H,W]
  *   and n_contrib [H,W] (1-based list position of the last contributor, 0 if
- *   none), both optional (NULL).
+ *   none), both optional (NULL).  tile_order: NULL (tiles in row-major
+ *   order) or a permutation of the tile ids from gsr_tile_order, the order
+ *   in which CTAs take tiles; ids outside the grid are skipped, and an id
+ *   that appears twice is rendered twice (the same values written again).
  */
 int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                 const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
                 const float* bg, float* image, float* final_T, int32_t* n_contrib,
-                gsr_stream_t stream);
+                const uint32_t* tile_order, gsr_stream_t stream);
 
 /*
  * Backward blend + per-splat gradient accumulation: the gradient computation
@@ -319,13 +339,16 @@ int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
  * tier forms the same sum; only the float summation order differs.
  *   final_T, n_contrib: from gsr_forward (ignored when opts->store_T == 0).
  *   bg: HOST pointer.  opts: HOST pointer (NULL = WARP, threshold 0, 16x2,
- *   store_T 1).
+ *   store_T 1).  tile_order: NULL or a permutation of the tile ids
+ *   (gsr_tile_order), as for gsr_forward; it must not repeat an id (a
+ *   repeated tile would be accumulated twice).  The cluster tier keeps
+ *   row-major order (a cluster is a 2x2 block of neighbouring tiles).
  */
 int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                  const uint32_t* tile_ranges, const uint32_t* point_list,
                  const float* splat2d, const float* bg, const float* final_T,
                  const int32_t* n_contrib, const float* dL_dimage, float* grad2d,
-                 const gsr_backward_opts* opts, gsr_stream_t stream);
+                 const gsr_backward_opts* opts, const uint32_t* tile_order, gsr_stream_t stream);
 
 /*
  * Work order of a batched backward: one item per (view, 16x16 tile), encoded
@@ -381,8 +404,9 @@ int gsr_entry_offsets(int32_t n, int32_t width, int32_t height, int32_t tile_w, 
  *   partial_entries, both kernels return without writing anything and
  *   grad2d keeps its values: size partial by the key capacity of the
  *   binning, so that a step whose binning fitted always fits.  Other
- *   arguments as gsr_backward.  opts: lane_layout, store_T, pixels_per_thread are used
- *   (reduce_mode and threshold are ignored: every active warp reduces).  The
+ *   arguments (tile_order included) as gsr_backward.  opts: lane_layout,
+ *   store_T, pixels_per_thread are used (reduce_mode and threshold are
+ *   ignored: every active warp reduces).  The
  *   bits of the result depend on lane_layout and pixels_per_thread (they fix
  *   the summation order), not on scheduling.
  */
@@ -392,7 +416,7 @@ int gsr_backward_deterministic(int32_t width, int32_t height, int32_t tile_w, in
                                const uint32_t* entry_offsets, const float* bg, const float* final_T,
                                const int32_t* n_contrib, const float* dL_dimage, float* partial,
                                int64_t partial_entries, float* grad2d, const gsr_backward_opts* opts,
-                               gsr_stream_t stream);
+                               const uint32_t* tile_order, gsr_stream_t stream);
 
 /*
  * Traversal statistics of gsr_backward (nothing else is written): walks the

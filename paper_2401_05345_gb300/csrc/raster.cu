@@ -9,17 +9,67 @@
 namespace gsr {
 namespace {
 
+// Bucket of a tile list of `len` entries for gsr_tile_order: floor(log2 len)
+// with the next two bits below the leading one (0 for empty lists).
+__device__ __forceinline__ int order_bucket(uint32_t len) {
+    if (len == 0) return 0;
+    const int l2 = 31 - __clz(len);
+    return l2 < 2 ? 1 + l2 : 4 * l2 + (int)((len >> (l2 - 2)) & 3u);
+}
+
+// One CTA: a counting sort of the tiles by decreasing bucket.
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderBuckets = 128;
+__global__ void __launch_bounds__(kOrderThreads)
+tile_order_kernel(int tiles, const uint2* __restrict__ ranges, uint32_t* __restrict__ order) {
+    __shared__ uint32_t cnt[kOrderBuckets];
+    for (int b = threadIdx.x; b < kOrderBuckets; b += kOrderThreads) cnt[b] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += kOrderThreads) {
+        const uint2 r = ranges[t];
+        atomicAdd(&cnt[kOrderBuckets - 1 - order_bucket(r.y - r.x)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the bucket counts, in place
+        constexpr int PER = kOrderBuckets / 32;
+        uint32_t v[PER], s = 0;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            v[j] = cnt[threadIdx.x * PER + j];
+            s += v[j];
+        }
+        uint32_t incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(kFull, incl, o);
+            if ((int)threadIdx.x >= o) incl += x;
+        }
+        uint32_t run = incl - s;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            cnt[threadIdx.x * PER + j] = run;
+            run += v[j];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += kOrderThreads) {
+        const uint2 r = ranges[t];
+        order[atomicAdd(&cnt[kOrderBuckets - 1 - order_bucket(r.y - r.x)], 1u)] = (uint32_t)t;
+    }
+}
+
 template <class SH>
 __global__ void __launch_bounds__(SH::NT)
 forward_kernel(RasterGeom g, const uint2* __restrict__ ranges, const uint32_t* __restrict__ point_list,
                const float* __restrict__ splat2d, float bg0, float bg1, float bg2, float* __restrict__ image,
-               float* __restrict__ final_T, int* __restrict__ n_contrib) {
+               float* __restrict__ final_T, int* __restrict__ n_contrib, const uint32_t* __restrict__ order) {
     constexpr int PPT = SH::B / SH::NT;
     __shared__ float4 s_a[SH::B];
     __shared__ float4 s_b[SH::B];
     __shared__ float s_c[SH::B];
     __shared__ unsigned s_mask[SH::B];
-    const int tile = blockIdx.x;
+    const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    if ((unsigned)tile >= (unsigned)(g.gx * g.gy)) return;  // not a tile id
     const int ox = (tile % g.gx) * SH::TWd, oy = (tile / g.gx) * SH::THd;
     float px[PPT], py[PPT], T[PPT], C[PPT][3];
     bool inside[PPT];
@@ -51,7 +101,9 @@ template <class SH, int MODE, bool STORE_T>
 __global__ void __launch_bounds__(SH::NT)
 backward_kernel(BwdArgs p) {
     __shared__ BwdSmem<SH::B, MODE> sm;
-    backward_tile<SH, MODE, STORE_T>(p, blockIdx.x, sm);
+    const int tile = p.order ? (int)p.order[blockIdx.x] : (int)blockIdx.x;
+    if ((unsigned)tile >= (unsigned)(p.g.gx * p.g.gy)) return;  // not a tile id
+    backward_tile<SH, MODE, STORE_T>(p, tile, sm);
 }
 
 // Cluster tier: tiles (blockIdx.x, blockIdx.y) in 2 x 2 clusters (the grid is
@@ -153,12 +205,14 @@ __global__ void __launch_bounds__(SH::NT)
 backward_det_kernel(BwdArgs p) {
     __shared__ BwdSmem<SH::B, kModeDet> sm;
     if (p.entry_off[p.n] > p.partial_cap) return;  // partial too small: nothing is written
+    const int tile = p.order ? (int)p.order[blockIdx.x] : (int)blockIdx.x;
+    if ((unsigned)tile >= (unsigned)(p.g.gx * p.g.gy)) return;  // not a tile id
     extern __shared__ float s_dyn[];
     DetSmem det;
     det.part = s_dyn;
     det.wflags = reinterpret_cast<unsigned*>(s_dyn + SH::NW * SH::B * 9);
     det.slot = det.wflags + SH::B;
-    backward_tile<SH, kModeDet, STORE_T>(p, blockIdx.x, sm, det);
+    backward_tile<SH, kModeDet, STORE_T>(p, tile, sm, det);
 }
 
 // grad2d[i] += sum of Gaussian i's entry partials, in slot (tile) order.
@@ -256,10 +310,20 @@ int check_bwd_opts(const gsr_backward_opts& o) {
 
 using namespace gsr;
 
+extern "C" int gsr_tile_order(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                              const uint32_t* tile_ranges, uint32_t* order, gsr_stream_t stream) {
+    if (width <= 0 || height <= 0 || !tile_ranges || !order) return GSR_EINVAL;
+    if (tile_w != 16 || tile_h != 16 || !aligned8(tile_ranges)) return GSR_EINVAL;
+    const int tiles = ((width + 15) / 16) * ((height + 15) / 16);
+    tile_order_kernel<<<1, kOrderThreads, 0, (cudaStream_t)stream>>>(tiles, reinterpret_cast<const uint2*>(tile_ranges),
+                                                                     order);
+    return check_launch();
+}
+
 extern "C" int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                            const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
                            const float* bg, float* image, float* final_T, int32_t* n_contrib,
-                           gsr_stream_t stream) {
+                           const uint32_t* tile_order, gsr_stream_t stream) {
     if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !bg || !image) return GSR_EINVAL;
     if (!aligned16(splat2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
     if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
@@ -267,7 +331,7 @@ extern "C" int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_
     using SH = Shape<16, 16, 1, GSR_FORWARD_PPT>;
     forward_kernel<SH><<<g.gx * g.gy, SH::NT, 0, (cudaStream_t)stream>>>(
         g, reinterpret_cast<const uint2*>(tile_ranges), point_list, splat2d, bg[0], bg[1], bg[2], image, final_T,
-        n_contrib);
+        n_contrib, tile_order);
     return check_launch();
 }
 
@@ -275,7 +339,7 @@ extern "C" int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32
                             const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
                             const float* bg, const float* final_T, const int32_t* n_contrib,
                             const float* dL_dimage, float* grad2d, const gsr_backward_opts* opts,
-                            gsr_stream_t stream_) {
+                            const uint32_t* tile_order, gsr_stream_t stream_) {
     gsr_backward_opts o = {GSR_REDUCE_WARP, 0, 0, 1, 1, {0, 0, 0}};
     if (opts) o = *opts;
     if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !bg || !dL_dimage || !grad2d) return GSR_EINVAL;
@@ -294,6 +358,7 @@ extern "C" int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32
     a.dL_dimage = dL_dimage;
     a.grad2d = grad2d;
     a.threshold = o.threshold;
+    a.order = tile_order;
     const int tiles = a.g.gx * a.g.gy;
     cudaStream_t s = (cudaStream_t)stream_;
     const bool st = o.store_T != 0;
@@ -338,7 +403,7 @@ extern "C" int gsr_backward_deterministic(int32_t width, int32_t height, int32_t
                                           const uint32_t* entry_offsets, const float* bg, const float* final_T,
                                           const int32_t* n_contrib, const float* dL_dimage, float* partial,
                                           int64_t partial_entries, float* grad2d, const gsr_backward_opts* opts,
-                                          gsr_stream_t stream_) {
+                                          const uint32_t* tile_order, gsr_stream_t stream_) {
     gsr_backward_opts o = {GSR_REDUCE_WARP, 0, 1, 1, 2, {0, 0, 0}};
     if (opts) o = *opts;
     if (width <= 0 || height <= 0 || n < 0 || !tile_ranges || !splat2d || !bg || !dL_dimage || !grad2d)
@@ -364,6 +429,7 @@ extern "C" int gsr_backward_deterministic(int32_t width, int32_t height, int32_t
     a.radius = radius;
     a.entry_off = entry_offsets;
     a.partial = partial;
+    a.order = tile_order;
     a.n = n;
     a.partial_cap = partial_entries > 0xffffffffll ? 0xffffffffu : (uint32_t)partial_entries;
     const int tiles = a.g.gx * a.g.gy;

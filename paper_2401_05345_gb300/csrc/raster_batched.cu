@@ -37,6 +37,7 @@ backward_batched_kernel(const gsr_view* __restrict__ views, const uint32_t* __re
         p.dL_dimage = v.dL_dimage;
         p.grad2d = v.grad2d;
         p.threshold = threshold;
+        p.order = nullptr;  // the item list is the order
         backward_tile<SH, MODE, STORE_T>(p, (int)(code & 0xffffffu), sm);
     }
 }

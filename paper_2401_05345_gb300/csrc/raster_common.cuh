@@ -199,6 +199,7 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
 
 struct BwdArgs {
     RasterGeom g;
+    const uint32_t* order;  // tile of CTA b: order[b] (NULL: b)
     const uint2* ranges;
     const uint32_t* point_list;
     const float* splat2d;

@@ -97,9 +97,10 @@ def lib():
                                      P, P, P, P, P]
     L.gsr_bin_sort_static.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, c_int64, P, P, P,
                                       POINTER(c_int64), P]
-    L.gsr_forward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P]
+    L.gsr_tile_order.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P]
+    L.gsr_forward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P, P]
     L.gsr_backward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P,
-                               POINTER(BackwardOpts), P]
+                               POINTER(BackwardOpts), P, P]
     L.gsr_backward_stats.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, P, c_int32, P, P]
     L.gsr_backward_project.argtypes = [c_int32, c_int32, P, P, P, P, P, POINTER(Camera), P, P, P, P, P,
                                        P, P, P]
@@ -111,14 +112,14 @@ def lib():
     L.gsr_entry_offsets_scratch_bytes.argtypes = [c_int32, POINTER(c_size_t)]
     L.gsr_entry_offsets.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, P, c_size_t, P, P]
     L.gsr_backward_deterministic.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, P, c_int32, P,
-                                             POINTER(c_float), P, P, P, P, c_int64, P, POINTER(BackwardOpts), P]
+                                             POINTER(c_float), P, P, P, P, c_int64, P, POINTER(BackwardOpts), P, P]
     L.gsr_scatter_add9.argtypes = [c_int64, P, P, P, c_int32, c_int32, c_int32, P]
     L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
     L.gsr_cube_forward.argtypes = [c_int32, c_int32, P, c_int32, P, P, P]
     L.gsr_cube_backward.argtypes = [c_int32, c_int32, P, P, c_int32, P, c_int32, c_int32, P]
     for name in ("gsr_preprocess", "gsr_bin_scratch_bytes", "gsr_bin_sort", "gsr_bin_sort_static",
                  "gsr_bin_scratch_bytes_library", "gsr_bin_sort_library",
-                 "gsr_forward", "gsr_backward",
+                 "gsr_tile_order", "gsr_forward", "gsr_backward",
                  "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red",
                  "gsr_activate", "gsr_activate_backward", "gsr_scatter_add9", "gsr_entry_offsets_scratch_bytes",
                  "gsr_entry_offsets", "gsr_backward_deterministic", "gsr_cube_forward", "gsr_cube_backward",
@@ -211,20 +212,26 @@ def gsr_bin_sort_static(n, width, height, tile_w, tile_h, splat2d, radius, key_c
     return st, int(nk.value)
 
 
+def gsr_tile_order(width, height, tile_w, tile_h, tile_ranges, order, stream=None):
+    """order: int32 tensor [tiles] (out): tile ids, longest lists first."""
+    _check("gsr_tile_order", lib().gsr_tile_order(width, height, tile_w, tile_h, _ptr(tile_ranges), _ptr(order),
+                                                  _stream(stream)))
+
+
 def gsr_forward(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, bg, image, final_T=None,
-                n_contrib=None, stream=None):
+                n_contrib=None, stream=None, tile_order=None):
     _check("gsr_forward", lib().gsr_forward(width, height, tile_w, tile_h, _ptr(tile_ranges),
                                             _ptr(point_list), _ptr(splat2d), _f3(bg), _ptr(image),
-                                            _ptr(final_T), _ptr(n_contrib), _stream(stream)))
+                                            _ptr(final_T), _ptr(n_contrib), _ptr(tile_order), _stream(stream)))
 
 
 def gsr_backward(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, bg, final_T, n_contrib,
-                 dL_dimage, grad2d, opts=None, stream=None):
+                 dL_dimage, grad2d, opts=None, stream=None, tile_order=None):
     o = opts if opts is not None else backward_opts()
     _check("gsr_backward", lib().gsr_backward(width, height, tile_w, tile_h, _ptr(tile_ranges),
                                               _ptr(point_list), _ptr(splat2d), _f3(bg), _ptr(final_T),
                                               _ptr(n_contrib), _ptr(dL_dimage), _ptr(grad2d),
-                                              ctypes.byref(o), _stream(stream)))
+                                              ctypes.byref(o), _ptr(tile_order), _stream(stream)))
 
 
 def gsr_entry_offsets_scratch_bytes(n) -> int:
@@ -241,13 +248,13 @@ def gsr_entry_offsets(n, width, height, tile_w, tile_h, splat2d, radius, scratch
 
 def gsr_backward_deterministic(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, radius, n,
                                entry_offsets, bg, final_T, n_contrib, dL_dimage, partial, grad2d, opts=None,
-                               stream=None):
+                               stream=None, tile_order=None):
     """partial: float tensor; its size / 9 is the entry capacity passed on."""
     o = opts if opts is not None else backward_opts("warp", 0, 1, True, 2)
     _check("gsr_backward_deterministic", lib().gsr_backward_deterministic(
         width, height, tile_w, tile_h, _ptr(tile_ranges), _ptr(point_list), _ptr(splat2d), _ptr(radius), n,
         _ptr(entry_offsets), _f3(bg), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage), _ptr(partial),
-        partial.numel() // 9, _ptr(grad2d), ctypes.byref(o), _stream(stream)))
+        partial.numel() // 9, _ptr(grad2d), ctypes.byref(o), _ptr(tile_order), _stream(stream)))
 
 
 def gsr_backward_stats(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, n_contrib, hist,

@@ -65,6 +65,9 @@ class ViewBuffers:
         self.radius = torch.zeros(max(self.n, 1), dtype=torch.int32, device=device)
         self.grad2d = torch.zeros((max(self.n, 1), gsr.GSR_REC), **f32)
         self.tile_ranges = torch.zeros((self.gx * self.gy, 2), dtype=torch.int32, device=device)
+        # order in which the blend kernels take tiles (longest lists first);
+        # any permutation is correct, so it starts as the identity
+        self.tile_order = torch.arange(self.gx * self.gy, dtype=torch.int32, device=device)
         self.image = torch.zeros((3, self.H, self.W), **f32)
         self.final_T = torch.zeros((self.H, self.W), **f32) if store_T else None
         self.n_contrib = torch.zeros((self.H, self.W), dtype=torch.int32, device=device) if store_T else None
@@ -104,6 +107,7 @@ class ViewBuffers:
                                       keys_out, stream)
             self.n_keys = nk
             if st == gsr.GSR_OK:
+                self.order_tiles(stream)
                 return nk
             if keys_out is not None:
                 raise RuntimeError("keys_out smaller than the key count %d" % nk)
@@ -121,6 +125,11 @@ class ViewBuffers:
         gsr.gsr_bin_sort_async(self.n, self.W, self.H, self.tw, self.th, self.splat2d, self.radius,
                                self.key_capacity, self.scratch, self.point_list, self.tile_ranges, self.bin_count,
                                None, stream)
+        self.order_tiles(stream)
+
+    def order_tiles(self, stream=None):
+        """Longest-first tile order of the current lists (gsr_tile_order)."""
+        gsr.gsr_tile_order(self.W, self.H, self.tw, self.th, self.tile_ranges, self.tile_order, stream)
 
     def check_bin(self) -> bool:
         """After an asynchronous binning (and a sync): True if the lists were
@@ -136,11 +145,12 @@ class ViewBuffers:
 
     def forward(self, bg, stream=None):
         gsr.gsr_forward(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
-                        bg, self.image, self.final_T, self.n_contrib, stream)
+                        bg, self.image, self.final_T, self.n_contrib, stream, tile_order=self.tile_order)
 
     def backward(self, bg, dL_dimage, opts=None, stream=None):
         gsr.gsr_backward(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
-                         bg, self.final_T, self.n_contrib, dL_dimage, self.grad2d, opts, stream)
+                         bg, self.final_T, self.n_contrib, dL_dimage, self.grad2d, opts, stream,
+                         tile_order=self.tile_order)
 
     def backward_deterministic(self, bg, dL_dimage, opts=None, stream=None):
         """Backward without float atomics (bit-identical run to run); keeps
@@ -158,7 +168,8 @@ class ViewBuffers:
                               self._det_offsets, stream)
         gsr.gsr_backward_deterministic(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list,
                                        self.splat2d, self.radius, self.n, self._det_offsets, bg, self.final_T,
-                                       self.n_contrib, dL_dimage, self._det_partial, self.grad2d, opts, stream)
+                                       self.n_contrib, dL_dimage, self._det_partial, self.grad2d, opts, stream,
+                                       tile_order=self.tile_order)
 
     def backward_project(self, sc: SceneTensors, grads: SceneTensors, stream=None, accumulate=True):
         """3D gradients of this view: added to ``grads``, or (accumulate=False)

@@ -451,3 +451,82 @@ def test_deterministic_backward_leaves_everything_when_partial_is_too_small(dev,
     torch.cuda.synchronize()
     assert bool((grad == 3.0).all()) and bool((partial == 7.0).all())
     assert not np.isnan(N(partial)[:9 * nk]).any()
+
+
+def _order_bucket(lens):
+    """Bucket of gsr_tile_order, written from its definition: floor(log2 len)
+    and the next two bits below the leading one (0 for an empty list)."""
+    out = np.zeros(len(lens), np.int64)
+    for i, n in enumerate(int(x) for x in lens):
+        if n == 0:
+            continue
+        l2 = n.bit_length() - 1
+        out[i] = 1 + l2 if l2 < 2 else 4 * l2 + ((n >> (l2 - 2)) & 3)
+    return out
+
+
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_tile_order_changes_no_result(dev, orc, name):
+    """gsr_tile_order gives a permutation of the tiles with non-increasing
+    list-length buckets; the forward taking tiles in that order writes the
+    same bits, the atomic backward stays within the oracle tolerance and the
+    deterministic backward writes the same bits."""
+    st_ = oracle_stage(orc, name, (0.3, 0.7, 0.1))
+    cam = st_["cam"]
+    W, H = cam.width, cam.height
+    tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    f = gpu_forward(dev, st_)
+    order = torch.full((tiles,), -1, dtype=torch.int32, device=dev)
+    gsr.gsr_tile_order(W, H, 16, 16, f["ranges"], order)
+    o = N(order)
+    assert sorted(o.tolist()) == list(range(tiles))
+    rg = st_["ranges"].astype(np.int64).reshape(-1, 2)
+    b = _order_bucket(rg[o, 1] - rg[o, 0])
+    assert np.all(np.diff(b) <= 0)
+    # forward: bit for bit
+    image = torch.zeros_like(f["image"])
+    fT = torch.zeros_like(f["final_T"])
+    nc = torch.zeros_like(f["n_contrib"])
+    gsr.gsr_forward(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], st_["bg"], image, fT, nc, tile_order=order)
+    for a, c in ((image, f["image"]), (fT, f["final_T"]), (nc, f["n_contrib"])):
+        assert torch.equal(a, c)
+    # atomic backward: oracle tolerance
+    n = len(st_["rec"])
+    out = st_["out"]
+    for opts in (gsr.backward_opts("hybrid", 12, 1, True, 2), gsr.backward_opts("plain", 0, 1, True, 1)):
+        grad = torch.zeros((n, 12), device=dev)
+        gsr.gsr_backward(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], st_["bg"], f["final_T"], f["n_contrib"],
+                         T(st_["g"]), grad, opts, tile_order=order)
+        check_scaled(f"{name} ordered backward", N(grad)[:, :9], out["grad2d"], out["gscale"], out["gallow"])
+    # deterministic backward: the same bits in either order
+    radius = T(st_["radius"])
+    off = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+    scr = torch.empty(gsr.gsr_entry_offsets_scratch_bytes(n), dtype=torch.uint8, device=dev)
+    gsr.gsr_entry_offsets(n, W, H, 16, 16, f["splat"], radius, scr, off)
+    partial = torch.empty(9 * int(off[n]) + 9, device=dev)
+    res = []
+    for tord in (None, order):
+        grad = torch.zeros((n, 12), device=dev)
+        gsr.gsr_backward_deterministic(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], radius, n, off, st_["bg"],
+                                       f["final_T"], f["n_contrib"], T(st_["g"]), partial, grad, tile_order=tord)
+        res.append(N(grad))
+    np.testing.assert_array_equal(res[0], res[1])
+
+
+def test_tile_ids_outside_the_grid_are_skipped(dev, orc):
+    """An order whose entries are all past the last tile renders nothing:
+    the outputs keep their values (no access outside the grid)."""
+    st_ = oracle_stage(orc, "tiny", (0.3, 0.7, 0.1))
+    cam = st_["cam"]
+    W, H = cam.width, cam.height
+    tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    f = gpu_forward(dev, st_)
+    bad = torch.arange(tiles, 2 * tiles, dtype=torch.int32, device=dev)
+    image = torch.full_like(f["image"], 5.0)
+    gsr.gsr_forward(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], st_["bg"], image, None, None, tile_order=bad)
+    n = len(st_["rec"])
+    grad = torch.full((n, 12), 3.0, device=dev)
+    gsr.gsr_backward(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], st_["bg"], f["final_T"], f["n_contrib"],
+                     T(st_["g"]), grad, gsr.backward_opts("hybrid", 12, 1, True, 2), tile_order=bad)
+    torch.cuda.synchronize()
+    assert bool((image == 5.0).all()) and bool((grad == 3.0).all())
