@@ -320,7 +320,13 @@ struct BwdSmem {
 // fused multiply-add into its running sum.
 __device__ __forceinline__ void pair_grads(const SplatEval& e, float4 a, float4 b, float cb, float g0, float g1,
                                            float g2, float& T, float& S, float* v) {
-    const float inv = __frcp_rn(1.0f - e.alpha);
+    // 1 / (1 - alpha), 1 - alpha in [0.01, 1): the hardware reciprocal
+    // estimate refined by one Newton-Raphson step r <- r + r (1 - d r), which
+    // squares the estimate's relative error (a few ulp before the step)
+    const float d = 1.0f - e.alpha;
+    float inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(d));
+    inv = fmaf(inv, fmaf(-d, inv, 1.0f), inv);
     const float Tj = T * inv;
     const float cg = fmaf(b.z, g0, fmaf(b.w, g1, cb * g2));
     const float dal = fmaf(Tj, cg, -S * inv);
