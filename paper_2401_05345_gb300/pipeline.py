@@ -135,6 +135,12 @@ class ViewBuffers:
         """After an asynchronous binning (and a sync): True if the lists were
         complete; otherwise the key buffers are grown for the next attempt."""
         cnt, status = (int(x) for x in self.bin_count.cpu())
+        return self.apply_bin_status(cnt, status)
+
+    def apply_bin_status(self, cnt, status) -> bool:
+        """``check_bin`` on a (key count, status) pair the caller already
+        copied to the host."""
+        cnt, status = int(cnt), int(status)
         self.n_keys = cnt
         if status == 0:
             return True

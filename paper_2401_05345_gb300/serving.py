@@ -246,10 +246,30 @@ def job_footprint(n, sh_degree, width, height, keys_per_gaussian=16):
     return params + act + view + img
 
 
-class GpuExecutor:
-    """Runs job steps on CUDA streams through libgsr."""
+class _Step:
+    """An issued step: phase 1 (render, loss, backward, 3D gradients) then,
+    once its binning is known to have fitted, phase 2 (Adam)."""
 
-    def __init__(self, device, slots, opts, lr=1e-3, bg=(0.0, 0.0, 0.0), deterministic=False):
+    __slots__ = ("phase", "event", "st", "job_id", "step", "stream")
+
+    def __init__(self, st, job_id, step, stream):
+        self.phase, self.event = 1, None
+        self.st, self.job_id, self.step, self.stream = st, job_id, step, stream
+
+
+class GpuExecutor:
+    """Runs job steps on CUDA streams through libgsr.
+
+    The host never waits for the GPU.  A step is issued in two phases on its
+    slot's stream.  Phase 1 bins asynchronously and ends with one copy of the
+    loss and the binning status to pinned host memory.  ``poll`` reads them
+    once phase 1 has finished.  If the lists fitted, phase 2 (the Adam update)
+    is enqueued.  If the key buffers overflowed, phase 1 changed no parameter
+    or moment, so the buffers are grown and phase 1 runs again.
+    key_capacity_per_gaussian sizes each job's key buffers at load."""
+
+    def __init__(self, device, slots, opts, lr=1e-3, bg=(0.0, 0.0, 0.0), deterministic=False,
+                 key_capacity_per_gaussian=16):
         import torch
 
         from . import gsr, pipeline
@@ -260,6 +280,8 @@ class GpuExecutor:
         self.deterministic = deterministic
         self.lr = lr
         self.bg = bg
+        self.key_capacity_per_gaussian = key_capacity_per_gaussian
+        self.rebins = 0  # phase-1 reruns after a key-buffer overflow
         self.t0_event = torch.cuda.Event(enable_timing=True)
         self.t0_event.record()
         self.t0_host = time.perf_counter()
@@ -293,10 +315,12 @@ class GpuExecutor:
                   sh=scene.sh_degree, scale=torch.empty(3 * n, device=self.device),
                   opac=torch.empty(n, device=self.device), dscale=torch.empty(3 * n, device=self.device),
                   dopac=torch.empty(n, device=self.device),
-                  vb=self.pipeline.ViewBuffers(n, cam, self.device, 16 * n),
+                  vb=self.pipeline.ViewBuffers(n, cam, self.device,
+                                               max(1024, int(self.key_capacity_per_gaussian * n))),
                   targets=[torch.from_numpy(t).to(self.device) for t in targets],
                   loss=torch.zeros(1, device=self.device),
-                  loss_host=torch.zeros(1).pin_memory(), adam_step=0)
+                  loss_host=torch.zeros(1).pin_memory(),
+                  bin_host=torch.zeros(2, dtype=torch.int32).pin_memory(), adam_step=0)
         st["dimg"] = torch.empty_like(st["vb"].image)
         torch.cuda.synchronize(self.device)
         self.loaded[job.job_id] = st
@@ -308,19 +332,23 @@ class GpuExecutor:
             self.final_params[job.job_id] = st["P"].detach().cpu().numpy()
 
     def issue(self, slot, job, step):
+        h = _Step(self.loaded[job.job_id], job.job_id, step, self.streams[slot])
+        self._phase1(h)
+        return h
+
+    def _phase1(self, h):
         torch, gsr = self.torch, self.gsr
-        st = self.loaded[job.job_id]
-        s = self.streams[slot]
+        st, s = h.st, h.stream
         n = st["n"]
         pv, gv, vb = st["pv"], st["gv"], st["vb"]
         with torch.cuda.stream(s):
             gsr.gsr_activate(n, pv[1], pv[3], st["scale"], st["opac"], s)
             sc = self.pipeline.SceneTensors(pv[0], st["scale"], pv[2], st["opac"], pv[4], st["sh"])
             vb.preprocess(sc, zero_grad=True, stream=s)
-            vb.bin(s)
+            vb.bin_async(s)
             vb.forward(self.bg, s)
             st["loss"].zero_()
-            tgt = st["targets"][step % len(st["targets"])]
+            tgt = st["targets"][h.step % len(st["targets"])]
             gsr.gsr_l1_loss(vb.image.numel(), vb.image, tgt, st["dimg"], st["loss"], s)
             if self.deterministic:
                 vb.backward_deterministic(self.bg, st["dimg"], self.opts, s)
@@ -332,21 +360,38 @@ class GpuExecutor:
             grads = self.pipeline.SceneTensors(gv[0], st["dscale"], gv[2], st["dopac"], gv[4], st["sh"])
             vb.backward_project(sc, grads, s)
             gsr.gsr_activate_backward(n, st["scale"], st["opac"], st["dscale"], st["dopac"], gv[1], gv[3], s)
+            st["loss_host"].copy_(st["loss"], non_blocking=True)
+            st["bin_host"].copy_(vb.bin_count, non_blocking=True)
+            h.event = torch.cuda.Event(enable_timing=True)
+            h.event.record(s)
+        h.phase = 1
+
+    def _phase2(self, h):
+        torch, gsr = self.torch, self.gsr
+        st, s = h.st, h.stream
+        with torch.cuda.stream(s):
             st["adam_step"] += 1
             gsr.gsr_adam_step(st["P"].numel(), st["P"], st["G"], st["M"], st["V"], self.lr, 0.9, 0.999, 1e-8,
                               st["adam_step"], s)
-            st["loss_host"].copy_(st["loss"], non_blocking=True)
-            ev = torch.cuda.Event(enable_timing=True)
-            ev.record(s)
-        return (ev, st, job.job_id, step)
+            h.event = torch.cuda.Event(enable_timing=True)
+            h.event.record(s)
+        h.phase = 2
 
     def poll(self, h):
-        ev, st, jid, step = h
-        if not ev.query():
+        if not h.event.query():
             return None
-        completed = self.t0_event.elapsed_time(ev) / 1e3
+        st = h.st
+        if h.phase == 1:
+            cnt, status = (int(x) for x in st["bin_host"])
+            if st["vb"].apply_bin_status(cnt, status):
+                self._phase2(h)
+            else:  # key buffers grown: the lists of this step were empty, run it again
+                self.rebins += 1
+                self._phase1(h)
+            return None
+        completed = self.t0_event.elapsed_time(h.event) / 1e3
         loss = float(st["loss_host"][0])
-        self.loss_log.setdefault(jid, []).append(loss)
+        self.loss_log.setdefault(h.job_id, []).append(loss)
         return completed + 0.0, loss
 
 
@@ -364,8 +409,9 @@ def make_jobs(spec, seed=0):
 
 
 def run_serving(spec, slots, budget_bytes, opts, rate_per_job, seed=0, device="cuda", jobs=None,
-                deterministic=False):
-    ex = GpuExecutor(device, slots, opts, deterministic=deterministic)
+                deterministic=False, key_capacity_per_gaussian=16):
+    ex = GpuExecutor(device, slots, opts, deterministic=deterministic,
+                     key_capacity_per_gaussian=key_capacity_per_gaussian)
     jobs = jobs if jobs is not None else make_jobs(spec, seed)
     for j in jobs:
         j.state, j.done_steps, j.busy = "waiting", 0, False

@@ -63,3 +63,24 @@ def test_deterministic_tier_gives_bitwise_equal_jobs_alone_and_in_the_mix(dev):
         _, _, ex1, _ = SV.run_serving(None, 1, j.footprint, opts, 400.0, seed=3, device=dev, jobs=[alone],
                                       deterministic=True)
         np.testing.assert_array_equal(ex1.final_params[j.job_id], ex.final_params[j.job_id])
+
+
+def test_key_buffer_overflow_reruns_the_render_phase(dev):
+    """Jobs loaded with key buffers far too small for their lists: the first
+    step of every job overflows, the executor grows the buffers and runs the
+    render phase again before any Adam update, and every job ends with the
+    same parameters, bit for bit (atomic-free backward), as a run whose
+    buffers were large enough from the start."""
+    spec = [(20000, 3, 0.0, 160, 120), (30000, 3, 0.005, 200, 150)]
+    jobs = SV.make_jobs(spec, seed=5)
+    budget = sum(j.footprint for j in jobs) + 1
+    opts = gsr.backward_opts("warp", 0, 1, True, 2)
+    _, _, ex_small, _ = SV.run_serving(None, 2, budget, opts, 400.0, seed=5, device=dev, jobs=jobs,
+                                       deterministic=True, key_capacity_per_gaussian=0.01)
+    assert ex_small.rebins >= len(jobs)
+    _, _, ex_ok, _ = SV.run_serving(None, 2, budget, opts, 400.0, seed=5, device=dev, jobs=jobs,
+                                    deterministic=True)
+    assert ex_ok.rebins == 0
+    for j in jobs:
+        np.testing.assert_array_equal(ex_small.final_params[j.job_id], ex_ok.final_params[j.job_id])
+        np.testing.assert_allclose(ex_small.loss_log[j.job_id], ex_ok.loss_log[j.job_id], rtol=1e-5)
