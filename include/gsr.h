@@ -396,13 +396,14 @@ int gsr_entry_offsets(int32_t n, int32_t width, int32_t height, int32_t tile_w, 
  * else runs on the GPU (the atomic buffering idea of Sec. VIII, "DAB", done
  * in software).  Inside a tile every warp reduces its lanes (fixed shuffle
  * tree) into its own shared-memory slot; the slots are combined in warp
- * order and written to the entry's slot of `partial`; a second kernel sums
- * each Gaussian's entries in slot order into grad2d (accumulated).
+ * order and written to the entry's slot of `partial` (cleared by the call
+ * first); a last kernel sums each Gaussian's entries in slot order into
+ * grad2d (accumulated).
  *   radius: from gsr_preprocess; entry_offsets: from gsr_entry_offsets (n+1);
  *   partial: device float [partial_entries * 9] scratch.  When
  *   entry_offsets[n] (a device value: the view's entry count) exceeds
- *   partial_entries, both kernels return without writing anything and
- *   grad2d keeps its values: size partial by the key capacity of the
+ *   partial_entries, no kernel of the call writes anything and grad2d
+ *   keeps its values: size partial by the key capacity of the
  *   binning, so that a step whose binning fitted always fits.  Other
  *   arguments (tile_order included) as gsr_backward.  opts: lane_layout,
  *   store_T, pixels_per_thread are used (reduce_mode and threshold are

@@ -211,8 +211,16 @@ backward_det_kernel(BwdArgs p) {
     DetSmem det;
     det.part = s_dyn;
     det.wflags = reinterpret_cast<unsigned*>(s_dyn + SH::NW * SH::B * 9);
-    det.slot = det.wflags + SH::B;
     backward_tile<SH, kModeDet, STORE_T>(p, tile, sm, det);
+}
+
+// Clears the 9 slots of every entry (nothing when the entry count exceeds cap).
+__global__ void zero_partial_kernel(int n, const uint32_t* __restrict__ off, uint32_t cap, float* __restrict__ partial) {
+    const uint32_t cnt = off[n];
+    if (cnt > cap) return;
+    const size_t total = 9 * (size_t)cnt;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+        partial[i] = 0.0f;
 }
 
 // grad2d[i] += sum of Gaussian i's entry partials, in slot (tile) order.
@@ -235,7 +243,7 @@ __global__ void entries_reduce_kernel(int n, const uint32_t* __restrict__ off, c
 
 template <class SH, bool STORE_T>
 int launch_det(int tiles, const BwdArgs& a, cudaStream_t s) {
-    constexpr size_t dyn = sizeof(float) * SH::NW * SH::B * 9 + 2 * sizeof(uint32_t) * SH::B;
+    constexpr size_t dyn = sizeof(float) * SH::NW * SH::B * 9 + sizeof(uint32_t) * SH::B;
     auto k = backward_det_kernel<SH, STORE_T>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -435,6 +443,7 @@ extern "C" int gsr_backward_deterministic(int32_t width, int32_t height, int32_t
     const int tiles = a.g.gx * a.g.gy;
     cudaStream_t s = (cudaStream_t)stream_;
     const bool st = o.store_T != 0;
+    zero_partial_kernel<<<152 * 8, 256, 0, s>>>(n, entry_offsets, a.partial_cap, partial);
     int rc;
     if (o.pixels_per_thread == 2)
         rc = o.lane_layout ? launch_det_store<1, 2>(st, tiles, a, s) : launch_det_store<0, 2>(st, tiles, a, s);

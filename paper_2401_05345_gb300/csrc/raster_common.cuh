@@ -218,14 +218,15 @@ struct BwdArgs {
 };
 
 // Deterministic tier: per-warp partial sums are combined in warp order and
-// written, without atomics, to one 9-float slot per (tile, splat) list entry.
+// written, without atomics, to one 9-float slot per (tile, splat) list entry
+// that some pixel of the tile reaches (the other slots keep the zeros they
+// were cleared to before the launch).
 constexpr int kModeDet = 4;
 
 // Shared arrays of the deterministic tier (dynamic shared memory).
 struct DetSmem {
     float* part;        // [warps][B][9] per-warp partial sums of the batch
     unsigned* wflags;   // [B] warps that wrote a partial for entry k
-    uint32_t* slot;     // [B] entry slot of staged entry k
 };
 
 // Cluster tier: a 2 x 2 cluster of tile CTAs pre-reduces its warps' splat
@@ -352,7 +353,7 @@ __device__ __forceinline__ void pair_grads(const SplatEval& e, float4 a, float4 
 // it; shared storage is reused across calls.
 template <class SH, int MODE, bool STORE_T>
 __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, BwdSmem<SH::B, MODE>& sm,
-                                              DetSmem det = DetSmem{nullptr, nullptr, nullptr},
+                                              DetSmem det = DetSmem{nullptr, nullptr},
                                               const ClusterTab* ct = nullptr) {
     constexpr int B = SH::B, NT = SH::NT;
     constexpr int PPT = B / NT;
@@ -413,16 +414,6 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
     const int maxlast = sm.maxlast;
     const int rparam = reduce9_param(lane);
     float* __restrict__ grad = p.grad2d;
-    if (MODE == kModeDet) {
-        // entries no pixel of the tile reaches still get their (zero) slot
-        for (int q = maxlast + tid; q < nlist; q += NT) {
-            const uint32_t id = p.point_list[rg.x + (uint32_t)q];
-            const float2 uv = *reinterpret_cast<const float2*>(p.splat2d + (size_t)id * GSR_REC);
-            float* dst = p.partial + 9 * (size_t)entry_slot(p, id, uv.x, uv.y, tile);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) dst[i] = 0.0f;
-        }
-    }
 
     for (int top = maxlast; top > 0; top -= B) {
         const int cnt = min(B, top);
@@ -430,10 +421,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
         stage_batch<SH, true, true>(cnt, [&](int e) { return rg.x + (uint32_t)(top - 1 - e); }, p.point_list,
                                     p.splat2d, ox, oy, sm.a, sm.b, sm.c, sm.id, sm.mask);
         if (MODE == kModeDet)
-            for (int e = tid; e < cnt; e += NT) {  // entries this thread staged
-                det.wflags[e] = 0u;
-                det.slot[e] = entry_slot(p, sm.id[e], sm.a[e].x, sm.a[e].y, tile);
-            }
+            for (int e = tid; e < cnt; e += NT) det.wflags[e] = 0u;  // entries this thread staged
         __syncthreads();
         // each warp visits, back to front, only the staged splats whose
         // alpha >= 1/255 region touches its pixel block and that lie before
@@ -504,14 +492,18 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
         if (MODE == kModeDet) {
             // warp partials combined in warp order: a fixed summation order
             __syncthreads();
-            for (int i = tid; i < cnt * 9; i += NT) {
-                const int k = i / 9, q = i - 9 * k;
+            for (int k = tid; k < cnt; k += NT) {
                 const unsigned fl = det.wflags[k];
-                float sum = 0.0f;
+                if (fl == 0u) continue;  // the slot keeps the zeros it was cleared to
+                float* dst = p.partial + 9 * (size_t)entry_slot(p, sm.id[k], sm.a[k].x, sm.a[k].y, tile);
 #pragma unroll
-                for (int w = 0; w < SH::NW; ++w)
-                    if ((fl >> w) & 1u) sum += det.part[(w * B + k) * 9 + q];
-                p.partial[9 * (size_t)det.slot[k] + q] = sum;
+                for (int q = 0; q < 9; ++q) {
+                    float sum = 0.0f;
+#pragma unroll
+                    for (int w = 0; w < SH::NW; ++w)
+                        if ((fl >> w) & 1u) sum += det.part[(w * B + k) * 9 + q];
+                    dst[q] = sum;
+                }
             }
         }
         if (MODE == GSR_REDUCE_BLOCK) {
