@@ -210,7 +210,7 @@ backward_det_kernel(BwdArgs p) {
     extern __shared__ float s_dyn[];
     DetSmem det;
     det.part = s_dyn;
-    det.wflags = reinterpret_cast<unsigned*>(s_dyn + SH::NW * SH::B * 9);
+    det.wflags = reinterpret_cast<unsigned*>(s_dyn + SH::NW * kDetGroup * 9);
     backward_tile<SH, kModeDet, STORE_T>(p, tile, sm, det);
 }
 
@@ -243,7 +243,7 @@ __global__ void entries_reduce_kernel(int n, const uint32_t* __restrict__ off, c
 
 template <class SH, bool STORE_T>
 int launch_det(int tiles, const BwdArgs& a, cudaStream_t s) {
-    constexpr size_t dyn = sizeof(float) * SH::NW * SH::B * 9 + sizeof(uint32_t) * SH::B;
+    constexpr size_t dyn = sizeof(float) * SH::NW * kDetGroup * 9 + sizeof(uint32_t) * SH::B;
     auto k = backward_det_kernel<SH, STORE_T>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return cuda_fail(e);

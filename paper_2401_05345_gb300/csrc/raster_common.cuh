@@ -222,6 +222,10 @@ struct BwdArgs {
 // that some pixel of the tile reaches (the other slots keep the zeros they
 // were cleared to before the launch).
 constexpr int kModeDet = 4;
+// Staged entries whose per-warp sums are combined at a time: the per-warp
+// sums of 64 entries (9 KB for 4 warps) instead of a whole 256-entry batch
+// let more CTAs share an SM.
+constexpr int kDetGroup = 64;
 
 // Shared arrays of the deterministic tier (dynamic shared memory).
 struct DetSmem {
@@ -357,6 +361,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                                               const ClusterTab* ct = nullptr) {
     constexpr int B = SH::B, NT = SH::NT;
     constexpr int PPT = B / NT;
+    constexpr int DG = MODE == kModeDet ? kDetGroup : B;  // entries per combine of the deterministic tier
     static_assert(MODE != GSR_REDUCE_PLAIN || PPT == 1, "the plain tier keeps one pixel per thread");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx = tile % p.g.gx, ty = tile / p.g.gx;
@@ -426,10 +431,12 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
         // each warp visits, back to front, only the staged splats whose
         // alpha >= 1/255 region touches its pixel block and that lie before
         // the warp's last contributor
-        for (int c0 = 0; c0 < cnt; c0 += 32) {
+        for (int grp0 = 0; grp0 < cnt; grp0 += DG) {
+        const int grp1 = min(cnt, grp0 + DG);
+        for (int c0 = grp0; c0 < grp1; c0 += 32) {
             const int kq = c0 + lane;
             unsigned bits =
-                __ballot_sync(kFull, kq < cnt && ((sm.mask[kq] >> warp) & 1u) && (top - 1 - kq < wlast));
+                __ballot_sync(kFull, kq < grp1 && ((sm.mask[kq] >> warp) & 1u) && (top - 1 - kq < wlast));
             while (bits) {
                 const int k = c0 + __ffs(bits) - 1;
                 bits &= bits - 1u;
@@ -451,7 +458,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                 if (MODE == kModeDet) {
                     if (__ballot_sync(kFull, any) == 0u) continue;
                     const float z = reduce9(v, lane);
-                    if (rparam < 9) det.part[(warp * B + k) * 9 + rparam] = z;
+                    if (rparam < 9) det.part[(warp * DG + (k - grp0)) * 9 + rparam] = z;
                     if (lane == 0) atomicOr(&det.wflags[k], 1u << warp);
                 } else if (MODE == GSR_REDUCE_PLAIN) {
                     if (any) {
@@ -492,7 +499,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
         if (MODE == kModeDet) {
             // warp partials combined in warp order: a fixed summation order
             __syncthreads();
-            for (int k = tid; k < cnt; k += NT) {
+            for (int k = grp0 + tid; k < grp1; k += NT) {
                 const unsigned fl = det.wflags[k];
                 if (fl == 0u) continue;  // the slot keeps the zeros it was cleared to
                 float* dst = p.partial + 9 * (size_t)entry_slot(p, sm.id[k], sm.a[k].x, sm.a[k].y, tile);
@@ -501,10 +508,12 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                     float sum = 0.0f;
 #pragma unroll
                     for (int w = 0; w < SH::NW; ++w)
-                        if ((fl >> w) & 1u) sum += det.part[(w * B + k) * 9 + q];
+                        if ((fl >> w) & 1u) sum += det.part[(w * DG + (k - grp0)) * 9 + q];
                     dst[q] = sum;
                 }
             }
+            if (grp1 < cnt) __syncthreads();  // the next group reuses the partial sums' storage
+        }
         }
         if (MODE == GSR_REDUCE_BLOCK) {
             __syncthreads();
