@@ -325,6 +325,24 @@ int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                 const uint32_t* tile_order, gsr_stream_t stream);
 
 /*
+ * Forward blend fused with the L1 loss of Sec. II-B (the "loss" stage of the
+ * training iteration, Fig. 2): the forward of gsr_forward, and from each
+ * composited pixel value `out`, for every channel,
+ *   dL_dimage = sign(out - target) (0 where equal),
+ *   loss_sum[0] += |out - target|,
+ * with the operations of gsr_l1_loss: dL_dimage is bit for bit what
+ * gsr_forward followed by gsr_l1_loss writes; the loss is the same float sum
+ * added in another order.
+ *   target: [3,H,W]; dL_dimage: [3,H,W] (out); loss_sum: device float,
+ *   accumulated, or NULL; image: [3,H,W] or NULL (not written).  Other
+ *   arguments as gsr_forward.
+ */
+int gsr_forward_l1(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                   const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
+                   const float* bg, const float* target, float* image, float* final_T, int32_t* n_contrib,
+                   float* dL_dimage, float* loss_sum, const uint32_t* tile_order, gsr_stream_t stream);
+
+/*
  * Backward blend + per-splat gradient accumulation: the gradient computation
  * step of Sec. III-A.  One thread per pixel walks its tile's list back to
  * front from the pixel's last contributor, recovers T_j = T_{j+1}/(1-alpha_j),

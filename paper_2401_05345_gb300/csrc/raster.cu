@@ -58,11 +58,20 @@ tile_order_kernel(int tiles, const uint2* __restrict__ ranges, uint32_t* __restr
     }
 }
 
-template <class SH>
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// L1: the epilogue also forms the L1 loss of each pixel (target, dL_dimage,
+// loss_sum; image may then be NULL).
+template <class SH, bool L1>
 __global__ void __launch_bounds__(SH::NT)
 forward_kernel(RasterGeom g, const uint2* __restrict__ ranges, const uint32_t* __restrict__ point_list,
                const float* __restrict__ splat2d, float bg0, float bg1, float bg2, float* __restrict__ image,
-               float* __restrict__ final_T, int* __restrict__ n_contrib, const uint32_t* __restrict__ order) {
+               float* __restrict__ final_T, int* __restrict__ n_contrib, const uint32_t* __restrict__ order,
+               const float* __restrict__ target, float* __restrict__ dimg, float* __restrict__ loss_sum) {
     constexpr int PPT = SH::B / SH::NT;
     __shared__ float4 s_a[SH::B];
     __shared__ float4 s_b[SH::B];
@@ -85,15 +94,36 @@ forward_kernel(RasterGeom g, const uint2* __restrict__ ranges, const uint32_t* _
     walk_front<SH, true>(ranges[tile], point_list, splat2d, px, py, inside, ox, oy, s_a, s_b, s_c, s_mask, T, last,
                          C);
     const size_t HW = (size_t)g.W * g.H;
+    float labs = 0.0f;  // L1: sum of |out - target| over this thread's pixels
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         if (!inside[q]) continue;
         const size_t pix = (size_t)py[q] * g.W + (size_t)px[q];
-        image[pix] = __fmaf_rn(T[q], bg0, C[q][0]);
-        image[HW + pix] = __fmaf_rn(T[q], bg1, C[q][1]);
-        image[2 * HW + pix] = __fmaf_rn(T[q], bg2, C[q][2]);
+        const float out[3] = {__fmaf_rn(T[q], bg0, C[q][0]), __fmaf_rn(T[q], bg1, C[q][1]),
+                              __fmaf_rn(T[q], bg2, C[q][2])};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            if (!L1 || image) image[ch * HW + pix] = out[ch];
+            if (L1) {  // the operations of gsr_l1_loss
+                const float d = __fsub_rn(out[ch], target[ch * HW + pix]);
+                dimg[ch * HW + pix] = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
+                labs += fabsf(d);
+            }
+        }
         if (final_T) final_T[pix] = T[q];
         if (n_contrib) n_contrib[pix] = last[q];
+    }
+    if (L1 && loss_sum) {
+        __shared__ float s_l[SH::NW];
+        labs = warp_sum(labs);
+        if ((threadIdx.x & 31) == 0) s_l[threadIdx.x >> 5] = labs;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+#pragma unroll
+            for (int w = 0; w < SH::NW; ++w) t += s_l[w];
+            atomicAdd(loss_sum, t);
+        }
     }
 }
 
@@ -337,9 +367,25 @@ extern "C" int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_
     if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
     RasterGeom g{width, height, (width + 15) / 16, (height + 15) / 16};
     using SH = Shape<16, 16, 1, GSR_FORWARD_PPT>;
-    forward_kernel<SH><<<g.gx * g.gy, SH::NT, 0, (cudaStream_t)stream>>>(
+    forward_kernel<SH, false><<<g.gx * g.gy, SH::NT, 0, (cudaStream_t)stream>>>(
         g, reinterpret_cast<const uint2*>(tile_ranges), point_list, splat2d, bg[0], bg[1], bg[2], image, final_T,
-        n_contrib, tile_order);
+        n_contrib, tile_order, nullptr, nullptr, nullptr);
+    return check_launch();
+}
+
+extern "C" int gsr_forward_l1(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                              const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
+                              const float* bg, const float* target, float* image, float* final_T,
+                              int32_t* n_contrib, float* dL_dimage, float* loss_sum, const uint32_t* tile_order,
+                              gsr_stream_t stream) {
+    if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !bg || !target || !dL_dimage) return GSR_EINVAL;
+    if (!aligned16(splat2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
+    if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
+    RasterGeom g{width, height, (width + 15) / 16, (height + 15) / 16};
+    using SH = Shape<16, 16, 1, GSR_FORWARD_PPT>;
+    forward_kernel<SH, true><<<g.gx * g.gy, SH::NT, 0, (cudaStream_t)stream>>>(
+        g, reinterpret_cast<const uint2*>(tile_ranges), point_list, splat2d, bg[0], bg[1], bg[2], image, final_T,
+        n_contrib, tile_order, target, dL_dimage, loss_sum);
     return check_launch();
 }
 

@@ -98,6 +98,8 @@ def lib():
     L.gsr_bin_sort_static.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, c_int64, P, P, P,
                                       POINTER(c_int64), P]
     L.gsr_tile_order.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P]
+    L.gsr_forward_l1.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P, P, P,
+                                 P, P]
     L.gsr_forward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P, P]
     L.gsr_backward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P,
                                POINTER(BackwardOpts), P, P]
@@ -119,7 +121,7 @@ def lib():
     L.gsr_cube_backward.argtypes = [c_int32, c_int32, P, P, c_int32, P, c_int32, c_int32, P]
     for name in ("gsr_preprocess", "gsr_bin_scratch_bytes", "gsr_bin_sort", "gsr_bin_sort_static",
                  "gsr_bin_scratch_bytes_library", "gsr_bin_sort_library",
-                 "gsr_tile_order", "gsr_forward", "gsr_backward",
+                 "gsr_tile_order", "gsr_forward", "gsr_forward_l1", "gsr_backward",
                  "gsr_backward_stats", "gsr_backward_project", "gsr_l1_loss", "gsr_adam_step", "gsr_bench_red",
                  "gsr_activate", "gsr_activate_backward", "gsr_scatter_add9", "gsr_entry_offsets_scratch_bytes",
                  "gsr_entry_offsets", "gsr_backward_deterministic", "gsr_cube_forward", "gsr_cube_backward",
@@ -223,6 +225,14 @@ def gsr_forward(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d,
     _check("gsr_forward", lib().gsr_forward(width, height, tile_w, tile_h, _ptr(tile_ranges),
                                             _ptr(point_list), _ptr(splat2d), _f3(bg), _ptr(image),
                                             _ptr(final_T), _ptr(n_contrib), _ptr(tile_order), _stream(stream)))
+
+
+def gsr_forward_l1(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, bg, target, image, final_T,
+                   n_contrib, dL_dimage, loss_sum=None, stream=None, tile_order=None):
+    _check("gsr_forward_l1", lib().gsr_forward_l1(width, height, tile_w, tile_h, _ptr(tile_ranges),
+                                                  _ptr(point_list), _ptr(splat2d), _f3(bg), _ptr(target),
+                                                  _ptr(image), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage),
+                                                  _ptr(loss_sum), _ptr(tile_order), _stream(stream)))
 
 
 def gsr_backward(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, bg, final_T, n_contrib,

@@ -153,6 +153,12 @@ class ViewBuffers:
         gsr.gsr_forward(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
                         bg, self.image, self.final_T, self.n_contrib, stream, tile_order=self.tile_order)
 
+    def forward_l1(self, bg, target, dL_dimage, loss_sum=None, stream=None):
+        """Forward with the L1 loss formed in its epilogue (gsr_forward_l1)."""
+        gsr.gsr_forward_l1(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
+                           bg, target, self.image, self.final_T, self.n_contrib, dL_dimage, loss_sum, stream,
+                           tile_order=self.tile_order)
+
     def backward(self, bg, dL_dimage, opts=None, stream=None):
         gsr.gsr_backward(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
                          bg, self.final_T, self.n_contrib, dL_dimage, self.grad2d, opts, stream,
@@ -187,8 +193,9 @@ class ViewBuffers:
 
 class Renderer:
     """One view's render + backward through libgsr: the unit of work of the
-    training iteration (Sec. II-B, Fig. 2): projection, binning, forward blend,
-    L1 loss gradient, backward blend with gradient accumulation, backward
+    training iteration (Sec. II-B, Fig. 2): projection, binning, forward blend
+    with the L1 loss gradient formed in its epilogue, backward blend with
+    gradient accumulation, backward
     projection."""
 
     def __init__(self, n, cam, device="cuda", opts=None, store_T=True, key_capacity=None, deterministic=False):
@@ -214,8 +221,7 @@ class Renderer:
             vb.bin(stream)
         else:
             vb.bin_async(stream)
-        vb.forward(bg, stream)
-        gsr.gsr_l1_loss(vb.image.numel(), vb.image, target, self.dimg, self.loss, stream)
+        vb.forward_l1(bg, target, self.dimg, self.loss, stream)
         if on_backward:
             on_backward(True)
         if self.deterministic:

@@ -75,6 +75,9 @@ def test_argument_errors_are_reported_before_any_launch(lib):
     assert lib.gsr_tile_order(0, 16, 16, 16, p, p, None) == gsr.GSR_EINVAL
     assert lib.gsr_tile_order(32, 32, 8, 16, p, p, None) == gsr.GSR_EINVAL
     assert lib.gsr_tile_order(32, 32, 16, 16, p, None, None) == gsr.GSR_EINVAL
+    # forward + L1: the target and the loss gradient are required
+    assert lib.gsr_forward_l1(32, 32, 16, 16, p, p, p, bg, None, p, None, None, p, None, None, None) == gsr.GSR_EINVAL
+    assert lib.gsr_forward_l1(32, 32, 16, 16, p, p, p, bg, p, p, None, None, None, None, None, None) == gsr.GSR_EINVAL
     cam = gsr.Camera()
     assert lib.gsr_preprocess(10, 4, p, p, p, p, p, ctypes.byref(cam), 16, 16, p, p, None, None) == gsr.GSR_EINVAL
     out = ctypes.c_size_t(0)

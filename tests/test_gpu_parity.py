@@ -530,3 +530,35 @@ def test_tile_ids_outside_the_grid_are_skipped(dev, orc):
                      T(st_["g"]), grad, gsr.backward_opts("hybrid", 12, 1, True, 2), tile_order=bad)
     torch.cuda.synchronize()
     assert bool((image == 5.0).all()) and bool((grad == 3.0).all())
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged_sh3", "dense_sh1"])
+def test_forward_with_l1_equals_forward_then_l1(dev, orc, name):
+    """gsr_forward_l1 writes the image, transmittance, contributor counts
+    and loss gradient of gsr_forward followed by gsr_l1_loss bit for bit,
+    and the same loss within the 1e-5 relative tolerance of float sums in
+    another order; without an image buffer it writes the same gradient."""
+    st_ = oracle_stage(orc, name, (0.3, 0.7, 0.1))
+    cam = st_["cam"]
+    W, H = cam.width, cam.height
+    f = gpu_forward(dev, st_)
+    tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    order = torch.empty(tiles, dtype=torch.int32, device=dev)
+    gsr.gsr_tile_order(W, H, 16, 16, f["ranges"], order)
+    target = T(S.target_image(3, W, H))
+    dref = torch.empty_like(f["image"])
+    lref = torch.zeros(1, device=dev)
+    gsr.gsr_l1_loss(dref.numel(), f["image"], target, dref, lref)
+    image = torch.zeros_like(f["image"])
+    fT = torch.zeros_like(f["final_T"])
+    nc = torch.zeros_like(f["n_contrib"])
+    dimg = torch.full_like(f["image"], 7.0)
+    loss = torch.zeros(1, device=dev)
+    gsr.gsr_forward_l1(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], st_["bg"], target, image, fT, nc, dimg, loss,
+                       tile_order=order)
+    for a, b in ((image, f["image"]), (fT, f["final_T"]), (nc, f["n_contrib"]), (dimg, dref)):
+        assert torch.equal(a, b)
+    assert float(loss) == pytest.approx(float(lref), rel=1e-5)
+    dimg2 = torch.full_like(f["image"], 7.0)
+    gsr.gsr_forward_l1(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], st_["bg"], target, None, None, None, dimg2)
+    assert torch.equal(dimg2, dref)
