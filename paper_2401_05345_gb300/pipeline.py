@@ -285,3 +285,54 @@ class StepGraph:
         """After replays and a sync: True if every replay's binning fitted the
         key buffers."""
         return self.renderer.vb.check_bin()
+
+
+class StepPipeline:
+    """Training steps of one view fed from host memory with two steps in
+    flight.  ``submit`` copies the step's target from pinned host memory on a
+    copy stream, replays the captured step once the copy has landed, and
+    copies the loss back to pinned memory; ``result`` waits for one step's
+    loss.  So the upload of step k+1 overlaps the kernels of step k when the
+    caller submits step k+1 before reading step k's loss.
+
+    Each of the two target buffers has its own captured step (StepGraph);
+    a buffer is refilled only after the replay that last read it has
+    finished.  Handles name the buffer, so read a step's result before
+    submitting the step after the next.  Binning overflow works as for StepGraph: ``ok()`` after the
+    steps, capture again if it returns False."""
+
+    def __init__(self, renderer: "Renderer", sc: SceneTensors, bg, grads: SceneTensors, accumulate=False):
+        vb = renderer.vb
+        dev = vb.device
+        self.renderer = renderer
+        self.targets = [torch.zeros((3, vb.H, vb.W), dtype=torch.float32, device=dev) for _ in range(2)]
+        self.graphs = [StepGraph(renderer, sc, t, bg, grads, accumulate) for t in self.targets]
+        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.copied = [torch.cuda.Event() for _ in range(2)]
+        self.done = [torch.cuda.Event() for _ in range(2)]
+        self.loss_host = [torch.zeros(1, dtype=torch.float32).pin_memory() for _ in range(2)]
+        self.k = 0
+
+    def submit(self, target_host: torch.Tensor) -> int:
+        """Queues one step on the current stream; returns its handle."""
+        i = self.k % 2
+        main = torch.cuda.current_stream(self.targets[i].device)
+        if self.k >= 2:
+            self.copy_stream.wait_event(self.done[i])  # the replay that read this buffer has finished
+        with torch.cuda.stream(self.copy_stream):
+            self.targets[i].copy_(target_host, non_blocking=True)
+            self.copied[i].record(self.copy_stream)
+        main.wait_event(self.copied[i])
+        loss = self.graphs[i].replay()
+        self.loss_host[i].copy_(loss, non_blocking=True)
+        self.done[i].record(main)
+        self.k += 1
+        return i
+
+    def result(self, handle: int) -> float:
+        """The loss of the step ``handle`` (waits for that step only)."""
+        self.done[handle].synchronize()
+        return float(self.loss_host[handle][0])
+
+    def ok(self) -> bool:
+        return self.renderer.vb.check_bin()

@@ -143,3 +143,31 @@ def test_graph_backward_events_time_the_backward(dev):
         a, b = got[k].cpu().numpy(), ref[k].cpu().numpy()
         scale = np.abs(b).max()
         assert np.abs(a - b).max() <= 1e-4 * scale + 1e-7, k
+
+
+def test_pipeline_with_two_steps_in_flight(dev):
+    """StepPipeline: five steps on different targets, each submitted before
+    the previous step's loss is read, give every step's loss as a lone graph
+    replay on that target does, and the last step's outputs bit for bit."""
+    scene = S.gmm_scene(6, 40_000, components=8)
+    cam = S.front_camera(512, 384)
+    sc, grads, target, R = _setup(dev, scene, cam)
+    hosts = [torch.from_numpy(S.target_image(20 + i, cam.width, cam.height)).pin_memory() for i in range(5)]
+    pipe = pipeline.StepPipeline(R, sc, (0.0, 0.0, 0.0), grads)
+    losses, prev = [], None
+    for h in hosts:
+        k = pipe.submit(h)
+        if prev is not None:
+            losses.append(pipe.result(prev))
+        prev = k
+    losses.append(pipe.result(prev))
+    torch.cuda.synchronize()
+    assert pipe.ok()
+    last = _snapshot(R, grads)
+    g = pipeline.StepGraph(R, sc, target, (0.0, 0.0, 0.0), grads, accumulate=False)
+    for h, loss in zip(hosts, losses):
+        target.copy_(h)
+        g.replay()
+        torch.cuda.synchronize()
+        assert float(R.loss.item()) == pytest.approx(loss, rel=1e-5)
+    _assert_same(_snapshot(R, grads), last)
