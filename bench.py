@@ -138,6 +138,21 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate_over_ranks(tot_ms, e2e_ms, units, world, device):
+    """Whole-job numbers of the replicas (one view per rank, no data-path
+    collective): the slowest rank's device and end-to-end times, since the
+    job ends with its last rank, and the units of all ranks."""
+    if world <= 1:
+        return tot_ms, e2e_ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([tot_ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(u[0])
+
+
 # ----------------------------------------------------------------------------
 # CPU oracle on a bounded sample (band of tile rows)
 # ----------------------------------------------------------------------------
@@ -601,15 +616,7 @@ def run_ours(args):
 
     # aggregate over ranks
     import torch.distributed as dist
-    units_all = units * args.steps
-    e2e_tot = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms, e2e_tot], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([units_all], dtype=torch.float64, device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        tot_ms, e2e_tot = float(t[0]), float(t[1])
-        units_all = float(u[0])
+    tot_ms, e2e_tot, units_all = aggregate_over_ranks(tot_ms, sum(e2e_ms), units * args.steps, world, dev)
     value = units_all / (tot_ms / 1e3)
     e2e_value = units_all / (e2e_tot / 1e3)
 
