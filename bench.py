@@ -60,18 +60,33 @@ def load_peaks():
 # clocks during the timed region
 # ----------------------------------------------------------------------------
 class ClockSampler:
+    """nvidia-smi sampling every 20 ms on a reader thread.  Each sample is
+    stamped when it arrives; only samples that arrive between ``mark()``
+    calls (the timed region) are summarised.  ``start`` returns once the
+    first sample has arrived, so sampling is running when the timed region
+    begins."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, device_index):
         self.proc = None
-        self.lines = []
+        self.samples = []  # (arrival time, line)
+        self.window = [None, None]
         self.device_index = device_index
+        self.thread = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), line))
 
     def start(self):
+        import threading
+
         import torch
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms",
+               str(self.PERIOD_MS)]
         try:
             p = torch.cuda.get_device_properties(self.device_index)
             bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
@@ -82,20 +97,37 @@ class ClockSampler:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        t_end = time.perf_counter() + 10.0
+        while not self.samples and time.perf_counter() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def mark(self):
+        """First call: the timed region starts; second call: it ends."""
+        self.window[0 if self.window[0] is None else 1] = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
+        time.sleep(2.0 * self.PERIOD_MS / 1e3)  # the sample taken as the region ended
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        t0, t1 = self.window
+        if t0 is None or t1 is None:
+            return None
+        t1 += self.PERIOD_MS / 1e3
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for t, line in self.samples:
+            if not t0 <= t <= t1:
+                continue
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -110,7 +142,8 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "period_ms": self.PERIOD_MS,
+                "window_s": t1 - t0, "note": "samples arriving during the timed steps"}
 
 
 # ----------------------------------------------------------------------------
@@ -384,6 +417,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     if not args.profile:
         clocks.start()
+    clocks.mark()
     wall0 = time.perf_counter()
     graph_bwd_ms = []
     for k in range(args.steps):
@@ -400,6 +434,7 @@ def run_ours(args):
             e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    clocks.mark()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop() if not args.profile else None
@@ -724,7 +759,7 @@ LAUNCHES_PER_STEP = 17
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="single_view")
