@@ -487,10 +487,13 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                             else red_add(rec + rparam, z);
                         }
                     } else if (any) {
+                        if (MODE == GSR_REDUCE_BLOCK) {
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) {
-                            if (MODE == GSR_REDUCE_BLOCK) atomicAdd(&sm.acc[k * 9 + i], v[i]);
-                            else atomicAdd(rec + i, v[i]);
+                            for (int i = 0; i < 9; ++i) atomicAdd(&sm.acc[k * 9 + i], v[i]);
+                        } else {  // the 16-byte-aligned record takes two vector reds and one scalar
+                            red_add_v4(rec, v[0], v[1], v[2], v[3]);
+                            red_add_v4(rec + 4, v[4], v[5], v[6], v[7]);
+                            red_add(rec + 8, v[8]);
                         }
                     }
                 }
