@@ -528,7 +528,9 @@ int gsr_adam_step(int64_t n, float* param, const float* grad, float* m, float* v
  *            (threshold ignored).
  * idx [n] (uint32 row indices), vals [n,9], out [rows,stride] (stride >= 9,
  * accumulated).  Every method forms the same sums; only the float summation
- * order differs.
+ * order differs.  When stride is a multiple of 4 and out is 16-byte aligned,
+ * methods 1 and 2 send a record's 9 values as two 4-wide vector reds and one
+ * scalar red.
  */
 int gsr_scatter_add9(int64_t n, const uint32_t* idx, const float* vals, float* out, int32_t stride,
                      int32_t method, int32_t threshold, gsr_stream_t stream);

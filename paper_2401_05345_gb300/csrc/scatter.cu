@@ -15,13 +15,29 @@ __device__ __forceinline__ void load9(const float* __restrict__ v, float* x) {
 // PLAIN: one atomic add per parameter per item.
 // SERIAL: lanes with the same destination are found with match_any; a group
 //   of at least `threshold` lanes is summed by its lowest lane, which pulls
-//   each peer's 9 values in turn (all parameters per peer) and issues one red
-//   per parameter; smaller groups send per-lane atomics to L2.
+//   each peer's 9 values in turn (all parameters per peer) and sends the
+//   record's reds; smaller groups send each lane's reds to L2.  The reduced
+//   methods send a record as two vector reds and one scalar red when rows are
+//   16-byte aligned, else as 9 scalar reds.
 // SORTED: the warp's (destination, lane) pairs are sorted with a bitonic
 //   network in registers, each lane fetches the values of its sorted
 //   position, and a 5-step segmented shuffle scan leaves every group's total
 //   with the group's last lane, which issues the 9 reds.
-template <int METHOD>
+// The 9 reds of one record: with VEC (rows 16-byte aligned) two vector reds
+// and one scalar red.
+template <bool VEC>
+__device__ __forceinline__ void red9(float* rec, const float* x) {
+    if (VEC) {
+        red_add_v4(rec, x[0], x[1], x[2], x[3]);
+        red_add_v4(rec + 4, x[4], x[5], x[6], x[7]);
+        red_add(rec + 8, x[8]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) red_add(rec + q, x[q]);
+    }
+}
+
+template <int METHOD, bool VEC>
 __global__ void __launch_bounds__(256)
 scatter9_kernel(long long n, const uint32_t* __restrict__ idx, const float* __restrict__ vals,
                 float* __restrict__ out, int stride, int threshold) {
@@ -61,12 +77,9 @@ scatter9_kernel(long long n, const uint32_t* __restrict__ idx, const float* __re
                     if (lane == leader) x[q] += y;
                 }
             }
-            if (lane == leader)
-#pragma unroll
-                for (int q = 0; q < 9; ++q) red_add(rec + q, x[q]);
+            if (lane == leader) red9<VEC>(rec, x);
         } else {
-#pragma unroll
-            for (int q = 0; q < 9; ++q) atomicAdd(rec + q, x[q]);
+            red9<VEC>(rec, x);
         }
         return;
     }
@@ -89,11 +102,7 @@ scatter9_kernel(long long n, const uint32_t* __restrict__ idx, const float* __re
     }
     const uint32_t kn = __shfl_down_sync(kFull, key, 1);
     const bool run_end = (lane == 31) || (kn != key);
-    if (run_end && key != 0xffffffffu) {
-        float* rec = out + (size_t)key * stride;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) red_add(rec + q, y[q]);
-    }
+    if (run_end && key != 0xffffffffu) red9<VEC>(out + (size_t)key * stride, y);
 }
 
 }  // namespace
@@ -109,8 +118,12 @@ extern "C" int gsr_scatter_add9(int64_t n, const uint32_t* idx, const float* val
     if (n == 0) return GSR_OK;
     const unsigned blocks = (unsigned)((n + 255) / 256);
     cudaStream_t s = (cudaStream_t)stream;
-    if (method == 0) scatter9_kernel<0><<<blocks, 256, 0, s>>>(n, idx, vals, out, stride, threshold);
-    else if (method == 1) scatter9_kernel<1><<<blocks, 256, 0, s>>>(n, idx, vals, out, stride, threshold);
-    else scatter9_kernel<2><<<blocks, 256, 0, s>>>(n, idx, vals, out, stride, threshold);
+    // the reduced methods send a record as vector reds when every row is 16-byte aligned
+    const bool vec = (stride % 4) == 0 && aligned16(out);
+    if (method == 0) scatter9_kernel<0, false><<<blocks, 256, 0, s>>>(n, idx, vals, out, stride, threshold);
+    else if (method == 1 && vec) scatter9_kernel<1, true><<<blocks, 256, 0, s>>>(n, idx, vals, out, stride, threshold);
+    else if (method == 1) scatter9_kernel<1, false><<<blocks, 256, 0, s>>>(n, idx, vals, out, stride, threshold);
+    else if (vec) scatter9_kernel<2, true><<<blocks, 256, 0, s>>>(n, idx, vals, out, stride, threshold);
+    else scatter9_kernel<2, false><<<blocks, 256, 0, s>>>(n, idx, vals, out, stride, threshold);
     return check_launch();
 }

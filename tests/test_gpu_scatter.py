@@ -33,17 +33,18 @@ def divergent_indices(rng, n, distinct_per_warp, rows):
     return idx
 
 
+@pytest.mark.parametrize("stride", [12, 9])  # 12: rows 16-byte aligned (vector reds); 9: scalar reds
 @pytest.mark.parametrize("distinct", [1, 2, 3, 8, 32])
 @pytest.mark.parametrize("method,threshold", [("plain", 0), ("serial", 0), ("serial", 4), ("serial", 33),
                                               ("sorted", 0)])
-def test_scatter_add9_matches_oracle(dev, orc, distinct, method, threshold):
+def test_scatter_add9_matches_oracle(dev, orc, distinct, method, threshold, stride):
     rng = np.random.default_rng(distinct * 7 + threshold)
     n, rows = 10_000 + 13, 500
     idx = divergent_indices(rng, n, distinct, rows)
     vals = rng.normal(size=(n, 9)).astype(np.float32)
-    out = torch.zeros((rows, 12), device=dev)
-    gsr.gsr_scatter_add9(n, torch.from_numpy(idx.view(np.int32)).to(dev), torch.from_numpy(vals).to(dev), out, 12,
-                         method, threshold)
+    out = torch.zeros((rows, stride), device=dev)
+    gsr.gsr_scatter_add9(n, torch.from_numpy(idx.view(np.int32)).to(dev), torch.from_numpy(vals).to(dev), out,
+                         stride, method, threshold)
     got = out.cpu().numpy()
     ref = orc.scatter_add9(idx, vals.astype(np.float64), rows)
     scale = orc.scatter_add9(idx, np.abs(vals.astype(np.float64)), rows)
