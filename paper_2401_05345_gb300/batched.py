@@ -188,7 +188,7 @@ def autotune_batched(bv: BatchedViews, reps=3, flush=None):
     for ppt in (1, 2):
         for lay in (0, 1):
             cands.append((gsr.backward_opts("warp", 0, lay, bv.store_T, ppt), 0))
-            for thr in (8, 12, 16):
+            for thr in (8, 16, 24, 28):
                 for cps in (0, 2, 3):
                     cands.append((gsr.backward_opts("hybrid", thr, lay, bv.store_T, ppt), cps))
             cands.append((gsr.backward_opts("block", 0, lay, bv.store_T, ppt), 0))
