@@ -50,10 +50,10 @@ class _Rasterize(torch.autograd.Function):
     def backward(ctx, dL_dimage):
         mean, scale, quat, opacity, feat = ctx.saved_tensors
         vb, st = ctx.vb, ctx.settings
-        opts = st.opts if st.opts is not None else gsr.backward_opts("warp", 0, 0, st.store_T)
+        opts = st.opts if st.opts is not None else gsr.default_backward_opts(st.store_T)
         if bool(opts.store_T) != bool(st.store_T):
             opts = gsr.backward_opts(int(opts.reduce_mode), int(opts.threshold), int(opts.lane_layout),
-                                     st.store_T)
+                                     st.store_T, int(opts.pixels_per_thread))
         vb.backward(st.bg, dL_dimage.contiguous(), opts)
         sc = SceneTensors(mean, scale, quat, opacity, feat, ctx.sh_degree)
         g = sc.zeros_like_params()

@@ -54,6 +54,13 @@ def backward_opts(reduce="warp", threshold=0, lane_layout=0, store_T=True, pixel
     return o
 
 
+def default_backward_opts(store_T=True) -> BackwardOpts:
+    """The tier the autotuner picks on a GB300 for the 500k single-view
+    workload: HYBRID with threshold 24, 8x8 pixel blocks per warp, two pixels
+    per thread.  autotune.tune measures the candidates for a given view."""
+    return backward_opts("hybrid", 24, 1, store_T, 2)
+
+
 def camera(cam) -> Camera:
     """ctypes camera from an object with the fields of ``scenes.Camera``."""
     c = Camera()

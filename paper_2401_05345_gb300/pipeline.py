@@ -200,7 +200,7 @@ class Renderer:
 
     def __init__(self, n, cam, device="cuda", opts=None, store_T=True, key_capacity=None, deterministic=False):
         self.vb = ViewBuffers(n, cam, device, key_capacity, store_T)
-        self.opts = opts if opts is not None else gsr.backward_opts("warp", 0, 0, store_T)
+        self.opts = opts if opts is not None else gsr.default_backward_opts(store_T)
         self.deterministic = deterministic
         self.dimg = torch.zeros_like(self.vb.image)
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)

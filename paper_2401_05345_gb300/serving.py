@@ -448,7 +448,7 @@ def main():
     spec = [(int(ns[i]), args.steps, float(arrivals[i]), *res_list[i % 2]) for i in range(args.jobs)]
     jobs = make_jobs(spec, args.seed)
     budget = int(args.budget_gb * (1 << 30))
-    _, cont, _, sch = run_serving(spec, args.slots, budget, gsr.backward_opts("hybrid", 12, 1, True, 2), args.rate,
+    _, cont, _, sch = run_serving(spec, args.slots, budget, gsr.backward_opts("hybrid", 24, 1, True, 2), args.rate,
                                   args.seed, jobs=jobs)
     torch.cuda.synchronize()
     one_budget = max(j.footprint for j in jobs)
