@@ -335,6 +335,53 @@ def ingest_traffic(csv_path):
     return 0
 
 
+def large_scene_autograd(dev, flush, reps=5):
+    """The large differentiation workload (3M Gaussians, SH3, 1920x1080):
+    one training step through GaussianModel and the autograd Function
+    (forward, L1 loss in torch, backward into the raw parameters), with the
+    transmittance stored between the passes or recomputed by the backward.
+    Median CUDA-event time of ``reps`` steps (L2 flushed before each) and the
+    peak device memory of a step."""
+    import torch
+
+    from paper_2401_05345_gb300 import autograd as AG
+    from paper_2401_05345_gb300 import gsr
+    from paper_2401_05345_gb300 import scenes as S
+    scene, cam = S.large_workload(0)
+    model = AG.GaussianModel(scene, dev)
+    target = torch.from_numpy(S.target_image(0, cam.width, cam.height)).to(dev)
+    out = {"workload": f"large: {scene.n} Gaussians (256-component mixture), SH degree 3, "
+                       f"{cam.width}x{cam.height}, L1 loss, autograd"}
+    cap = None
+    for key, store_T in (("store", True), ("recompute", False)):
+        settings = AG.RasterSettings(cam, (0.0, 0.0, 0.0), gsr.default_backward_opts(store_T), store_T, cap)
+
+        def step():
+            model.zero_grad(set_to_none=False)
+            loss = (model(settings) - target).abs().sum()
+            loss.backward()
+        step()  # first step: allocations, key capacity
+        torch.cuda.synchronize()
+        ts = []
+        for r in range(reps):
+            flush()
+            torch.cuda.synchronize()
+            torch.cuda.reset_peak_memory_stats(dev)
+            base = torch.cuda.memory_allocated(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out[f"ms_{key}"] = statistics.median(ts)
+        out[f"step_peak_mb_{key}"] = (torch.cuda.max_memory_allocated(dev) - base) / 2 ** 20
+    out["per_pixel_state_mb_saved"] = 8.0 * cam.width * cam.height / 2 ** 20
+    out["note"] = ("per step: projection, synchronous binning, forward, torch L1, backward, backward projection, "
+                   "torch activation backward; view buffers allocated per call by the Function")
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -506,6 +553,8 @@ def run_ours(args):
     for thr in (4, 8, 12, 16, 20, 24, 28, 32):
         sweep[str(thr)] = autotune.time_backward(
             vb, bg, R.dimg, gsr.backward_opts("hybrid", thr, lay, True, ppt), 5, flush)
+
+    large = large_scene_autograd(dev, flush) if args.workload == "single_view" else None
 
     # L2 atomic (red) throughput: the plain tier's roofline
     red_buf = torch.zeros(12 * 1_000_000, dtype=torch.float32, device=dev)
@@ -716,6 +765,7 @@ def run_ours(args):
                            "note": "same outputs; each includes its one host sync for the key count"},
             "texture_gradient": tex_results,
             "l2_red_adds_per_s": red,
+            "differentiation_large": large,
             "divergent_accumulation_ms": {"items": n_items, "records": rows,
                                           "by_distinct_destinations_per_warp": scat},
             "traffic_counts": {"P_active": p_active, "P_examined": p_exam, "P_ts": vb.n_keys,
