@@ -820,7 +820,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu)")
     ap.add_argument("--stream-launches", action="store_true",
                     help="launch the steps kernel by kernel instead of replaying one CUDA graph")
-    ap.add_argument("--opts", default="hybrid-thr16-lay1-ppt2", help="backward tier of a --profile run")
+    ap.add_argument("--opts", default="hybrid-thr24-lay1-ppt2", help="backward tier of a --profile run")
     ap.add_argument("--profile-tiers", action="store_true",
                     help="--profile: then one backward launch per autotune candidate")
     ap.add_argument("--ingest-traffic", metavar="CSV",
