@@ -245,7 +245,8 @@ backward_det_kernel(BwdArgs p) {
 }
 
 // Clears the 9 slots of every entry (nothing when the entry count exceeds cap).
-__global__ void zero_partial_kernel(int n, const uint32_t* __restrict__ off, uint32_t cap, float* __restrict__ partial) {
+__global__ void zero_partial_kernel(int n, const uint32_t* __restrict__ off, uint32_t cap,
+                                    float* __restrict__ partial) {
     const uint32_t cnt = off[n];
     if (cnt > cap) return;
     const size_t total = 9 * (size_t)cnt;

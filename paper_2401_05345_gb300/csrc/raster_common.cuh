@@ -428,95 +428,100 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
         if (MODE == kModeDet)
             for (int e = tid; e < cnt; e += NT) det.wflags[e] = 0u;  // entries this thread staged
         __syncthreads();
-        // each warp visits, back to front, only the staged splats whose
-        // alpha >= 1/255 region touches its pixel block and that lie before
-        // the warp's last contributor
+        // The batch is taken in groups of DG entries: the deterministic tier
+        // combines its per-warp sums after each group, the other tiers take
+        // the whole batch as one group.  Each warp visits, back to front, only
+        // the staged splats whose alpha >= 1/255 region touches its pixel
+        // block and that lie before the warp's last contributor.
         for (int grp0 = 0; grp0 < cnt; grp0 += DG) {
-        const int grp1 = min(cnt, grp0 + DG);
-        for (int c0 = grp0; c0 < grp1; c0 += 32) {
-            const int kq = c0 + lane;
-            unsigned bits =
-                __ballot_sync(kFull, kq < grp1 && ((sm.mask[kq] >> warp) & 1u) && (top - 1 - kq < wlast));
-            while (bits) {
-                const int k = c0 + __ffs(bits) - 1;
-                bits &= bits - 1u;
-                const int pos = top - 1 - k;
-                const float4 a = sm.a[k], b = sm.b[k];
-                const float cb = sm.c[k];
-                float v[9];
+            const int grp1 = min(cnt, grp0 + DG);
+            for (int c0 = grp0; c0 < grp1; c0 += 32) {
+                const int kq = c0 + lane;
+                unsigned bits =
+                    __ballot_sync(kFull, kq < grp1 && ((sm.mask[kq] >> warp) & 1u) && (top - 1 - kq < wlast));
+                while (bits) {
+                    const int k = c0 + __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    const int pos = top - 1 - k;
+                    const float4 a = sm.a[k], b = sm.b[k];
+                    const float cb = sm.c[k];
+                    float v[9];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) v[i] = 0.0f;
-                bool any = false;
+                    for (int i = 0; i < 9; ++i) v[i] = 0.0f;
+                    bool any = false;
 #pragma unroll
-                for (int q = 0; q < PPT; ++q) {
-                    SplatEval e;
-                    const bool act = (pos < last[q]) && eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, fpx[q], fpy[q], e);
-                    if (act) pair_grads(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
-                    any |= act;
-                }
-                float* rec = grad + (size_t)sm.id[k] * GSR_REC;
-                if (MODE == kModeDet) {
-                    if (__ballot_sync(kFull, any) == 0u) continue;
-                    const float z = reduce9(v, lane);
-                    if (rparam < 9) det.part[(warp * DG + (k - grp0)) * 9 + rparam] = z;
-                    if (lane == 0) atomicOr(&det.wflags[k], 1u << warp);
-                } else if (MODE == GSR_REDUCE_PLAIN) {
-                    if (any) {
-#pragma unroll
-                        for (int i = 0; i < 9; ++i) atomicAdd(rec + i, v[i]);
+                    for (int q = 0; q < PPT; ++q) {
+                        SplatEval e;
+                        const bool act = (pos < last[q]) && eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, fpx[q], fpy[q], e);
+                        if (act) pair_grads(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
+                        any |= act;
                     }
-                } else {
-                    const unsigned m = __ballot_sync(kFull, any);
-                    if (m == 0u) continue;
-                    const bool dense = (MODE == GSR_REDUCE_WARP) || (__popc(m) >= p.threshold);
-                    if (dense) {
+                    float* rec = grad + (size_t)sm.id[k] * GSR_REC;
+                    if (MODE == kModeDet) {
+                        if (__ballot_sync(kFull, any) == 0u) continue;
                         const float z = reduce9(v, lane);
-                        if (MODE == kModeCluster) {
-                            uint32_t owner = 0;
-                            int slot = -1;
-                            if (lane == 0) slot = cluster_slot(*ct, sm.id[k], owner);
-                            slot = __shfl_sync(kFull, slot, 0);
-                            owner = __shfl_sync(kFull, owner, 0);
-                            if (rparam < 9) {
-                                if (slot >= 0)
-                                    dsm_red_add(cluster_map(ct->val_base + 4u * (uint32_t)(slot * 9 + rparam), owner), z);
+                        if (rparam < 9) det.part[(warp * DG + (k - grp0)) * 9 + rparam] = z;
+                        if (lane == 0) atomicOr(&det.wflags[k], 1u << warp);
+                    } else if (MODE == GSR_REDUCE_PLAIN) {
+                        if (any) {
+#pragma unroll
+                            for (int i = 0; i < 9; ++i) atomicAdd(rec + i, v[i]);
+                        }
+                    } else {
+                        const unsigned m = __ballot_sync(kFull, any);
+                        if (m == 0u) continue;
+                        const bool dense = (MODE == GSR_REDUCE_WARP) || (__popc(m) >= p.threshold);
+                        if (dense) {
+                            const float z = reduce9(v, lane);
+                            if (MODE == kModeCluster) {
+                                uint32_t owner = 0;
+                                int slot = -1;
+                                if (lane == 0) slot = cluster_slot(*ct, sm.id[k], owner);
+                                slot = __shfl_sync(kFull, slot, 0);
+                                owner = __shfl_sync(kFull, owner, 0);
+                                if (rparam < 9) {
+                                    if (slot >= 0) {
+                                        const uint32_t la = ct->val_base + 4u * (uint32_t)(slot * 9 + rparam);
+                                        dsm_red_add(cluster_map(la, owner), z);
+                                    } else {
+                                        red_add(rec + rparam, z);
+                                    }
+                                }
+                            } else if (rparam < 9) {
+                                if (MODE == GSR_REDUCE_BLOCK) atomicAdd(&sm.acc[k * 9 + rparam], z);
                                 else red_add(rec + rparam, z);
                             }
-                        } else if (rparam < 9) {
-                            if (MODE == GSR_REDUCE_BLOCK) atomicAdd(&sm.acc[k * 9 + rparam], z);
-                            else red_add(rec + rparam, z);
-                        }
-                    } else if (any) {
-                        if (MODE == GSR_REDUCE_BLOCK) {
+                        } else if (any) {
+                            if (MODE == GSR_REDUCE_BLOCK) {
 #pragma unroll
-                            for (int i = 0; i < 9; ++i) atomicAdd(&sm.acc[k * 9 + i], v[i]);
-                        } else {  // the 16-byte-aligned record takes two vector reds and one scalar
-                            red_add_v4(rec, v[0], v[1], v[2], v[3]);
-                            red_add_v4(rec + 4, v[4], v[5], v[6], v[7]);
-                            red_add(rec + 8, v[8]);
+                                for (int i = 0; i < 9; ++i) atomicAdd(&sm.acc[k * 9 + i], v[i]);
+                            } else {  // the 16-byte-aligned record takes two vector reds and one scalar
+                                red_add_v4(rec, v[0], v[1], v[2], v[3]);
+                                red_add_v4(rec + 4, v[4], v[5], v[6], v[7]);
+                                red_add(rec + 8, v[8]);
+                            }
                         }
                     }
                 }
             }
-        }
-        if (MODE == kModeDet) {
-            // warp partials combined in warp order: a fixed summation order
-            __syncthreads();
-            for (int k = grp0 + tid; k < grp1; k += NT) {
-                const unsigned fl = det.wflags[k];
-                if (fl == 0u) continue;  // the slot keeps the zeros it was cleared to
-                float* dst = p.partial + 9 * (size_t)entry_slot(p, sm.id[k], sm.a[k].x, sm.a[k].y, tile);
+            if (MODE == kModeDet) {
+                // warp partials combined in warp order: a fixed summation order
+                __syncthreads();
+                for (int k = grp0 + tid; k < grp1; k += NT) {
+                    const unsigned fl = det.wflags[k];
+                    if (fl == 0u) continue;  // the slot keeps the zeros it was cleared to
+                    float* dst = p.partial + 9 * (size_t)entry_slot(p, sm.id[k], sm.a[k].x, sm.a[k].y, tile);
 #pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    float sum = 0.0f;
+                    for (int q = 0; q < 9; ++q) {
+                        float sum = 0.0f;
 #pragma unroll
-                    for (int w = 0; w < SH::NW; ++w)
-                        if ((fl >> w) & 1u) sum += det.part[(w * DG + (k - grp0)) * 9 + q];
-                    dst[q] = sum;
+                        for (int w = 0; w < SH::NW; ++w)
+                            if ((fl >> w) & 1u) sum += det.part[(w * DG + (k - grp0)) * 9 + q];
+                        dst[q] = sum;
+                    }
                 }
+                if (grp1 < cnt) __syncthreads();  // the next group reuses the partial sums' storage
             }
-            if (grp1 < cnt) __syncthreads();  // the next group reuses the partial sums' storage
-        }
         }
         if (MODE == GSR_REDUCE_BLOCK) {
             __syncthreads();
