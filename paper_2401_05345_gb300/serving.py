@@ -282,6 +282,9 @@ class GpuExecutor:
         self.bg = bg
         self.key_capacity_per_gaussian = key_capacity_per_gaussian
         self.rebins = 0  # phase-1 reruns after a key-buffer overflow
+        self.copy_stream = torch.cuda.Stream(device=device)
+        self._unloading = []  # (job id, pinned host copy, event, device state)
+        self._final_params = {}
         self.t0_event = torch.cuda.Event(enable_timing=True)
         self.t0_event.record()
         self.t0_host = time.perf_counter()
@@ -293,43 +296,73 @@ class GpuExecutor:
 
     # job state on the device ------------------------------------------------
     def load(self, job):
+        """Allocates the job's device state and queues the upload of its
+        parameters and targets on the copy stream; nothing waits.  Steps of
+        the job wait for the upload on the GPU (``issue``)."""
         torch = self.torch
-        scene, cam, targets = job.payload
-        n = scene.n
-        k = scene.feat.reshape(n, -1).shape[1]
-        sizes = [3 * n, 3 * n, 4 * n, n, k * n]
-        # every segment starts on a 16-byte boundary (vector loads of the features)
-        padded = [(x + 3) // 4 * 4 for x in sizes]
-        P = torch.zeros(sum(padded), dtype=torch.float32, device=self.device)
-        offs = np.cumsum([0] + padded)
-        views = [P[offs[i]:offs[i] + sizes[i]] for i in range(5)]
-        views[0].copy_(torch.from_numpy(scene.mean.reshape(-1)))
-        views[1].copy_(torch.from_numpy(np.log(scene.scale.astype(np.float64)).astype(np.float32).reshape(-1)))
-        views[2].copy_(torch.from_numpy(scene.quat.reshape(-1)))
-        o = scene.opacity.astype(np.float64)
-        views[3].copy_(torch.from_numpy((np.log(o) - np.log1p(-o)).astype(np.float32)))
-        views[4].copy_(torch.from_numpy(scene.feat.reshape(-1)))
-        G = torch.zeros_like(P)
-        gv = [G[offs[i]:offs[i] + sizes[i]] for i in range(5)]
-        st = dict(P=P, G=G, M=torch.zeros_like(P), V=torch.zeros_like(P), pv=views, gv=gv, n=n,
-                  sh=scene.sh_degree, scale=torch.empty(3 * n, device=self.device),
-                  opac=torch.empty(n, device=self.device), dscale=torch.empty(3 * n, device=self.device),
-                  dopac=torch.empty(n, device=self.device),
-                  vb=self.pipeline.ViewBuffers(n, cam, self.device,
-                                               max(1024, int(self.key_capacity_per_gaussian * n))),
-                  targets=[torch.from_numpy(t).to(self.device) for t in targets],
-                  loss=torch.zeros(1, device=self.device),
-                  loss_host=torch.zeros(1).pin_memory(),
-                  bin_host=torch.zeros(2, dtype=torch.int32).pin_memory(), adam_step=0)
-        st["dimg"] = torch.empty_like(st["vb"].image)
-        torch.cuda.synchronize(self.device)
+        data = job.payload if isinstance(job.payload, JobData) else prepare_job_data(*job.payload)
+        n, sizes, offs = data.n, data.sizes, data.offsets
+        self._reap()
+        with torch.cuda.stream(self.copy_stream):
+            P = torch.empty(data.params.numel(), dtype=torch.float32, device=self.device)
+            P.copy_(data.params, non_blocking=True)
+            views = [P[offs[i]:offs[i] + sizes[i]] for i in range(5)]
+            G = torch.zeros_like(P)
+            gv = [G[offs[i]:offs[i] + sizes[i]] for i in range(5)]
+            targets = []
+            for t in data.targets:
+                d = torch.empty(t.shape, dtype=torch.float32, device=self.device)
+                d.copy_(t, non_blocking=True)
+                targets.append(d)
+            st = dict(P=P, G=G, M=torch.zeros_like(P), V=torch.zeros_like(P), pv=views, gv=gv, n=n,
+                      sh=data.sh_degree, scale=torch.empty(3 * n, device=self.device),
+                      opac=torch.empty(n, device=self.device), dscale=torch.empty(3 * n, device=self.device),
+                      dopac=torch.empty(n, device=self.device),
+                      vb=self.pipeline.ViewBuffers(n, data.cam, self.device,
+                                                   max(1024, int(self.key_capacity_per_gaussian * n))),
+                      targets=targets, loss=torch.zeros(1, device=self.device),
+                      loss_host=torch.zeros(1).pin_memory(),
+                      bin_host=torch.zeros(2, dtype=torch.int32).pin_memory(), adam_step=0)
+            st["dimg"] = torch.empty_like(st["vb"].image)
+            st["ready"] = torch.cuda.Event()
+            st["ready"].record(self.copy_stream)
         self.loaded[job.job_id] = st
 
     def unload(self, job):
+        """Queues the copy of the job's final parameters to pinned host
+        memory; the device state is released once that copy has finished
+        (the scheduler already counts the footprint as free)."""
+        torch = self.torch
         st = self.loaded.pop(job.job_id, None)
-        if st is not None:
-            self.final_params = getattr(self, "final_params", {})
-            self.final_params[job.job_id] = st["P"].detach().cpu().numpy()
+        if st is None:
+            return
+        host = torch.empty(st["P"].numel(), dtype=torch.float32).pin_memory()
+        with torch.cuda.stream(self.copy_stream):
+            if "done" in st:  # the job's last step (a job cancelled before any step has none)
+                self.copy_stream.wait_event(st["done"])
+            host.copy_(st["P"], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.copy_stream)
+        self._unloading.append((job.job_id, host, ev, st))
+
+    def _reap(self, wait=False):
+        """Moves finished final-parameter copies to final_params and drops
+        those jobs' device state."""
+        keep = []
+        for jid, host, ev, st in self._unloading:
+            if wait:
+                ev.synchronize()
+            if ev.query():
+                self._final_params[jid] = host.numpy()
+            else:
+                keep.append((jid, host, ev, st))
+        self._unloading = keep
+
+    @property
+    def final_params(self):
+        """Final raw parameters of every unloaded job (waits for pending copies)."""
+        self._reap(wait=True)
+        return self._final_params
 
     def issue(self, slot, job, step):
         h = _Step(self.loaded[job.job_id], job.job_id, step, self.streams[slot])
@@ -341,6 +374,7 @@ class GpuExecutor:
         st, s = h.st, h.stream
         n = st["n"]
         pv, gv, vb = st["pv"], st["gv"], st["vb"]
+        s.wait_event(st["ready"])  # the job's upload (complete after its first step)
         with torch.cuda.stream(s):
             gsr.gsr_activate(n, pv[1], pv[3], st["scale"], st["opac"], s)
             sc = self.pipeline.SceneTensors(pv[0], st["scale"], pv[2], st["opac"], pv[4], st["sh"])
@@ -375,6 +409,7 @@ class GpuExecutor:
                               st["adam_step"], s)
             h.event = torch.cuda.Event(enable_timing=True)
             h.event.record(s)
+            st["done"] = h.event
         h.phase = 2
 
     def poll(self, h):
@@ -395,6 +430,39 @@ class GpuExecutor:
         return completed + 0.0, loss
 
 
+@dataclasses.dataclass
+class JobData:
+    """What a client submits with a job: the raw parameters packed in the
+    executor's layout (mean, log-scale, quaternion, opacity logit, features;
+    each segment starting on 16 bytes) in pinned host memory, the camera and
+    the target images (pinned)."""
+    n: int
+    sh_degree: int
+    sizes: list
+    offsets: list
+    params: object
+    cam: object
+    targets: list
+
+
+def prepare_job_data(scene, cam, targets) -> JobData:
+    import torch
+    n = scene.n
+    k = scene.feat.reshape(n, -1).shape[1]
+    sizes = [3 * n, 3 * n, 4 * n, n, k * n]
+    padded = [(x + 3) // 4 * 4 for x in sizes]
+    offs = [int(x) for x in np.cumsum([0] + padded)]
+    flat = np.zeros(offs[-1], np.float32)
+    o = scene.opacity.astype(np.float64)
+    parts = [scene.mean.reshape(-1), np.log(scene.scale.astype(np.float64)).reshape(-1), scene.quat.reshape(-1),
+             np.log(o) - np.log1p(-o), scene.feat.reshape(-1)]
+    for i, part in enumerate(parts):
+        flat[offs[i]:offs[i] + sizes[i]] = part
+    params = torch.from_numpy(flat).pin_memory()
+    tg = [torch.from_numpy(np.ascontiguousarray(t, dtype=np.float32)).pin_memory() for t in targets]
+    return JobData(n, int(scene.sh_degree), sizes, offs, params, cam, tg)
+
+
 def make_jobs(spec, seed=0):
     """``spec``: list of (n, steps, arrival_s, width, height)."""
     from . import scenes as S
@@ -404,7 +472,8 @@ def make_jobs(spec, seed=0):
         rng = np.random.default_rng(seed + 7 * i)
         cams = S.sphere_cameras(rng, 1, (0.0, 0.0, 0.0), 4.0, [(w, h)])
         targets = [S.target_image(seed + i, w, h)]
-        jobs.append(Job(i, n, steps, arrival, job_footprint(n, 3, w, h), payload=(scene, cams[0], targets)))
+        jobs.append(Job(i, n, steps, arrival, job_footprint(n, 3, w, h),
+                        payload=prepare_job_data(scene, cams[0], targets)))
     return jobs
 
 
