@@ -193,16 +193,17 @@ class OracleSample:
     """The FP64 oracle pipeline on a bounded sample of the workload.  The
     whole-scene stages (projection, binning, backward projection) run once and
     are timed; each sample then rasterizes (forward, L1 gradient, backward) a
-    band of ``rows`` tile rows and is charged the band's share of the
-    whole-scene stages."""
+    band of ``rows`` tile rows (``cols`` tile columns of them, centred, if
+    given) and is charged the band's share of the whole-scene stages."""
 
-    def __init__(self, scene, cam, target, rows):
+    def __init__(self, scene, cam, target, rows, cols=None):
         from oracle import oracle as O
         O.build()
         self.O, self.scene, self.cam, self.target = O, scene, cam, target
         W, H = cam.width, cam.height
         self.gx, self.gy = (W + 15) // 16, (H + 15) // 16
         self.rows = max(1, min(rows, self.gy))
+        self.cols = self.gx if cols is None else max(1, min(int(cols), self.gx))
         t0 = time.perf_counter()
         self.pp = O.preprocess(scene, cam)
         self.keys, self.pl, self.ranges = O.bin_sort(self.pp["uv"], self.pp["depth"], self.pp["radius"], W, H)
@@ -215,25 +216,31 @@ class OracleSample:
         O, pp, cam = self.O, self.pp, self.cam
         W, H = cam.width, cam.height
         r0 = (self.gy // 2 - self.rows // 2 + band_index) % max(1, self.gy - self.rows + 1)
+        c0 = (self.gx - self.cols) // 2
         mask = np.zeros((self.gy, self.gx), np.uint8)
-        mask[r0:r0 + self.rows] = 1
-        frac = self.rows / self.gy
+        mask[r0:r0 + self.rows, c0:c0 + self.cols] = 1
+        frac = self.rows * self.cols / (self.gy * self.gx)
         bg = np.zeros(3)
         t0 = time.perf_counter()
         fwd = O.render(W, H, self.ranges, self.pl, pp["uv"], pp["conic"], pp["opacity"], pp["rgb"], bg, None,
                        extras=False, tile_mask=mask.reshape(-1))
         band = np.zeros((H, W), bool)
-        band[r0 * 16:min(H, (r0 + self.rows) * 16)] = True
+        band[r0 * 16:min(H, (r0 + self.rows) * 16), c0 * 16:min(W, (c0 + self.cols) * 16)] = True
         dimg = np.where(band[None], np.sign(fwd["image"] - self.target), 0.0).astype(np.float32)
         out = O.render(W, H, self.ranges, self.pl, pp["uv"], pp["conic"], pp["opacity"], pp["rgb"], bg, dimg,
                        extras=False, tile_mask=mask.reshape(-1))
         t1 = time.perf_counter()
         updates = 9 * int(out["n_active"][band].sum())
         seconds = (t1 - t0) + frac * self.t_global
-        desc = (f"FP64 oracle, 1 thread: forward + L1 gradient + backward on {self.rows} of {self.gy} tile rows "
+        part = (f"{self.rows} of {self.gy} tile rows" if self.cols == self.gx else
+                f"{self.rows} x {self.cols} of {self.gy} x {self.gx} tiles")
+        desc = (f"FP64 oracle, 1 thread: forward + L1 gradient + backward on {part} "
                 f"per sample; projection + binning + backward projection of the whole scene "
                 f"({self.t_global:.2f} s, timed once) charged at {frac:.4f} per sample")
         return updates, seconds, desc
+
+
+REF_BUDGET_S = 120.0  # oracle seconds of a reference run (warm-up and timed steps)
 
 
 def run_reference(args):
@@ -244,6 +251,16 @@ def run_reference(args):
     vals, times = [], []
     note = ""
     smp = OracleSample(scene, cam, target, args.cpu_rows)
+    # each step is a band sized so that the W + K steps take about REF_BUDGET_S
+    # of oracle time: the first warm-up step measures the band's cost
+    t_probe = time.perf_counter()
+    smp.run(0)
+    per_tile = (time.perf_counter() - t_probe) / (smp.rows * smp.cols)
+    tiles = REF_BUDGET_S / max(1, args.warmup + args.steps) / per_tile
+    if tiles < smp.rows * smp.cols:
+        rows = max(1, min(smp.rows, int(tiles // smp.gx)))
+        cols = max(1, min(smp.gx, int(tiles // rows)))
+        smp.rows, smp.cols = rows, cols
     for i in range(args.warmup + args.steps):
         upd, sec, note = smp.run(i)
         if i >= args.warmup:
