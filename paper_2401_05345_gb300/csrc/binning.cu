@@ -133,14 +133,17 @@ colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restric
         for (int r = r0; r < r1; ++r) sum += m[(size_t)r * cols + c];
     s_seg[seg][cx] = sum;
     __syncthreads();
-    if (seg == 0) {
-        uint32_t run = 0;
-        for (int q = 0; q < 32; ++q) {
-            const uint32_t x = s_seg[q][cx];
-            s_seg[q][cx] = run;
-            run += x;
+    {   // exclusive scan over the segments: warp `seg` takes column `seg`, lane `cx` its segment `cx`
+        const uint32_t x = s_seg[cx][seg];
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (cx >= o) incl += t;
         }
-        if (c < cols) tot[c] = run;
+        s_seg[cx][seg] = incl - x;
+        const int cc = blockIdx.x * 32 + seg;
+        if (cx == 31 && cc < cols) tot[cc] = incl;
     }
     __syncthreads();
     if (c < cols) {
@@ -303,6 +306,9 @@ radix_scatter_kernel(int n, const uint32_t* __restrict__ kin, const uint32_t* __
 // ---- tile counting sort -----------------------------------------------------
 constexpr int kPlaceWarps = 8;
 constexpr int kPlaceThreads = 32 * kPlaceWarps;
+// Earlier same-row peers a placement lane checks for overlap (more peers:
+// every row of the group takes the turn of its rank).
+constexpr int kOverlapScan = 8;
 constexpr int kMaxWindowTiles = 8192;  // tiles handled per placement window
 constexpr int kTargetSMs = 152;
 constexpr int kRectPer = 8;                            // Gaussians per thread of the rectangle pass
@@ -606,10 +612,9 @@ place_kernel(int n, int nb, Geom g, int t0, int tw, uint32_t cap, const uint32_t
     if (mine)
         walk_rows<false>(wb, lane, n, e0, e1, k, rects, nullptr, nullptr, pk, g, t0, [&](bool ok, const RowWork& r) {
             if (!ok) return;
-            for (int x = r.xs; x < r.xe; ++x) {
-                const int t = r.row_t0 + x;
-                if ((unsigned)t < (unsigned)tw) atomicAdd(&wc[t >> 1], (t & 1) ? 0x10000u : 1u);
-            }
+            const int lo = max(r.row_t0 + r.xs, 0), hi = min(r.row_t0 + r.xe, tw);
+            for (int q = lo >> 1; 2 * q < hi; ++q)
+                atomicAdd(&wc[q], (2 * q >= lo ? 1u : 0u) + (2 * q + 1 < hi ? 0x10000u : 0u));
         });
     __syncthreads();
     // tile bases; per-warp exclusive offsets (two tiles per word)
@@ -634,26 +639,53 @@ place_kernel(int n, int nb, Geom g, int t0, int tw, uint32_t cap, const uint32_t
     const uint32_t key_total = info[0];
     walk_rows<true>(wb, lane, n, e0, e1, k, rects, order, KEYS ? dkeys : nullptr, pk, g, t0,
                     [&](bool ok, const RowWork& r) {
-        // rows of the same tile row in one round share tiles: they take
-        // turns in lane order (lane order is depth order); rows of
-        // different tile rows never share a tile
+        // rows of the same tile row in one round may share tiles: those
+        // take turns in lane order (lane order is depth order).  A row that
+        // overlaps no earlier row of its tile row goes in the first turn,
+        // the others in the turn of their rank; rows of different tile
+        // rows never share a tile.
         const unsigned peers = __match_any_sync(kFull, ok ? (uint32_t)r.y : 0xffffffffu);
         const int rank = __popc(peers & lt);
-        const int turns = __reduce_max_sync(kFull, ok ? __popc(peers) : 0);
+        const int maxrank = __reduce_max_sync(kFull, ok ? rank : 0);
+        int my_turn = rank;
+        if (maxrank > 0 && maxrank <= kOverlapScan) {
+            const int ts = ok ? r.row_t0 + r.xs : 0, te = ok ? r.row_t0 + r.xe : 0;
+            unsigned below = ok ? (peers & lt) : 0u;
+            bool overlap = false;
+            for (int q = 0; q < maxrank; ++q) {  // earlier peers, nearest first
+                const int pl = below ? 31 - __clz(below) : lane;
+                if (below) below ^= 1u << pl;
+                const int ps = __shfl_sync(kFull, ts, pl), pe = __shfl_sync(kFull, te, pl);
+                overlap |= pl != lane && ps < te && ts < pe;
+            }
+            if (!overlap) my_turn = 0;
+        }
+        const int turns = __reduce_max_sync(kFull, ok ? my_turn + 1 : 0);
         const uint32_t id = ok ? wb.id[r.j] : 0u;
         const uint64_t dk = KEYS && ok ? (uint64_t)wb.dk[r.j] : 0ull;
         for (int turn = 0; turn < turns; ++turn) {
-            if (ok && rank == turn) {
-                for (int x = r.xs; x < r.xe; ++x) {
-                    const int t = r.row_t0 + x;
-                    if ((unsigned)t >= (unsigned)tw) continue;
-                    const uint32_t c = c16[t];
-                    const uint32_t pos = s_base[t] + c;
-                    if (pos < key_total) {  // always, unless the counts were inconsistent
-                        point_list[pos] = id;
-                        if (KEYS) keys_out[pos] = ((uint64_t)(uint32_t)(t + t0) << 32) | dk;
+            if (ok && my_turn == turn) {
+                for (int xb = r.xs; xb < r.xe; xb += 4) {
+                    int t[4];
+                    bool in[4];
+                    uint32_t c[4], sb[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        t[i] = r.row_t0 + xb + i;
+                        in[i] = xb + i < r.xe && (unsigned)t[i] < (unsigned)tw;
+                        c[i] = in[i] ? (uint32_t)c16[t[i]] : 0u;
+                        sb[i] = in[i] ? s_base[t[i]] : 0u;
                     }
-                    c16[t] = (uint16_t)(c + 1);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (!in[i]) continue;
+                        const uint32_t pos = sb[i] + c[i];
+                        if (pos < key_total) {  // always, unless the counts were inconsistent
+                            point_list[pos] = id;
+                            if (KEYS) keys_out[pos] = ((uint64_t)(uint32_t)(t[i] + t0) << 32) | dk;
+                        }
+                        c16[t[i]] = (uint16_t)(c[i] + 1);
+                    }
                 }
             }
             __syncwarp();

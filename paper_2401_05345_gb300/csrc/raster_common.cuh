@@ -130,6 +130,24 @@ __device__ __forceinline__ void stage_batch(int cnt, PosOf pos_of, const uint32_
     }
 }
 
+// eval_splat without the early return: every field is set (G and alpha from
+// the same operations), and the result is eval_splat's.
+__device__ __forceinline__ bool eval_splat_all(float u, float v, float A, float B, float C, float o, float px,
+                                               float py, SplatEval& e) {
+    e.dx = __fsub_rn(u, px);
+    e.dy = __fsub_rn(v, py);
+    e.dxx = __fmul_rn(e.dx, e.dx);
+    e.dyy = __fmul_rn(e.dy, e.dy);
+    e.dxy = __fmul_rn(e.dx, e.dy);
+    const float q = __fmaf_rn(C, e.dyy, __fmul_rn(A, e.dxx));
+    e.sigma = __fmaf_rn(0.5f, q, __fmul_rn(B, e.dxy));
+    e.G = __expf(-e.sigma);
+    const float oG = __fmul_rn(o, e.G);
+    e.capped = oG > kAlphaMax;
+    e.alpha = e.capped ? kAlphaMax : oG;
+    return e.sigma >= 0.0f && e.alpha >= kAlphaMin;
+}
+
 // Front-to-back walk of each of the thread's pixels over the tile list (the
 // forward rule; shared by the forward kernel and the recompute mode of the
 // backward, so both produce the same final transmittance and last
@@ -166,33 +184,31 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
                 const int k = c0 + __ffs(bits) - 1;
                 bits &= bits - 1u;
                 const float4 a = s_a[k], b = s_b[k];
+                const float cz = COLOR ? s_c[k] : 0.0f;
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
-                    if (done[q]) continue;
+                    // no branches: a pixel that is done or skips the splat
+                    // keeps T, last and C (its blend weight is 0)
                     SplatEval e;
-                    if (!eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, px[q], py[q], e)) continue;
+                    const bool hit = eval_splat_all(a.x, a.y, a.z, a.w, b.x, b.y, px[q], py[q], e) && !done[q];
                     const float testT = __fmul_rn(T[q], __fsub_rn(1.0f, e.alpha));
-                    if (testT < kTMin) {
-                        done[q] = true;
-                        continue;
-                    }
+                    const bool stop = hit && testT < kTMin;
+                    const bool take = hit && !stop;
+                    done[q] = done[q] || stop;
                     if (COLOR) {
-                        const float wgt = __fmul_rn(e.alpha, T[q]);
+                        const float wgt = take ? __fmul_rn(e.alpha, T[q]) : 0.0f;
                         C[q][0] = __fmaf_rn(b.z, wgt, C[q][0]);
                         C[q][1] = __fmaf_rn(b.w, wgt, C[q][1]);
-                        C[q][2] = __fmaf_rn(s_c[k], wgt, C[q][2]);
+                        C[q][2] = __fmaf_rn(cz, wgt, C[q][2]);
                     }
-                    T[q] = testT;
-                    last[q] = base + k + 1;
-                }
-                all_done = true;
-#pragma unroll
-                for (int q = 0; q < PPT; ++q) all_done &= done[q];
-                if (__all_sync(kFull, all_done)) {
-                    wdone = true;
-                    break;
+                    T[q] = take ? testT : T[q];
+                    last[q] = take ? base + k + 1 : last[q];
                 }
             }
+            all_done = true;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) all_done &= done[q];
+            wdone = __all_sync(kFull, all_done);
         }
     }
 }
@@ -323,6 +339,7 @@ struct BwdSmem {
 // dL/d(u, v) = (A dx + B dy, B dx + C dy) dL/dsigma,
 // dL/d(A, B, C) = (dx^2/2, dx dy, dy^2/2) dL/dsigma.  Every output is one
 // fused multiply-add into its running sum.
+template <bool FIRST>
 __device__ __forceinline__ void pair_grads(const SplatEval& e, float4 a, float4 b, float cb, float g0, float g1,
                                            float g2, float& T, float& S, float* v) {
     // 1 / (1 - alpha), 1 - alpha in [0.01, 1): the hardware reciprocal
@@ -338,18 +355,31 @@ __device__ __forceinline__ void pair_grads(const SplatEval& e, float4 a, float4 
     const float w = e.alpha * Tj;
     S = fmaf(cg, w, S);
     T = Tj;
-    v[6] = fmaf(w, g0, v[6]);
-    v[7] = fmaf(w, g1, v[7]);
-    v[8] = fmaf(w, g2, v[8]);
     const float dop = e.capped ? 0.0f : e.G * dal;
-    v[5] += dop;
     const float dsig = -b.y * dop;
     const float hd = 0.5f * dsig;
-    v[0] = fmaf(fmaf(a.z, e.dx, a.w * e.dy), dsig, v[0]);
-    v[1] = fmaf(fmaf(a.w, e.dx, b.x * e.dy), dsig, v[1]);
-    v[2] = fmaf(e.dxx, hd, v[2]);
-    v[3] = fmaf(e.dxy, dsig, v[3]);
-    v[4] = fmaf(e.dyy, hd, v[4]);
+    const float du = fmaf(a.z, e.dx, a.w * e.dy), dv = fmaf(a.w, e.dx, b.x * e.dy);
+    if (FIRST) {  // the first pixel slot writes the lane's sums
+        v[6] = w * g0;
+        v[7] = w * g1;
+        v[8] = w * g2;
+        v[5] = dop;
+        v[0] = du * dsig;
+        v[1] = dv * dsig;
+        v[2] = e.dxx * hd;
+        v[3] = e.dxy * dsig;
+        v[4] = e.dyy * hd;
+    } else {
+        v[6] = fmaf(w, g0, v[6]);
+        v[7] = fmaf(w, g1, v[7]);
+        v[8] = fmaf(w, g2, v[8]);
+        v[5] += dop;
+        v[0] = fmaf(du, dsig, v[0]);
+        v[1] = fmaf(dv, dsig, v[1]);
+        v[2] = fmaf(e.dxx, hd, v[2]);
+        v[3] = fmaf(e.dxy, dsig, v[3]);
+        v[4] = fmaf(e.dyy, hd, v[4]);
+    }
 }
 
 // Backward of one tile: the gradient-computation step (Sec. III-A) for the
@@ -445,15 +475,21 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                     const int pos = top - 1 - k;
                     const float4 a = sm.a[k], b = sm.b[k];
                     const float cb = sm.c[k];
+                    // every lane runs the gradient chain for every pixel slot; an
+                    // inactive pair enters it with alpha = G = 0, which leaves T and
+                    // S unchanged (1 / (1 - 0) is exactly 1 after the Newton step)
+                    // and adds only zeros
                     float v[9];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) v[i] = 0.0f;
                     bool any = false;
 #pragma unroll
                     for (int q = 0; q < PPT; ++q) {
                         SplatEval e;
-                        const bool act = (pos < last[q]) && eval_splat(a.x, a.y, a.z, a.w, b.x, b.y, fpx[q], fpy[q], e);
-                        if (act) pair_grads(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
+                        const bool act =
+                            eval_splat_all(a.x, a.y, a.z, a.w, b.x, b.y, fpx[q], fpy[q], e) && (pos < last[q]);
+                        e.alpha = act ? e.alpha : 0.0f;
+                        e.G = act ? e.G : 0.0f;
+                        if (q == 0) pair_grads<true>(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
+                        else pair_grads<false>(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
                         any |= act;
                     }
                     float* rec = grad + (size_t)sm.id[k] * GSR_REC;
