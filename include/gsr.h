@@ -115,7 +115,8 @@ typedef struct gsr_backward_opts {
 
 /* One view of a batched backward (an array of these lives in DEVICE memory).
  * All pointers are device pointers with the meaning and layout they have in
- * gsr_backward; final_T / n_contrib may be NULL when store_T is 0; 16x16
+ * gsr_backward; final_T / n_contrib may be NULL when store_T is 0, and so may
+ * block_mask (the view's forward block masks, see gsr_forward); 16x16
  * tiles. */
 typedef struct gsr_view {
     int32_t width, height;
@@ -126,6 +127,7 @@ typedef struct gsr_view {
     const int32_t* n_contrib;
     const float* dL_dimage;
     float* grad2d;
+    const uint8_t* block_mask;
     float bg[3];
     int32_t reserved;
 } gsr_view;
@@ -318,11 +320,19 @@ int gsr_tile_order(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h
  *   order) or a permutation of the tile ids from gsr_tile_order, the order
  *   in which CTAs take tiles; ids outside the grid are skipped, and an id
  *   that appears twice is rendered twice (the same values written again).
+ *   block_mask: NULL, or device uint8 with one byte per list entry (the
+ *   key capacity of the binning) that receives each entry's block mask:
+ *   bit b (b = 0..3) is clear only when no pixel of the 8x8 pixel block b
+ *   of the entry's tile (b = 2 (y >= 8) + (x >= 8), tile-local pixels) can
+ *   reach alpha >= 1/255 with this splat (a conservative test with margins
+ *   far above FP32 rounding; bits 4..7 are 0).  Written for every entry the
+ *   forward reads: every list position up to the end of the 256-entry batch
+ *   in which the tile's last pixel stops.  gsr_backward reads it back.
  */
 int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                 const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
                 const float* bg, float* image, float* final_T, int32_t* n_contrib,
-                const uint32_t* tile_order, gsr_stream_t stream);
+                uint8_t* block_mask, const uint32_t* tile_order, gsr_stream_t stream);
 
 /*
  * Forward blend fused with the L1 loss of Sec. II-B (the "loss" stage of the
@@ -340,7 +350,8 @@ int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
 int gsr_forward_l1(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                    const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
                    const float* bg, const float* target, float* image, float* final_T, int32_t* n_contrib,
-                   float* dL_dimage, float* loss_sum, const uint32_t* tile_order, gsr_stream_t stream);
+                   float* dL_dimage, float* loss_sum, uint8_t* block_mask, const uint32_t* tile_order,
+                   gsr_stream_t stream);
 
 /*
  * Backward blend + per-splat gradient accumulation: the gradient computation
@@ -361,12 +372,19 @@ int gsr_forward_l1(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h
  *   (gsr_tile_order), as for gsr_forward; it must not repeat an id (a
  *   repeated tile would be accumulated twice).  The cluster tier keeps
  *   row-major order (a cluster is a 2x2 block of neighbouring tiles).
+ *   block_mask: NULL, or the block masks that gsr_forward / gsr_forward_l1
+ *   wrote for these same lists and splats: each warp then skips the entries
+ *   whose bit for its pixel block is clear without recomputing the test.
+ *   Read by the configurations whose warps own those 8x8 blocks
+ *   (lane_layout 1, pixels_per_thread 2); the others compute the test
+ *   themselves.  Masks of other lists or splats give wrong gradients.
  */
 int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                  const uint32_t* tile_ranges, const uint32_t* point_list,
                  const float* splat2d, const float* bg, const float* final_T,
                  const int32_t* n_contrib, const float* dL_dimage, float* grad2d,
-                 const gsr_backward_opts* opts, const uint32_t* tile_order, gsr_stream_t stream);
+                 const gsr_backward_opts* opts, const uint8_t* block_mask, const uint32_t* tile_order,
+                 gsr_stream_t stream);
 
 /*
  * Work order of a batched backward: one item per (view, 16x16 tile), encoded
@@ -427,7 +445,8 @@ int gsr_entry_offsets(int32_t n, int32_t width, int32_t height, int32_t tile_w, 
  *   store_T, pixels_per_thread are used (reduce_mode and threshold are
  *   ignored: every active warp reduces).  The
  *   bits of the result depend on lane_layout and pixels_per_thread (they fix
- *   the summation order), not on scheduling.
+ *   the summation order), not on scheduling, nor on whether block_mask (as
+ *   for gsr_backward) is given.
  */
 int gsr_backward_deterministic(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                                const uint32_t* tile_ranges, const uint32_t* point_list,
@@ -435,7 +454,7 @@ int gsr_backward_deterministic(int32_t width, int32_t height, int32_t tile_w, in
                                const uint32_t* entry_offsets, const float* bg, const float* final_T,
                                const int32_t* n_contrib, const float* dL_dimage, float* partial,
                                int64_t partial_entries, float* grad2d, const gsr_backward_opts* opts,
-                               const uint32_t* tile_order, gsr_stream_t stream);
+                               const uint8_t* block_mask, const uint32_t* tile_order, gsr_stream_t stream);
 
 /*
  * Traversal statistics of gsr_backward (nothing else is written): walks the

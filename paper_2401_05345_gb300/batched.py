@@ -26,7 +26,7 @@ from .pipeline import SceneTensors, ViewBuffers
 class GsrView(ctypes.Structure):
     _fields_ = [("width", c_int32), ("height", c_int32), ("tile_ranges", c_void_p), ("point_list", c_void_p),
                 ("splat2d", c_void_p), ("final_T", c_void_p), ("n_contrib", c_void_p), ("dL_dimage", c_void_p),
-                ("grad2d", c_void_p), ("bg", c_float * 3), ("reserved", c_int32)]
+                ("grad2d", c_void_p), ("block_mask", c_void_p), ("bg", c_float * 3), ("reserved", c_int32)]
 
 
 def _setup_lib():
@@ -115,6 +115,9 @@ class BatchedViews:
             d.n_contrib = vb.n_contrib.data_ptr() if vb.n_contrib is not None else None
             d.dL_dimage = self.dimg[i].data_ptr()
             d.grad2d = vb.grad2d.data_ptr()
+            # the batched backward always follows render_all, whose forward
+            # writes each view's block masks
+            d.block_mask = vb.block_mask.data_ptr()
             for c in range(3):
                 d.bg[c] = self.bg[c]
         host = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)

@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(SH::NT)
 forward_kernel(RasterGeom g, const uint2* __restrict__ ranges, const uint32_t* __restrict__ point_list,
                const float* __restrict__ splat2d, float bg0, float bg1, float bg2, float* __restrict__ image,
                float* __restrict__ final_T, int* __restrict__ n_contrib, const uint32_t* __restrict__ order,
-               const float* __restrict__ target, float* __restrict__ dimg, float* __restrict__ loss_sum) {
+               const float* __restrict__ target, float* __restrict__ dimg, float* __restrict__ loss_sum,
+               uint8_t* __restrict__ block_mask) {
     constexpr int PPT = SH::B / SH::NT;
     __shared__ float4 s_a[SH::B];
     __shared__ float4 s_b[SH::B];
@@ -92,7 +93,7 @@ forward_kernel(RasterGeom g, const uint2* __restrict__ ranges, const uint32_t* _
         inside[q] = ox + lx < g.W && oy + ly < g.H;
     }
     walk_front<SH, true>(ranges[tile], point_list, splat2d, px, py, inside, ox, oy, s_a, s_b, s_c, s_mask, T, last,
-                         C);
+                         C, nullptr, block_mask);
     const size_t HW = (size_t)g.W * g.H;
     float labs = 0.0f;  // L1: sum of |out - target| over this thread's pixels
 #pragma unroll
@@ -204,7 +205,7 @@ stats_kernel(BwdArgs p, unsigned long long* __restrict__ hist) {
         const int cnt = min(B, top);
         __syncthreads();
         stage_batch<SH, false, false>(cnt, [&](int e) { return rg.x + (uint32_t)(top - 1 - e); }, p.point_list,
-                                      p.splat2d, ox, oy, s_a, s_b, nullptr, nullptr, s_mask);
+                                      p.splat2d, ox, oy, s_a, s_b, nullptr, nullptr, s_mask, nullptr, nullptr);
         __syncthreads();
         for (int k = 0; k < cnt; ++k) {
             const int pos = top - 1 - k;
@@ -362,7 +363,7 @@ extern "C" int gsr_tile_order(int32_t width, int32_t height, int32_t tile_w, int
 extern "C" int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                            const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
                            const float* bg, float* image, float* final_T, int32_t* n_contrib,
-                           const uint32_t* tile_order, gsr_stream_t stream) {
+                           uint8_t* block_mask, const uint32_t* tile_order, gsr_stream_t stream) {
     if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !bg || !image) return GSR_EINVAL;
     if (!aligned16(splat2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
     if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
@@ -370,15 +371,15 @@ extern "C" int gsr_forward(int32_t width, int32_t height, int32_t tile_w, int32_
     using SH = Shape<16, 16, 1, GSR_FORWARD_PPT>;
     forward_kernel<SH, false><<<g.gx * g.gy, SH::NT, 0, (cudaStream_t)stream>>>(
         g, reinterpret_cast<const uint2*>(tile_ranges), point_list, splat2d, bg[0], bg[1], bg[2], image, final_T,
-        n_contrib, tile_order, nullptr, nullptr, nullptr);
+        n_contrib, tile_order, nullptr, nullptr, nullptr, block_mask);
     return check_launch();
 }
 
 extern "C" int gsr_forward_l1(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                               const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
                               const float* bg, const float* target, float* image, float* final_T,
-                              int32_t* n_contrib, float* dL_dimage, float* loss_sum, const uint32_t* tile_order,
-                              gsr_stream_t stream) {
+                              int32_t* n_contrib, float* dL_dimage, float* loss_sum, uint8_t* block_mask,
+                              const uint32_t* tile_order, gsr_stream_t stream) {
     if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !bg || !target || !dL_dimage) return GSR_EINVAL;
     if (!aligned16(splat2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
     if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
@@ -386,7 +387,7 @@ extern "C" int gsr_forward_l1(int32_t width, int32_t height, int32_t tile_w, int
     using SH = Shape<16, 16, 1, GSR_FORWARD_PPT>;
     forward_kernel<SH, true><<<g.gx * g.gy, SH::NT, 0, (cudaStream_t)stream>>>(
         g, reinterpret_cast<const uint2*>(tile_ranges), point_list, splat2d, bg[0], bg[1], bg[2], image, final_T,
-        n_contrib, tile_order, target, dL_dimage, loss_sum);
+        n_contrib, tile_order, target, dL_dimage, loss_sum, block_mask);
     return check_launch();
 }
 
@@ -394,7 +395,7 @@ extern "C" int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32
                             const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
                             const float* bg, const float* final_T, const int32_t* n_contrib,
                             const float* dL_dimage, float* grad2d, const gsr_backward_opts* opts,
-                            const uint32_t* tile_order, gsr_stream_t stream_) {
+                            const uint8_t* block_mask, const uint32_t* tile_order, gsr_stream_t stream_) {
     gsr_backward_opts o = {GSR_REDUCE_WARP, 0, 0, 1, 1, {0, 0, 0}};
     if (opts) o = *opts;
     if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !bg || !dL_dimage || !grad2d) return GSR_EINVAL;
@@ -402,7 +403,7 @@ extern "C" int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32
     if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
     if (check_bwd_opts(o) != GSR_OK) return GSR_EINVAL;
     if (o.store_T && (!final_T || !n_contrib)) return GSR_EINVAL;
-    BwdArgs a;
+    BwdArgs a = {};
     a.g = RasterGeom{width, height, (width + 15) / 16, (height + 15) / 16};
     a.ranges = reinterpret_cast<const uint2*>(tile_ranges);
     a.point_list = point_list;
@@ -414,6 +415,7 @@ extern "C" int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32
     a.grad2d = grad2d;
     a.threshold = o.threshold;
     a.order = tile_order;
+    a.block_mask = block_mask;
     const int tiles = a.g.gx * a.g.gy;
     cudaStream_t s = (cudaStream_t)stream_;
     const bool st = o.store_T != 0;
@@ -458,7 +460,8 @@ extern "C" int gsr_backward_deterministic(int32_t width, int32_t height, int32_t
                                           const uint32_t* entry_offsets, const float* bg, const float* final_T,
                                           const int32_t* n_contrib, const float* dL_dimage, float* partial,
                                           int64_t partial_entries, float* grad2d, const gsr_backward_opts* opts,
-                                          const uint32_t* tile_order, gsr_stream_t stream_) {
+                                          const uint8_t* block_mask, const uint32_t* tile_order,
+                                          gsr_stream_t stream_) {
     gsr_backward_opts o = {GSR_REDUCE_WARP, 0, 1, 1, 2, {0, 0, 0}};
     if (opts) o = *opts;
     if (width <= 0 || height <= 0 || n < 0 || !tile_ranges || !splat2d || !bg || !dL_dimage || !grad2d)
@@ -485,6 +488,7 @@ extern "C" int gsr_backward_deterministic(int32_t width, int32_t height, int32_t
     a.entry_off = entry_offsets;
     a.partial = partial;
     a.order = tile_order;
+    a.block_mask = block_mask;
     a.n = n;
     a.partial_cap = partial_entries > 0xffffffffll ? 0xffffffffu : (uint32_t)partial_entries;
     const int tiles = a.g.gx * a.g.gy;

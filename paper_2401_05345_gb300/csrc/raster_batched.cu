@@ -38,6 +38,7 @@ backward_batched_kernel(const gsr_view* __restrict__ views, const uint32_t* __re
         p.grad2d = v.grad2d;
         p.threshold = threshold;
         p.order = nullptr;  // the item list is the order
+        p.block_mask = v.block_mask;
         backward_tile<SH, MODE, STORE_T>(p, (int)(code & 0xffffffu), sm);
     }
 }

@@ -78,18 +78,18 @@ __device__ __forceinline__ unsigned warp_cull_mask(float u, float v, float A, fl
     const float tx = t * C, ty = t * A;
     const float ex = tx * rsqrtf(tx) * 1.02f + 0.05f;
     const float ey = ty * rsqrtf(ty) * 1.02f + 0.05f;
+    const float fox = (float)ox, foy = (float)oy;  // pixel coordinates: integers, exact in FP32
     unsigned m = 0u;
-#pragma unroll 1
+#pragma unroll
     for (int w = 0; w < NW; ++w) {
-        int x0, y0;
-        SH::warp_origin(w, x0, y0);
-        x0 += ox;
-        y0 += oy;
-        bool hit = (u + ex >= (float)x0) && (u - ex <= (float)(x0 + SH::BX - 1)) &&
-                   (v + ey >= (float)y0) && (v - ey <= (float)(y0 + SH::BY - 1));
+        int bx, by;
+        SH::warp_origin(w, bx, by);
+        const float x0 = fox + (float)bx, x1 = fox + (float)(bx + SH::BX - 1);
+        const float y0 = foy + (float)by, y1 = foy + (float)(by + SH::BY - 1);
+        bool hit = (u + ex >= x0) && (u - ex <= x1) && (v + ey >= y0) && (v - ey <= y1);
         if (hit) {
-            const float dxa = (float)x0 - 0.05f - u, dxb = (float)(x0 + SH::BX - 1) + 0.05f - u;
-            const float dya = (float)y0 - 0.05f - v, dyb = (float)(y0 + SH::BY - 1) + 0.05f - v;
+            const float dxa = x0 - 0.05f - u, dxb = x1 + 0.05f - u;
+            const float dya = y0 - 0.05f - v, dyb = y1 + 0.05f - v;
             if (dxa > 0.0f || dxb < 0.0f || dya > 0.0f || dyb < 0.0f) {  // centre outside the block
                 float smin = 3.0e38f;
                 if (dxa > 0.0f || dxb < 0.0f) {
@@ -112,21 +112,41 @@ __device__ __forceinline__ unsigned warp_cull_mask(float u, float v, float A, fl
     return m;
 }
 
+// Whether a tile shape's warps own the 2 x 2 blocks of 8 x 8 pixels that the
+// per-entry block masks of gsr_forward / gsr_backward describe (bit w: block
+// w, row-major in the tile).
+template <class SH>
+struct HasBlockMask {
+    static constexpr bool value = SH::NW == 4 && SH::BX == 8 && SH::BY == 8 && SH::WX == 2;
+};
+
 // Stages batch entries [0, cnt) (list positions given by pos_of) into shared
-// memory; with PPT > 1 every thread stages several entries.
+// memory; with PPT > 1 every thread stages several entries.  The per-warp
+// cull mask of an entry is read from mask_in when given (shapes with 8 x 8
+// warp blocks), else computed, and then also written to mask_out when given.
 template <class SH, bool COLOR, bool IDS, class PosOf>
 __device__ __forceinline__ void stage_batch(int cnt, PosOf pos_of, const uint32_t* __restrict__ point_list,
                                             const float* __restrict__ splat2d, int ox, int oy, float4* s_a,
-                                            float4* s_b, float* s_c, uint32_t* s_id, unsigned* s_mask) {
+                                            float4* s_b, float* s_c, uint32_t* s_id, unsigned* s_mask,
+                                            const uint8_t* __restrict__ mask_in, uint8_t* __restrict__ mask_out) {
+    constexpr bool BM = HasBlockMask<SH>::value;
     for (int e = threadIdx.x; e < cnt; e += SH::NT) {
-        const uint32_t id = point_list[pos_of(e)];
+        const uint32_t pe = pos_of(e);
+        const uint32_t id = point_list[pe];
         const float4* rec = reinterpret_cast<const float4*>(splat2d + (size_t)id * GSR_REC);
         const float4 a = rec[0], b = rec[1];
         s_a[e] = a;
         s_b[e] = b;
         if (COLOR) s_c[e] = rec[2].x;
         if (IDS) s_id[e] = id;
-        s_mask[e] = warp_cull_mask<SH>(a.x, a.y, a.z, a.w, b.x, b.y, ox, oy);
+        unsigned mk;
+        if (BM && mask_in) {
+            mk = mask_in[pe];
+        } else {
+            mk = warp_cull_mask<SH>(a.x, a.y, a.z, a.w, b.x, b.y, ox, oy);
+            if (BM && mask_out) mask_out[pe] = (uint8_t)mk;
+        }
+        s_mask[e] = mk;
     }
 }
 
@@ -156,7 +176,8 @@ template <class SH, bool COLOR>
 __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict__ point_list,
                                            const float* __restrict__ splat2d, const float* px, const float* py,
                                            const bool* inside, int ox, int oy, float4* s_a, float4* s_b,
-                                           float* s_c, unsigned* s_mask, float* T, int* last, float (*C)[3]) {
+                                           float* s_c, unsigned* s_mask, float* T, int* last, float (*C)[3],
+                                           const uint8_t* mask_in, uint8_t* mask_out) {
     constexpr int PPT = SH::B / SH::NT;
     const int n = (int)(rg.y - rg.x);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -174,7 +195,7 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
         if (__syncthreads_count(all_done) == SH::NT) break;
         const int cnt = min(SH::B, n - base);
         stage_batch<SH, COLOR, false>(cnt, [&](int e) { return rg.x + (uint32_t)(base + e); }, point_list,
-                                      splat2d, ox, oy, s_a, s_b, s_c, nullptr, s_mask);
+                                      splat2d, ox, oy, s_a, s_b, s_c, nullptr, s_mask, mask_in, mask_out);
         __syncthreads();
         bool wdone = __all_sync(kFull, all_done);
         for (int c0 = 0; c0 < cnt && !wdone; c0 += 32) {
@@ -231,6 +252,7 @@ struct BwdArgs {
     float* partial;
     int n;                // Gaussians (entry_off has n + 1 values)
     uint32_t partial_cap; // entries partial holds
+    const uint8_t* block_mask;  // per-entry cull masks from the forward, or NULL
 };
 
 // Deterministic tier: per-warp partial sums are combined in warp order and
@@ -423,7 +445,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
     } else {
         float C[PPT][3];
         walk_front<SH, false>(rg, p.point_list, p.splat2d, fpx, fpy, inside, ox, oy, sm.a, sm.b, sm.c, sm.mask, Tf,
-                              last, C);
+                              last, C, p.block_mask, nullptr);
 #pragma unroll
         for (int q = 0; q < PPT; ++q)
             if (!inside[q]) { Tf[q] = 0.0f; last[q] = 0; }
@@ -454,7 +476,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
         const int cnt = min(B, top);
         __syncthreads();
         stage_batch<SH, true, true>(cnt, [&](int e) { return rg.x + (uint32_t)(top - 1 - e); }, p.point_list,
-                                    p.splat2d, ox, oy, sm.a, sm.b, sm.c, sm.id, sm.mask);
+                                    p.splat2d, ox, oy, sm.a, sm.b, sm.c, sm.id, sm.mask, p.block_mask, nullptr);
         if (MODE == kModeDet)
             for (int e = tid; e < cnt; e += NT) det.wflags[e] = 0u;  // entries this thread staged
         __syncthreads();

@@ -106,10 +106,10 @@ def lib():
                                       POINTER(c_int64), P]
     L.gsr_tile_order.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P]
     L.gsr_forward_l1.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P, P, P,
-                                 P, P]
-    L.gsr_forward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P, P]
+                                 P, P, P]
+    L.gsr_forward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P, P, P]
     L.gsr_backward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P,
-                               POINTER(BackwardOpts), P, P]
+                               POINTER(BackwardOpts), P, P, P]
     L.gsr_backward_stats.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, P, c_int32, P, P]
     L.gsr_backward_project.argtypes = [c_int32, c_int32, P, P, P, P, P, POINTER(Camera), P, P, P, P, P,
                                        P, P, P]
@@ -121,7 +121,8 @@ def lib():
     L.gsr_entry_offsets_scratch_bytes.argtypes = [c_int32, POINTER(c_size_t)]
     L.gsr_entry_offsets.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, P, c_size_t, P, P]
     L.gsr_backward_deterministic.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, P, c_int32, P,
-                                             POINTER(c_float), P, P, P, P, c_int64, P, POINTER(BackwardOpts), P, P]
+                                             POINTER(c_float), P, P, P, P, c_int64, P, POINTER(BackwardOpts), P, P,
+                                             P]
     L.gsr_scatter_add9.argtypes = [c_int64, P, P, P, c_int32, c_int32, c_int32, P]
     L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
     L.gsr_cube_forward.argtypes = [c_int32, c_int32, P, c_int32, P, P, P]
@@ -228,27 +229,30 @@ def gsr_tile_order(width, height, tile_w, tile_h, tile_ranges, order, stream=Non
 
 
 def gsr_forward(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, bg, image, final_T=None,
-                n_contrib=None, stream=None, tile_order=None):
+                n_contrib=None, stream=None, tile_order=None, block_mask=None):
     _check("gsr_forward", lib().gsr_forward(width, height, tile_w, tile_h, _ptr(tile_ranges),
                                             _ptr(point_list), _ptr(splat2d), _f3(bg), _ptr(image),
-                                            _ptr(final_T), _ptr(n_contrib), _ptr(tile_order), _stream(stream)))
+                                            _ptr(final_T), _ptr(n_contrib), _ptr(block_mask), _ptr(tile_order),
+                                            _stream(stream)))
 
 
 def gsr_forward_l1(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, bg, target, image, final_T,
-                   n_contrib, dL_dimage, loss_sum=None, stream=None, tile_order=None):
+                   n_contrib, dL_dimage, loss_sum=None, stream=None, tile_order=None, block_mask=None):
     _check("gsr_forward_l1", lib().gsr_forward_l1(width, height, tile_w, tile_h, _ptr(tile_ranges),
                                                   _ptr(point_list), _ptr(splat2d), _f3(bg), _ptr(target),
                                                   _ptr(image), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage),
-                                                  _ptr(loss_sum), _ptr(tile_order), _stream(stream)))
+                                                  _ptr(loss_sum), _ptr(block_mask), _ptr(tile_order),
+                                                  _stream(stream)))
 
 
 def gsr_backward(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, bg, final_T, n_contrib,
-                 dL_dimage, grad2d, opts=None, stream=None, tile_order=None):
+                 dL_dimage, grad2d, opts=None, stream=None, tile_order=None, block_mask=None):
     o = opts if opts is not None else backward_opts()
     _check("gsr_backward", lib().gsr_backward(width, height, tile_w, tile_h, _ptr(tile_ranges),
                                               _ptr(point_list), _ptr(splat2d), _f3(bg), _ptr(final_T),
                                               _ptr(n_contrib), _ptr(dL_dimage), _ptr(grad2d),
-                                              ctypes.byref(o), _ptr(tile_order), _stream(stream)))
+                                              ctypes.byref(o), _ptr(block_mask), _ptr(tile_order),
+                                              _stream(stream)))
 
 
 def gsr_entry_offsets_scratch_bytes(n) -> int:
@@ -265,13 +269,13 @@ def gsr_entry_offsets(n, width, height, tile_w, tile_h, splat2d, radius, scratch
 
 def gsr_backward_deterministic(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, radius, n,
                                entry_offsets, bg, final_T, n_contrib, dL_dimage, partial, grad2d, opts=None,
-                               stream=None, tile_order=None):
+                               stream=None, tile_order=None, block_mask=None):
     """partial: float tensor; its size / 9 is the entry capacity passed on."""
     o = opts if opts is not None else backward_opts("warp", 0, 1, True, 2)
     _check("gsr_backward_deterministic", lib().gsr_backward_deterministic(
         width, height, tile_w, tile_h, _ptr(tile_ranges), _ptr(point_list), _ptr(splat2d), _ptr(radius), n,
         _ptr(entry_offsets), _f3(bg), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage), _ptr(partial),
-        partial.numel() // 9, _ptr(grad2d), ctypes.byref(o), _ptr(tile_order), _stream(stream)))
+        partial.numel() // 9, _ptr(grad2d), ctypes.byref(o), _ptr(block_mask), _ptr(tile_order), _stream(stream)))
 
 
 def gsr_backward_stats(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, n_contrib, hist,

@@ -77,6 +77,10 @@ class ViewBuffers:
     def _alloc_keys(self, cap):
         self.key_capacity = int(cap)
         self.point_list = torch.zeros(max(self.key_capacity, 1), dtype=torch.int32, device=self.device)
+        # per-entry cull masks: written by the forward, read by the backward
+        # of the same lists (valid only between the two)
+        self.block_mask = torch.zeros(max(self.key_capacity, 1), dtype=torch.uint8, device=self.device)
+        self.mask_valid = False
         sb = gsr.gsr_bin_scratch_bytes(self.n, self.W, self.H, self.tw, self.th, self.key_capacity)
         self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
 
@@ -86,13 +90,14 @@ class ViewBuffers:
         self.scratch = None
 
     def device_bytes(self) -> int:
-        ts = [self.splat2d, self.radius, self.grad2d, self.tile_ranges, self.image, self.point_list]
+        ts = [self.splat2d, self.radius, self.grad2d, self.tile_ranges, self.image, self.point_list, self.block_mask]
         ts += [self.scratch] if self.scratch is not None else []
         ts += [t for t in (self.final_T, self.n_contrib) if t is not None]
         return sum(t.numel() * t.element_size() for t in ts)
 
     # -- stages ------------------------------------------------------------
     def preprocess(self, sc: SceneTensors, zero_grad=True, stream=None):
+        self.mask_valid = False
         gsr.gsr_preprocess(self.n, sc.sh_degree, sc.mean, sc.scale, sc.quat, sc.opacity, sc.feat,
                            self.c_cam, self.tw, self.th, self.splat2d, self.radius,
                            self.grad2d if zero_grad else None, stream)
@@ -128,7 +133,9 @@ class ViewBuffers:
         self.order_tiles(stream)
 
     def order_tiles(self, stream=None):
-        """Longest-first tile order of the current lists (gsr_tile_order)."""
+        """Longest-first tile order of the current lists (gsr_tile_order);
+        called after every binning, so it also marks the block masks stale."""
+        self.mask_valid = False
         gsr.gsr_tile_order(self.W, self.H, self.tw, self.th, self.tile_ranges, self.tile_order, stream)
 
     def check_bin(self) -> bool:
@@ -151,18 +158,25 @@ class ViewBuffers:
 
     def forward(self, bg, stream=None):
         gsr.gsr_forward(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
-                        bg, self.image, self.final_T, self.n_contrib, stream, tile_order=self.tile_order)
+                        bg, self.image, self.final_T, self.n_contrib, stream, tile_order=self.tile_order,
+                        block_mask=self.block_mask)
+        self.mask_valid = True
 
     def forward_l1(self, bg, target, dL_dimage, loss_sum=None, stream=None):
         """Forward with the L1 loss formed in its epilogue (gsr_forward_l1)."""
         gsr.gsr_forward_l1(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
                            bg, target, self.image, self.final_T, self.n_contrib, dL_dimage, loss_sum, stream,
-                           tile_order=self.tile_order)
+                           tile_order=self.tile_order, block_mask=self.block_mask)
+        self.mask_valid = True
+
+    def _mask(self):
+        """The forward's block masks when they belong to the current lists."""
+        return self.block_mask if self.mask_valid else None
 
     def backward(self, bg, dL_dimage, opts=None, stream=None):
         gsr.gsr_backward(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
                          bg, self.final_T, self.n_contrib, dL_dimage, self.grad2d, opts, stream,
-                         tile_order=self.tile_order)
+                         tile_order=self.tile_order, block_mask=self._mask())
 
     def backward_deterministic(self, bg, dL_dimage, opts=None, stream=None):
         """Backward without float atomics (bit-identical run to run); keeps
@@ -181,7 +195,7 @@ class ViewBuffers:
         gsr.gsr_backward_deterministic(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list,
                                        self.splat2d, self.radius, self.n, self._det_offsets, bg, self.final_T,
                                        self.n_contrib, dL_dimage, self._det_partial, self.grad2d, opts, stream,
-                                       tile_order=self.tile_order)
+                                       tile_order=self.tile_order, block_mask=self._mask())
 
     def backward_project(self, sc: SceneTensors, grads: SceneTensors, stream=None, accumulate=True):
         """3D gradients of this view: added to ``grads``, or (accumulate=False)

@@ -513,6 +513,83 @@ def test_tile_order_changes_no_result(dev, orc, name):
     np.testing.assert_array_equal(res[0], res[1])
 
 
+@pytest.mark.parametrize("name", ["tiny", "dense_sh1", "offaxis_sh2"])
+def test_forward_block_masks(dev, orc, name):
+    """Block masks written by the forward: every entry the forward reads
+    (at least every list position up to the tile's furthest last
+    contributor) gets a mask with bits 4..7 clear, and a clear bit is a
+    correct cull: in FP64 on the oracle's records, no pixel of that 8x8
+    block reaches alpha >= 1/255.  Backward results with the masks: the
+    deterministic tier gives the same bits as without them (stored and
+    recomputed transmittance), the hybrid tier matches the oracle."""
+    st_ = oracle_stage(orc, name, (0.3, 0.7, 0.1))
+    cam = st_["cam"]
+    W, H = cam.width, cam.height
+    gx, gy = (W + 15) // 16, (H + 15) // 16
+    f = gpu_forward(dev, st_)
+    nk = len(st_["pl"])
+    mask = torch.full((nk + 1,), 0xAA, dtype=torch.uint8, device=dev)  # 0xAA: bits 5 and 7 mark "not written"
+    image = torch.zeros_like(f["image"])
+    fT = torch.zeros_like(f["final_T"])
+    nc = torch.zeros_like(f["n_contrib"])
+    gsr.gsr_forward(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], st_["bg"], image, fT, nc, block_mask=mask)
+    for a, c in ((image, f["image"]), (fT, f["final_T"]), (nc, f["n_contrib"])):
+        assert torch.equal(a, c)  # writing the masks changes no output
+    m = N(mask)[:nk].astype(np.int64)
+    ncn = N(f["n_contrib"])
+    rec = st_["rec"].astype(np.float64)
+    pl = st_["pl"].astype(np.int64)
+    rg = st_["ranges"].astype(np.int64).reshape(-1, 2)
+    culled = 0
+    for t in range(gx * gy):
+        s0, s1 = rg[t]
+        if s1 == s0:
+            continue
+        tx, ty = t % gx, t // gx
+        reach = int(ncn[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16].max())
+        written = m[s0:s1] & 0xF0 == 0
+        assert written[:reach].all(), f"tile {t}: an entry before the last contributor has no mask"
+        for b in range(4):
+            x0, y0 = tx * 16 + 8 * (b & 1), ty * 16 + 8 * (b >> 1)
+            xs = np.arange(x0, min(x0 + 8, W), dtype=np.float64)
+            ys = np.arange(y0, min(y0 + 8, H), dtype=np.float64)
+            if len(xs) == 0 or len(ys) == 0:
+                continue
+            sel = np.nonzero(written & ((m[s0:s1] >> b) & 1 == 0))[0]
+            if len(sel) == 0:
+                continue
+            r = rec[pl[s0 + sel]]
+            dx = r[:, 0, None, None] - xs[None, None, :]
+            dy = r[:, 1, None, None] - ys[None, :, None]
+            sig = 0.5 * (r[:, 2, None, None] * dx * dx + r[:, 4, None, None] * dy * dy) + r[:, 3, None, None] * dx * dy
+            alpha = np.minimum(0.99, r[:, 5, None, None] * np.exp(-sig))
+            passes = (sig >= 0) & (alpha >= 1.0 / 255.0)
+            assert not passes.any(), f"tile {t} block {b}: a culled entry reaches alpha >= 1/255"
+            culled += len(sel)
+    assert culled > 0
+    n = len(st_["rec"])
+    out = st_["out"]
+    grad = torch.zeros((n, 12), device=dev)
+    gsr.gsr_backward(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], st_["bg"], f["final_T"], f["n_contrib"],
+                     T(st_["g"]), grad, gsr.backward_opts("hybrid", 12, 1, True, 2), block_mask=mask)
+    check_scaled(f"{name} backward with block masks", N(grad)[:, :9], out["grad2d"], out["gscale"], out["gallow"])
+    radius = T(st_["radius"])
+    off = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+    scr = torch.empty(gsr.gsr_entry_offsets_scratch_bytes(n), dtype=torch.uint8, device=dev)
+    gsr.gsr_entry_offsets(n, W, H, 16, 16, f["splat"], radius, scr, off)
+    partial = torch.empty(9 * int(off[n]) + 9, device=dev)
+    for store_T in (True, False):
+        opts = gsr.backward_opts("warp", 0, 1, store_T, 2)
+        res = []
+        for bm in (None, mask):
+            grad = torch.zeros((n, 12), device=dev)
+            gsr.gsr_backward_deterministic(W, H, 16, 16, f["ranges"], f["pl"], f["splat"], radius, n, off, st_["bg"],
+                                           f["final_T"], f["n_contrib"], T(st_["g"]), partial, grad, opts,
+                                           block_mask=bm)
+            res.append(N(grad))
+        np.testing.assert_array_equal(res[0], res[1])
+
+
 def test_tile_ids_outside_the_grid_are_skipped(dev, orc):
     """An order whose entries are all past the last tile renders nothing:
     the outputs keep their values (no access outside the grid)."""
