@@ -247,6 +247,14 @@ radix_scatter_kernel(int n, const uint32_t* __restrict__ kin, const uint32_t* __
         key[i] = idx < n ? kin[idx] : 0xffffffffu;
         val[i] = idx < n ? vin[idx] : 0u;
     }
+    // digit totals and this tile's column prefixes of the digits d = tid*DPT + j:
+    // independent of the ranking, so their loads are issued before it
+    uint32_t hv[DPT], cp[DPT];
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+        hv[j] = tot[tid * DPT + j];
+        cp[j] = colpre[(size_t)tile * NB + tid * DPT + j];
+    }
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
@@ -262,18 +270,15 @@ radix_scatter_kernel(int n, const uint32_t* __restrict__ kin, const uint32_t* __
     }
     __syncthreads();
     // digits d = tid*DPT + j: global base and the warps' exclusive offsets
-    uint32_t hv[DPT], hs = 0;
+    uint32_t hs = 0;
 #pragma unroll
-    for (int j = 0; j < DPT; ++j) {
-        hv[j] = tot[tid * DPT + j];
-        hs += hv[j];
-    }
+    for (int j = 0; j < DPT; ++j) hs += hv[j];
     uint32_t all = 0;
     uint32_t run = block_excl_scan(hs, s_wsum, &all);
 #pragma unroll
     for (int j = 0; j < DPT; ++j) {
         const int d = tid * DPT + j;
-        s_base[d] = run + colpre[(size_t)tile * NB + d];
+        s_base[d] = run + cp[j];
         run += hv[j];
         uint32_t wr = 0;
 #pragma unroll
@@ -547,10 +552,11 @@ __global__ void __launch_bounds__(kPlaceThreads)
 chunk_hist_kernel(int n, int nb, Geom g, int t0, int tw, const uint2* __restrict__ rects,
                   const uint32_t* __restrict__ apre, const uint32_t* __restrict__ boff,
                   const uint32_t* __restrict__ wstart, const uint32_t* __restrict__ info, uint32_t* __restrict__ m) {
-    extern __shared__ uint32_t h[];
+    extern __shared__ uint32_t h[];  // [(tw + 1) / 2] packed 16-bit counts (a block holds < 65536 entries)
     __shared__ WarpBatch s_wb[kPlaceWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < tw; t += kPlaceThreads) h[t] = 0;
+    const int tw2 = (tw + 1) / 2;
+    for (int q = threadIdx.x; q < tw2; q += kPlaceThreads) h[q] = 0;
     __syncthreads();
     const int b = blockIdx.x;
     const uint32_t total = info[4];
@@ -564,14 +570,14 @@ chunk_hist_kernel(int n, int nb, Geom g, int t0, int tw, const uint2* __restrict
         walk_rows<false>(s_wb[w], lane, n, e0, e1, k, rects, nullptr, nullptr, entry_prefix(apre, boff, k), g, t0,
                          [&](bool ok, const RowWork& r) {
                              if (!ok) return;
-                             for (int x = r.xs; x < r.xe; ++x) {
-                                 const int t = r.row_t0 + x;
-                                 if ((unsigned)t < (unsigned)tw) atomicAdd(&h[t], 1u);
-                             }
+                             const int lo = max(r.row_t0 + r.xs, 0), hi = min(r.row_t0 + r.xe, tw);
+                             for (int q = lo >> 1; 2 * q < hi; ++q)
+                                 atomicAdd(&h[q], (2 * q >= lo ? 1u : 0u) + (2 * q + 1 < hi ? 0x10000u : 0u));
                          });
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < tw; t += kPlaceThreads) m[(size_t)b * g.tiles + t0 + t] = h[t];
+    for (int t = threadIdx.x; t < tw; t += kPlaceThreads)
+        m[(size_t)b * g.tiles + t0 + t] = (h[t >> 1] >> (16 * (t & 1))) & 0xffffu;
 }
 
 // Writes the entries of the tiles in the window: block b's entries of tile
