@@ -127,10 +127,22 @@ colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restric
     const int c = blockIdx.x * 32 + cx;
     const int per = (rows + 31) / 32;
     const int r0 = seg * per, r1 = min(rows, r0 + per);
+    constexpr int kHeld = 16;  // segments up to this long are read once and kept in registers
+    const bool held = per <= kHeld;
+    uint32_t v[kHeld];
     uint32_t sum = 0;
-    if (c < cols)
+    if (c < cols) {
+        if (held) {
+#pragma unroll
+            for (int q = 0; q < kHeld; ++q) {
+                v[q] = r0 + q < r1 ? m[(size_t)(r0 + q) * cols + c] : 0u;
+                sum += v[q];
+            }
+        } else {
 #pragma unroll 4
-        for (int r = r0; r < r1; ++r) sum += m[(size_t)r * cols + c];
+            for (int r = r0; r < r1; ++r) sum += m[(size_t)r * cols + c];
+        }
+    }
     s_seg[seg][cx] = sum;
     __syncthreads();
     {   // exclusive scan over the segments: warp `seg` takes column `seg`, lane `cx` its segment `cx`
@@ -148,12 +160,20 @@ colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restric
     __syncthreads();
     if (c < cols) {
         uint32_t run = s_seg[seg][cx];
+        if (held) {
+#pragma unroll
+            for (int q = 0; q < kHeld; ++q) {
+                if (r0 + q < r1) m[(size_t)(r0 + q) * cols + c] = run;
+                run += v[q];
+            }
+        } else {
 #pragma unroll 4
-        for (int r = r0; r < r1; ++r) {
-            const size_t o = (size_t)r * cols + c;
-            const uint32_t x = m[o];
-            m[o] = run;
-            run += x;
+            for (int r = r0; r < r1; ++r) {
+                const size_t o = (size_t)r * cols + c;
+                const uint32_t x = m[o];
+                m[o] = run;
+                run += x;
+            }
         }
     }
     if (!ranges) return;
