@@ -28,6 +28,7 @@ class RasterSettings:
     opts: object = None           # gsr.BackwardOpts; default WARP
     store_T: bool = True
     key_capacity: int | None = None
+    deterministic: bool = False   # atomic-free backward: bit-identical gradients run to run
 
 
 class _Rasterize(torch.autograd.Function):
@@ -54,7 +55,10 @@ class _Rasterize(torch.autograd.Function):
         if bool(opts.store_T) != bool(st.store_T):
             opts = gsr.backward_opts(int(opts.reduce_mode), int(opts.threshold), int(opts.lane_layout),
                                      st.store_T, int(opts.pixels_per_thread))
-        vb.backward(st.bg, dL_dimage.contiguous(), opts)
+        if st.deterministic:
+            vb.backward_deterministic(st.bg, dL_dimage.contiguous(), opts)
+        else:
+            vb.backward(st.bg, dL_dimage.contiguous(), opts)
         sc = SceneTensors(mean, scale, quat, opacity, feat, ctx.sh_degree)
         g = sc.zeros_like_params()
         vb.backward_project(sc, g)

@@ -40,28 +40,48 @@ __device__ __forceinline__ void tile_rect(float u, float v, int r, int gx, int g
 // Evaluation of one splat at one pixel with a fixed sequence of IEEE
 // operations, so that the forward and the backward kernels take bit-identical
 // skip decisions:  sigma = (A dx^2 + C dy^2)/2 + B dx dy, G = exp(-sigma),
-// alpha = min(0.99, o G).  Returns false when the splat is skipped
-// (sigma < 0 or alpha < 1/255).
+// alpha = min(0.99, o G).  A pair is skipped when sigma < 0 or
+// alpha < 1/255.
 struct SplatEval {
     float dx, dy, dxx, dyy, dxy, sigma, G, alpha;
     bool capped;
 };
 
-__device__ __forceinline__ bool eval_splat(float u, float v, float A, float B, float C, float o,
-                                           float px, float py, SplatEval& e) {
+__device__ __forceinline__ void splat_sigma(float u, float v, float A, float B, float C, float px, float py,
+                                            SplatEval& e) {
     e.dx = __fsub_rn(u, px);
     e.dy = __fsub_rn(v, py);
     e.dxx = __fmul_rn(e.dx, e.dx);
     e.dyy = __fmul_rn(e.dy, e.dy);
     e.dxy = __fmul_rn(e.dx, e.dy);
-    float q = __fmaf_rn(C, e.dyy, __fmul_rn(A, e.dxx));
+    const float q = __fmaf_rn(C, e.dyy, __fmul_rn(A, e.dxx));
     e.sigma = __fmaf_rn(0.5f, q, __fmul_rn(B, e.dxy));
-    if (e.sigma < 0.0f) return false;
+}
+
+__device__ __forceinline__ void splat_alpha(float o, SplatEval& e) {
     e.G = __expf(-e.sigma);
-    float oG = __fmul_rn(o, e.G);
+    const float oG = __fmul_rn(o, e.G);
     e.capped = oG > kAlphaMax;
     e.alpha = e.capped ? kAlphaMax : oG;
+}
+
+// Returns false when the pair is skipped (G and alpha are then unset when
+// sigma < 0).
+__device__ __forceinline__ bool eval_splat(float u, float v, float A, float B, float C, float o,
+                                           float px, float py, SplatEval& e) {
+    splat_sigma(u, v, A, B, C, px, py, e);
+    if (e.sigma < 0.0f) return false;
+    splat_alpha(o, e);
     return e.alpha >= kAlphaMin;
+}
+
+// eval_splat without the early return: every field is set, and the result
+// is eval_splat's.
+__device__ __forceinline__ bool eval_splat_all(float u, float v, float A, float B, float C, float o, float px,
+                                               float py, SplatEval& e) {
+    splat_sigma(u, v, A, B, C, px, py, e);
+    splat_alpha(o, e);
+    return e.sigma >= 0.0f && e.alpha >= kAlphaMin;
 }
 
 // pair step of the transposing reduce-scatter: lanes with bit b set keep y

@@ -150,24 +150,6 @@ __device__ __forceinline__ void stage_batch(int cnt, PosOf pos_of, const uint32_
     }
 }
 
-// eval_splat without the early return: every field is set (G and alpha from
-// the same operations), and the result is eval_splat's.
-__device__ __forceinline__ bool eval_splat_all(float u, float v, float A, float B, float C, float o, float px,
-                                               float py, SplatEval& e) {
-    e.dx = __fsub_rn(u, px);
-    e.dy = __fsub_rn(v, py);
-    e.dxx = __fmul_rn(e.dx, e.dx);
-    e.dyy = __fmul_rn(e.dy, e.dy);
-    e.dxy = __fmul_rn(e.dx, e.dy);
-    const float q = __fmaf_rn(C, e.dyy, __fmul_rn(A, e.dxx));
-    e.sigma = __fmaf_rn(0.5f, q, __fmul_rn(B, e.dxy));
-    e.G = __expf(-e.sigma);
-    const float oG = __fmul_rn(o, e.G);
-    e.capped = oG > kAlphaMax;
-    e.alpha = e.capped ? kAlphaMax : oG;
-    return e.sigma >= 0.0f && e.alpha >= kAlphaMin;
-}
-
 // Front-to-back walk of each of the thread's pixels over the tile list (the
 // forward rule; shared by the forward kernel and the recompute mode of the
 // backward, so both produce the same final transmittance and last

@@ -54,9 +54,9 @@ def weights(H, W, seed=3):
     return np.random.default_rng(seed).normal(size=(3, H, W)).astype(np.float32)
 
 
-def run_model(dev, scene, cam, w, store_T, opts=None):
+def run_model(dev, scene, cam, w, store_T, opts=None, deterministic=False):
     model = AG.GaussianModel(scene, dev)
-    st = AG.RasterSettings(cam, (0.1, 0.2, 0.3), opts, store_T)
+    st = AG.RasterSettings(cam, (0.1, 0.2, 0.3), opts, store_T, deterministic=deterministic)
     img = model(st)
     loss = (img * torch.from_numpy(w).to(dev)).sum()
     loss.backward()
@@ -195,23 +195,35 @@ def test_autograd_central_differences(dev, orc):
 
 
 def test_large_scene_through_autograd(dev):
+    """3M Gaussians at 1080p through the autograd Function.  With the
+    atomic-free backward every stage is bitwise repeatable, and recomputing T
+    in the backward reproduces the forward's T bit for bit, so stored and
+    recomputed T give the same gradient bits.  The atomic HYBRID tier on the
+    same scene gives finite gradients within float summation-order noise of
+    those (its exact sums are checked against the oracle at small sizes)."""
     scene, cam = S.large_workload(0)
     w = np.where(np.random.default_rng(1).uniform(size=(3, cam.height, cam.width)) < 0.5, -1.0, 1.0).astype(np.float32)
     res = {}
     for key, store_T in (("store", True), ("store_again", True), ("recompute", False)):
         torch.cuda.synchronize()
-        img, g = run_model(dev, scene, cam, w, store_T, gsr.backward_opts("hybrid", 12, 1, store_T))
+        img, g = run_model(dev, scene, cam, w, store_T, gsr.backward_opts("warp", 0, 1, store_T, 2),
+                           deterministic=True)
         res[key] = (img, g)
     np.testing.assert_array_equal(res["store"][0], res["recompute"][0])
     np.testing.assert_array_equal(res["store"][0], res["store_again"][0])
     for k in res["store"][1]:
-        a, a2, b = res["store"][1][k], res["store_again"][1][k], res["recompute"][1][k]
-        assert np.isfinite(a).all() and np.isfinite(b).all()
-        # recomputing T changes the gradients no more than re-running with T
-        # stored does (float summation order of the accumulation)
-        noise = np.linalg.norm(a - a2)
-        assert np.linalg.norm(a - b) <= 3 * noise + 1e-6 * np.linalg.norm(a), (k, np.linalg.norm(a - b), noise)
+        a = res["store"][1][k]
+        assert np.isfinite(a).all()
+        np.testing.assert_array_equal(a, res["store_again"][1][k])
+        np.testing.assert_array_equal(a, res["recompute"][1][k])
     assert np.abs(res["store"][1]["mean"]).max() > 0
+    img, ga = run_model(dev, scene, cam, w, True, gsr.backward_opts("hybrid", 12, 1, True))
+    np.testing.assert_array_equal(img, res["store"][0])
+    for k, ref in res["store"][1].items():
+        a = ga[k]
+        assert np.isfinite(a).all()
+        # two atomic runs differ by about 5e-5 of the norm (summation order)
+        assert np.linalg.norm(a - ref) <= 1e-3 * np.linalg.norm(ref), (k, np.linalg.norm(a - ref))
 
 
 def test_recompute_keeps_less_state(dev):
