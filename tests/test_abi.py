@@ -56,28 +56,36 @@ def test_argument_errors_are_reported_before_any_launch(lib):
     opts = gsr.backward_opts("warp")
     opts.reduce_mode = 7
     p = ctypes.c_void_p(16)
-    assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, p, p, p, p, ctypes.byref(opts), None, None, None) == gsr.GSR_EINVAL
+
+    def bwd(*head, opts_ref=None, final=(p, p)):
+        """gsr_backward with the given leading arguments, NULL tile order,
+        block mask and stream."""
+        return lib.gsr_backward(*head, *final, p, p, opts_ref, None, None, None)
+
+    assert bwd(32, 32, 16, 16, p, p, p, bg, opts_ref=ctypes.byref(opts)) == gsr.GSR_EINVAL
     opts = gsr.backward_opts("hybrid", threshold=40)
-    assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, p, p, p, p, ctypes.byref(opts), None, None, None) == gsr.GSR_EINVAL
+    assert bwd(32, 32, 16, 16, p, p, p, bg, opts_ref=ctypes.byref(opts)) == gsr.GSR_EINVAL
     opts = gsr.backward_opts("plain", pixels_per_thread=2)   # the plain baseline keeps one pixel per thread
-    assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, p, p, p, p, ctypes.byref(opts), None, None, None) == gsr.GSR_EINVAL
+    assert bwd(32, 32, 16, 16, p, p, p, bg, opts_ref=ctypes.byref(opts)) == gsr.GSR_EINVAL
     opts = gsr.backward_opts("warp", pixels_per_thread=3)
-    assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, p, p, p, p, ctypes.byref(opts), None, None, None) == gsr.GSR_EINVAL
+    assert bwd(32, 32, 16, 16, p, p, p, bg, opts_ref=ctypes.byref(opts)) == gsr.GSR_EINVAL
     opts = gsr.backward_opts("warp", store_T=True)
-    assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, None, None, p, p, ctypes.byref(opts), None, None, None) == gsr.GSR_EINVAL
-    assert lib.gsr_backward(32, 32, 12, 16, p, p, p, bg, p, p, p, p, None, None, None, None) == gsr.GSR_EINVAL
+    assert bwd(32, 32, 16, 16, p, p, p, bg, opts_ref=ctypes.byref(opts), final=(None, None)) == gsr.GSR_EINVAL
+    assert bwd(32, 32, 12, 16, p, p, p, bg) == gsr.GSR_EINVAL
     # records must be 16-byte aligned, ranges 8-byte aligned
     p8 = ctypes.c_void_p(24)
-    assert lib.gsr_backward(32, 32, 16, 16, p, p, p8, bg, p, p, p, p, None, None, None, None) == gsr.GSR_EINVAL
-    assert lib.gsr_backward(32, 32, 16, 16, ctypes.c_void_p(20), p, p, bg, p, p, p, p, None, None, None, None) == gsr.GSR_EINVAL
+    assert bwd(32, 32, 16, 16, p, p, p8, bg) == gsr.GSR_EINVAL
+    assert bwd(32, 32, 16, 16, ctypes.c_void_p(20), p, p, bg) == gsr.GSR_EINVAL
     assert lib.gsr_forward(32, 32, 16, 16, p, p, p8, bg, p, None, None, None, None, None) == gsr.GSR_EINVAL
     # tile order: empty image, unsupported tile, missing output
     assert lib.gsr_tile_order(0, 16, 16, 16, p, p, None) == gsr.GSR_EINVAL
     assert lib.gsr_tile_order(32, 32, 8, 16, p, p, None) == gsr.GSR_EINVAL
     assert lib.gsr_tile_order(32, 32, 16, 16, p, None, None) == gsr.GSR_EINVAL
     # forward + L1: the target and the loss gradient are required
-    assert lib.gsr_forward_l1(32, 32, 16, 16, p, p, p, bg, None, p, None, None, p, None, None, None, None) == gsr.GSR_EINVAL
-    assert lib.gsr_forward_l1(32, 32, 16, 16, p, p, p, bg, p, p, None, None, None, None, None, None, None) == gsr.GSR_EINVAL
+    assert lib.gsr_forward_l1(32, 32, 16, 16, p, p, p, bg, None, p, None, None, p,
+                              None, None, None, None) == gsr.GSR_EINVAL
+    assert lib.gsr_forward_l1(32, 32, 16, 16, p, p, p, bg, p, p, None, None, None,
+                              None, None, None, None) == gsr.GSR_EINVAL
     cam = gsr.Camera()
     assert lib.gsr_preprocess(10, 4, p, p, p, p, p, ctypes.byref(cam), 16, 16, p, p, None, None) == gsr.GSR_EINVAL
     out = ctypes.c_size_t(0)
