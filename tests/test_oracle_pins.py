@@ -112,6 +112,51 @@ def test_rotated_anisotropic_conic_on_axis(orc):
     np.testing.assert_allclose(pp["conic"][0], [inv[0, 0], inv[0, 1], inv[1, 1]], rtol=1e-10)
 
 
+def _rotated_sigma2(cam, sx, sy, th):
+    """Closed-form screen covariance of a Gaussian on the optical axis rotated
+    by th about it (scales sx, sy across the axis): k^2 R diag(sx^2, sy^2) R^T
+    + 0.3 I with k = f / z."""
+    k = cam.fx / 4.0
+    c, s_ = math.cos(th), math.sin(th)
+    sx, sy = float(np.float32(sx)), float(np.float32(sy))
+    S2 = k * k * np.array([[sx**2 * c * c + sy**2 * s_ * s_, (sx**2 - sy**2) * c * s_],
+                           [(sx**2 - sy**2) * c * s_, sx**2 * s_ * s_ + sy**2 * c * c]])
+    return S2 + float(np.float32(0.3)) * np.eye(2)
+
+
+def test_radius_is_three_sigma_of_the_larger_eigenvalue(orc):
+    """Strongly anisotropic splat (eigenvalue gap far above the 0.1 floor):
+    radius = ceil(3 sqrt(lambda_max)) with lambda_max from a library
+    eigensolver of the closed-form screen covariance; the smaller eigenvalue
+    would give 4 instead of 14."""
+    cam = _cam(257, 257)
+    th, sx, sy = 0.7, 0.08, 0.02
+    q = [math.cos(th / 2), 0, 0, math.sin(th / 2)]
+    pp = orc.preprocess(_scene([[0, 0, 0]], [[sx, sy, 0.05]], [q], [0.5], [[0.2, 0.4, 0.6]]), cam)
+    ev = np.linalg.eigvalsh(_rotated_sigma2(cam, sx, sy, th))
+    assert ((ev[1] - ev[0]) / 2) ** 2 > 10.0
+    assert pp["pp_ambig"][0] == 0
+    assert pp["radius"][0] == math.ceil(3 * math.sqrt(ev[1])) == 14
+    assert math.ceil(3 * math.sqrt(ev[0])) != 14
+
+
+def test_radius_floor_of_the_eigenvalue_gap(orc):
+    """Nearly isotropic splat whose squared half eigenvalue gap (0.022) lies
+    below the 0.1 floor: the extent uses mean eigenvalue + sqrt(0.1), which
+    here rounds up to 4 where the larger eigenvalue itself gives 3."""
+    cam = _cam(97, 97)
+    th, sx, sy = 0.4, 0.0375, 0.027
+    q = [math.cos(th / 2), 0, 0, math.sin(th / 2)]
+    pp = orc.preprocess(_scene([[0, 0, 0]], [[sx, sy, 0.05]], [q], [0.5], [[0.2, 0.4, 0.6]]), cam)
+    ev = np.linalg.eigvalsh(_rotated_sigma2(cam, sx, sy, th))
+    gap2 = ((ev[1] - ev[0]) / 2) ** 2
+    assert 0.0 < gap2 < 0.1
+    assert pp["pp_ambig"][0] == 0
+    floor = float(np.float32(0.1))
+    assert pp["radius"][0] == math.ceil(3 * math.sqrt(ev.mean() + math.sqrt(floor))) == 4
+    assert math.ceil(3 * math.sqrt(ev[1])) == 3
+
+
 def test_identity_quaternion_covariance_is_diag_scale(orc):
     """Identity rotation: Sigma3 = diag(s^2); on the axis Sigma2 = diag((f/z)^2 sx^2, (f/z)^2 sy^2) + 0.3."""
     cam = _cam(33, 33)
@@ -295,6 +340,102 @@ def test_ambiguous_alpha_floor_gets_allowance(orc):
     assert out["pix_ambig"][8, 8] >= 1
     np.testing.assert_allclose(out["iallow"][:, 8, 8], o * np.array([1.0, 0.5, 0.25]), rtol=1e-12)
     assert out["gallow"][0, 6] > 0
+
+
+def _center_pixel_grad(W, H):
+    g = np.zeros((3, H, W), np.float32)
+    g[:, 8, 8] = 1.0  # upstream gradient at the one pixel where a decision is ambiguous
+    return g
+
+
+def test_ambiguous_sigma_sign_gets_allowance(orc):
+    """A splat centred 2^-20 px from a pixel centre: sigma ~ 2e-13 is within
+    the FP32 rounding of the offset's products, so FP32 may find it negative
+    and skip the splat there.  The allowance is that pixel's whole
+    contribution (alpha c over a black background) and the splat's whole
+    single-splat gradient there: dL/dc = alpha g, dL/do = G c.g."""
+    W = H = 16
+    u, o, c = 8.0 + 2.0 ** -20, 0.6, np.array([1.0, 0.5, 0.25])
+    out = _render_2d(orc, W, H, [[u, 8.0]], [[0.5, 0, 0.5]], [o], [c], [0, 0, 0], _center_pixel_grad(W, H))
+    assert out["pix_ambig"][8, 8] == 1 and out["pix_ambig"].sum() == 1
+    G = math.exp(-0.25 * (u - 8.0) ** 2)
+    np.testing.assert_allclose(out["iallow"][:, 8, 8], o * G * c, rtol=1e-12)
+    np.testing.assert_allclose(out["gallow"][0, 6:9], [o * G] * 3, rtol=1e-12)
+    np.testing.assert_allclose(out["gallow"][0, 5], G * c.sum(), rtol=1e-12)
+    np.testing.assert_allclose(out["gallow"][0], np.abs(out["grad2d"][0]), rtol=1e-12)
+
+
+def test_ambiguous_alpha_cap_gets_allowance(orc):
+    """o G = 0.99 (1 + 1e-7) at the splat's centre: FP32 may leave alpha
+    uncapped.  Capped, dL/do is 0; uncapped, dL/do = G dL/dalpha = c.g (single
+    splat, black background, G = 1); the image differs by (o - 0.99) c."""
+    W = H = 16
+    cap = float(np.float32(0.99))
+    o, c = cap * (1 + 1e-7), np.array([1.0, 0.5, 0.25])
+    out = _render_2d(orc, W, H, [[8.0, 8.0]], [[0.5, 0, 0.5]], [o], [c], [0, 0, 0], _center_pixel_grad(W, H))
+    assert out["pix_ambig"][8, 8] == 1 and out["pix_ambig"].sum() == 1
+    assert out["grad2d"][0, 5] == 0.0  # capped: no opacity gradient
+    np.testing.assert_allclose(out["iallow"][:, 8, 8], (o - cap) * c, rtol=1e-9)
+    np.testing.assert_allclose(out["gallow"][0, 5], c.sum(), rtol=1e-12)
+    np.testing.assert_allclose(out["gallow"][0, 6:9], [o - cap] * 3, rtol=1e-9)
+    assert np.all(out["gallow"][0, 0:5] == 0.0)  # at the centre the conic and position terms vanish
+
+
+def test_ambiguous_transmittance_stop_gets_allowance(orc):
+    """Three stacked splats at a pixel centre with the third leaving
+    T = 1e-4 (1 + 1e-8): FP32 may stop before it.  Then n_contrib is 2, the
+    image differs by alpha_3 T_3 (c_3 - bg), the third splat loses its whole
+    gradient and the two in front change dL/dalpha by
+    alpha_3 T_3 (c_3 - bg).g / (1 - alpha_j)."""
+    W = H = 16
+    tmin = float(np.float32(1e-4))
+    o01 = 0.95
+    T3 = (1 - o01) * (1 - o01)
+    o3 = 1 - tmin * (1 + 1e-8) / T3
+    cs = np.array([[0.9, 0.1, 0.3], [0.2, 0.6, 0.5], [0.7, 0.3, 0.8]])
+    bg = np.array([0.05, 0.2, 0.1])
+    out = _render_2d(orc, W, H, [[8.0, 8.0]] * 3, [[0.5, 0, 0.5]] * 3, [o01, o01, o3], cs, bg,
+                     _center_pixel_grad(W, H))
+    assert out["pix_ambig"][8, 8] == 1
+    assert out["n_contrib"][8, 8] == 3 and out["nc_alt"][8, 8] == 2
+    d3 = o3 * T3 * (cs[2] - bg)
+    np.testing.assert_allclose(out["iallow"][:, 8, 8], np.abs(d3), rtol=1e-9)
+    np.testing.assert_allclose(out["gallow"][0:2, 5], [abs(d3.sum()) / (1 - o01)] * 2, rtol=1e-9)
+    np.testing.assert_allclose(out["gallow"][2, 6:9], [o3 * T3] * 3, rtol=1e-9)
+    np.testing.assert_allclose(out["gallow"][2, 5], T3 * (cs[2] - bg).sum(), rtol=1e-9)
+
+
+def test_widening_covers_fp32_alpha_error_in_front(orc):
+    """The per-pixel widening of the gradient scale must cover the FP32
+    error of alpha in front of a pixel, amplified by 1 / (1 - alpha) in
+    every transmittance behind it, without being orders of magnitude larger.
+    Measured on the oracle itself: the change of every gradient when the
+    front splat's alpha (0.98) moves by k ulp.  A 40-ulp move stays inside
+    the widened bound; a 5-ulp move already comes near the unwidened one
+    (so the widening is needed) and uses more than 1/128 of the widened one
+    (so it is not inflated)."""
+    W = H = 16
+    eps32 = 2.0 ** -24
+    off = (0.1, 0.1)
+    o0 = 0.98 / math.exp(-0.25 * (off[0] ** 2 + off[1] ** 2))
+    cs = np.array([[0.9, 0.1, 0.3], [0.2, 0.6, 0.5]])
+    bg = [0.3, 0.2, 0.1]
+    g = _center_pixel_grad(W, H)
+
+    def run(o):
+        return _render_2d(orc, W, H, [[8.0 + off[0], 8.0 + off[1]], [8.0, 8.0]], [[0.5, 0, 0.5]] * 2,
+                          [o, 0.5], cs, bg, g)
+    ref = run(o0)
+    assert ref["pix_ambig"][8, 8] == 0 and ref["pix_widen"][8, 8] > 1.0
+
+    def effect(k):
+        return np.maximum(*[np.abs(run(o0 * (1 + s * k * eps32))["grad2d"] - ref["grad2d"]) for s in (-1, 1)])
+    widened = lambda d: float((d / (1e-5 * ref["gscale"] + 1e-7)).max())
+    literal = lambda d: float((d / (1e-5 * ref["glit"] + 1e-7)).max())
+    assert widened(effect(40)) <= 1.0
+    d5 = effect(5)
+    assert literal(d5) > 0.5
+    assert widened(d5) > 1.0 / 128
 
 
 # ----------------------------------------------------------------------------
