@@ -34,7 +34,6 @@ if ROOT not in sys.path:
 
 METRIC = "backward-raster ms/iter and splat-grad updates/s: reduced vs plain atomicAdd"
 UNIT = "splat-grad updates/s"
-N_SM = 152
 FP32_LANES_PER_SM = 128
 # Algorithmic FP32 lane operations of the backward (an FMA counts as one):
 #   per examined (pixel, splat) pair: offset (2), quadratic form (7), exp (2),
@@ -339,7 +338,7 @@ def ingest_traffic(csv_path):
     out = {"kernel_hash": kh,
            "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                      "--clock-control none -k regex:backward_kernel (cold L2 per launch) of "
-                     "bench.py --profile --profile-tiers; see profiles/backward_tiers_single_view_500k.md"}
+                     "bench.py --profile --profile-tiers"}
     for name, i in zip(names, ids[-len(names):]):
         m = launches[i]
         rd, wr = m["dram__bytes_read.sum"], m["dram__bytes_write.sum"]
@@ -399,6 +398,85 @@ def large_scene_autograd(dev, flush, reps=5):
     return out
 
 
+RED_PATTERNS = ((0, "distinct"), (1, "one_address_per_warp"), (2, "nine_lanes_one_record"),
+                (3, "nine_per_lane_one_record"), (4, "v4_distinct"), (5, "v4_v4_scalar_per_lane_one_record"),
+                (6, "nine_per_lane_own_record"))
+
+
+def l2_red_sweep(dev, n_sm, stream, reps=3):
+    """gsr_bench_red over its access patterns and 1, 2, 4 and 8 CTAs per SM
+    (48 MB buffer: L2-resident); per pattern the best launch (median of reps)
+    in floats added per second."""
+    import torch
+
+    from paper_2401_05345_gb300 import gsr
+    red_buf = torch.zeros(12 * 1_000_000, dtype=torch.float32, device=dev)
+    out = {}
+    for pat, name in RED_PATTERNS:
+        best = None
+        for per_sm in (1, 2, 4, 8):
+            blocks = n_sm * per_sm
+            iters = max(8, 512 // per_sm)
+            gsr.gsr_bench_red(pat, blocks, 2, red_buf)
+            ts = []
+            for _ in range(reps):
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                adds = gsr.gsr_bench_red(pat, blocks, iters, red_buf)
+                a1.record(stream)
+                a1.synchronize()
+                ts.append(a0.elapsed_time(a1) / 1e3)
+            rate = adds / statistics.median(ts)
+            if best is None or rate > best["adds_per_s"]:
+                best = {"adds_per_s": rate, "ctas_per_sm": per_sm, "iters": iters}
+        out[name] = best
+    return out
+
+
+def l2_lane_rates(dev, n_sm, stream, per_sm=8, iters=64):
+    """Floats added per second by the access patterns of the accumulation
+    tiers' warp steps, by active lanes a = 1..32 (8 CTAs per SM): pattern 3
+    (PLAIN: 9 scalar reds per active lane into the step's record), pattern 5
+    (sparse hybrid warp: two v4 reds and one scalar per active lane) and
+    pattern 2 (reduced warp: one 9-lane red)."""
+    import torch
+
+    from paper_2401_05345_gb300 import gsr
+    red_buf = torch.zeros(12 * 1_000_000, dtype=torch.float32, device=dev)
+
+    def rate(pat, a):
+        gsr.gsr_bench_red(pat, n_sm * per_sm, 2, red_buf, active_lanes=a)
+        ts = []
+        for _ in range(3):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            adds = gsr.gsr_bench_red(pat, n_sm * per_sm, iters, red_buf, active_lanes=a)
+            a1.record(stream)
+            a1.synchronize()
+            ts.append(a0.elapsed_time(a1) / 1e3)
+        return adds / statistics.median(ts)
+    return {"plain": [None] + [rate(3, a) for a in range(1, 33)],
+            "sparse": [None] + [rate(5, a) for a in range(1, 33)],
+            "dense": rate(2, 32)}
+
+
+def l2_time_model(counts, tier, threshold, lane_rates):
+    """Seconds the L2 atomic units need for a backward's reds, from its
+    steps by active lanes and the microbenchmark rates of the same access
+    pattern; tier: 'plain', 'warp' or 'hybrid'."""
+    t = 0.0
+    for a, n in enumerate(counts["active_lane_hist"]):
+        if a == 0 or n == 0:
+            continue
+        if tier == "plain":
+            t += n * 9 * a / lane_rates["plain"][a]
+        elif tier == "warp" or a >= threshold:
+            t += n * 9 / lane_rates["dense"]
+        else:
+            t += n * 9 * a / lane_rates["sparse"][a]
+    return t
+
+
 def run_ours(args):
     import torch
 
@@ -412,6 +490,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     gsr.lib()
     peaks = load_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
 
     scene, cam, target_np, desc = make_workload(args.workload, args.seed + rank)
     bg = (0.0, 0.0, 0.0)
@@ -535,6 +614,15 @@ def run_ours(args):
                                        flush)
     t_recompute = autotune.time_backward(
         vb, bg, R.dimg, gsr.backward_opts(int(best.reduce_mode), int(best.threshold), lay, False, ppt), reps, flush)
+    # the reduction alone: the best tier's mode and threshold at the plain
+    # tier's one pixel per thread (same lane layout, no block masks)
+    best_ppt1 = gsr.backward_opts(int(best.reduce_mode), int(best.threshold), lay, True, 1)
+    t_best_ppt1 = autotune.time_backward(vb, bg, R.dimg, best_ppt1, reps, flush)
+    # global red traffic of the plain and the best tier (exact counts of the
+    # same traversal)
+    rc_plain = vb.red_counts(gsr.backward_opts("plain", 0, lay))
+    rc_best = (vb.red_counts(best) if int(best.reduce_mode) in (gsr.REDUCE_PLAIN, gsr.REDUCE_WARP, gsr.REDUCE_HYBRID)
+               else None)
     # deterministic tier (no float atomics): backward + per-Gaussian reduction
     det_ts = []
     det_opts = gsr.backward_opts("warp", 0, lay, True, ppt)
@@ -573,20 +661,16 @@ def run_ours(args):
 
     large = large_scene_autograd(dev, flush) if args.workload == "single_view" else None
 
-    # L2 atomic (red) throughput: the plain tier's roofline
-    red_buf = torch.zeros(12 * 1_000_000, dtype=torch.float32, device=dev)
-    red = {}
-    for pat, name in ((0, "distinct"), (1, "one_address_per_warp"), (2, "nine_lanes_one_record"),
-                      (3, "nine_per_lane_one_record")):
-        blocks, iters = N_SM * 8, 64
-        gsr.gsr_bench_red(pat, blocks, 4, red_buf)
-        torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        adds = gsr.gsr_bench_red(pat, blocks, iters, red_buf)
-        a1.record(stream)
-        a1.synchronize()
-        red[name] = adds / (a0.elapsed_time(a1) / 1e3)
+    # L2 atomic (red) throughput, the roofline of the atomic accumulation:
+    # every access pattern at 1-8 CTAs of 256 threads per SM; the peak is
+    # the best of all of them
+    red = l2_red_sweep(dev, n_sm, stream)
+    red_peak_name, red_peak = max(((k, v["adds_per_s"]) for k, v in red.items()), key=lambda kv: kv[1])
+    lane_rates = l2_lane_rates(dev, n_sm, stream)
+    inv_modes = {v: k for k, v in gsr.REDUCE_NAMES.items()}
+    t_l2_plain = l2_time_model(rc_plain, "plain", 0, lane_rates)
+    t_l2_best = (l2_time_model(rc_best, inv_modes[int(best.reduce_mode)], int(best.threshold), lane_rates)
+                 if rc_best else None)
 
     # divergent-destination accumulation (Sec. V-A1): plain atomics vs the
     # serialized warp reduction (SW-S) vs the sorted segmented reduction
@@ -656,7 +740,7 @@ def run_ours(args):
             "updates_per_s_plain": 12 * n_tex_px / (tex_ms["backward_plain_thr0"] / 1e3),
             "updates_per_s_best": 12 * n_tex_px / (tex_best[0] / 1e3),
             "speedup_best_vs_plain": tex_ms["backward_plain_thr0"] / tex_best[0],
-            "plain_frac_of_l2_distinct_red": (12 * n_tex_px / (tex_ms["backward_plain_thr0"] / 1e3)) / red["distinct"]}
+            "plain_frac_of_l2_red_peak": (12 * n_tex_px / (tex_ms["backward_plain_thr0"] / 1e3)) / red_peak}
 
     # end to end through the public API with host buffers.  A training step's
     # input is its target image (the scene is model state that stays on the
@@ -724,10 +808,13 @@ def run_ours(args):
     # roofline of the dominant kernel (the reduced backward): FP32 ALU issue
     bwd_avg_s = statistics.mean(bwd_ms) / 1e3
     ops = OPS_PER_EXAMINED * p_exam + OPS_PER_ACTIVE * p_active
-    peak_ops = N_SM * FP32_LANES_PER_SM * peaks["sm_max_mhz"] * 1e6
+    peak_ops = n_sm * FP32_LANES_PER_SM * peaks["sm_max_mhz"] * 1e6
     achieved = ops / bwd_avg_s
+    # the same with only the pairs the warps evaluate: (warp, splat) steps
+    # that pass the per-warp cull, 32 lanes x pixels per thread each
+    exec_pairs = rc_best["warp_steps"] * 32 * ppt if rc_best else None
+    ops_exec = OPS_PER_EXAMINED * exec_pairs + OPS_PER_ACTIVE * p_active if exec_pairs else None
     traffic = traffic_from_profile(kernel_source_hash(), best_name, p_active)
-    plain_atomics = 9 * p_active
     # algorithmic bytes of one backward: 4 B id + 36 B attributes per list
     # entry, 12 B dL/dimage + 4 B final_T + 4 B n_contrib per pixel, one read
     # and one write of the 36 B gradient record per visible splat
@@ -758,23 +845,50 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": f"backward_kernel ({best_name})",
                          "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "T fp32-ops/s",
                          "frac": achieved / peak_ops, "traffic": traffic,
-                         "peak_source": f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                         "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                         f"{peaks['sm_max_mhz']:.0f} MHz ({peaks['source']} max SM clock)",
-                         "ops_per_launch": ops, "launch_ms": bwd_avg_s * 1e3},
+                         "ops_per_launch": ops, "launch_ms": bwd_avg_s * 1e3,
+                         "frac_executed_pairs": (ops_exec / bwd_avg_s / peak_ops) if ops_exec else None,
+                         "executed_pairs": exec_pairs,
+                         "note": "frac counts 17 ops for every examined pair (P_examined, up to each pixel's "
+                                 "last contributor); frac_executed_pairs only for the pairs of the (warp, splat) "
+                                 "steps that pass the per-warp cull"},
             "backward_raster": {
                 "ms_plain_atomicAdd": t_plain, "ms_warp": t_warp, "ms_block": t_block,
                 "ms_cluster_dsmem": t_cluster, "cluster_threshold": thr_c,
                 "ms_best": t_best, "best": best_name, "ms_best_recompute_T": t_recompute,
                 "ms_deterministic_no_atomics": t_det,
                 "speedup_best_vs_plain": t_plain / t_best,
+                "ms_best_mode_one_pixel_per_thread": t_best_ppt1,
+                "speedup_reduction_alone_vs_plain": t_plain / t_best_ppt1,
+                "speedup_note": "speedup_best_vs_plain: plain (1 px/thread) against the autotuned tier (its "
+                                "pixels per thread and the forward's block masks); speedup_reduction_alone: "
+                                "the best tier's mode and threshold at 1 px/thread and the same lane layout",
                 "updates_per_s_plain": units / (t_plain / 1e3),
                 "updates_per_s_best": units / (t_best / 1e3),
                 "hybrid_threshold_sweep_ms": sweep, "autotune_ms": tune_table,
-                "plain_l2_atomic_roofline": {
-                    "achieved_adds_per_s": plain_atomics / (t_plain / 1e3),
-                    "peak_adds_per_s": red["nine_per_lane_one_record"],
-                    "frac": (plain_atomics / (t_plain / 1e3)) / red["nine_per_lane_one_record"],
-                    "peak_source": "gsr_bench_red pattern 3 (9 adds per lane into one record per warp), same GPU"},
+                "l2_atomic_roofline": {
+                    "peak_adds_per_s": red_peak,
+                    "peak_source": f"gsr_bench_red, best of {len(RED_PATTERNS)} access patterns x 1-8 CTAs per SM "
+                                   f"on the same GPU ({red_peak_name})",
+                    "model": "frac = (seconds the L2 atomic units need for the launch's reds: its warp steps by "
+                             "active lanes, each at the gsr_bench_red rate of the same access pattern with that "
+                             "many lanes) / (the launch's measured time); frac_of_peak_adds = achieved adds/s / "
+                             "peak_adds_per_s",
+                    "plain": {"adds": rc_plain["adds"], "lane_reds": rc_plain["lane_reds"],
+                              "achieved_adds_per_s": rc_plain["adds"] / (t_plain / 1e3),
+                              "l2_time_ms": t_l2_plain * 1e3, "frac": t_l2_plain / (t_plain / 1e3),
+                              "frac_of_peak_adds": rc_plain["adds"] / (t_plain / 1e3) / red_peak},
+                    "best": ({"tier": best_name, "adds": rc_best["adds"], "lane_reds": rc_best["lane_reds"],
+                              "red_instructions": rc_best["red_instructions"],
+                              "red_v4_instructions": rc_best["red_v4_instructions"],
+                              "achieved_adds_per_s": rc_best["adds"] / (t_best / 1e3),
+                              "l2_time_ms": t_l2_best * 1e3, "frac": t_l2_best / (t_best / 1e3),
+                              "frac_of_peak_adds": rc_best["adds"] / (t_best / 1e3) / red_peak,
+                              "adds_vs_plain": rc_best["adds"] / rc_plain["adds"]} if rc_best else None),
+                    "lane_rates_adds_per_s": {"plain_9_per_lane_one_record": lane_rates["plain"][1:],
+                                              "sparse_v4_v4_scalar_one_record": lane_rates["sparse"][1:],
+                                              "dense_9_lane_red": lane_rates["dense"]}},
                 "algorithmic_bytes_best": alg_bytes,
                 "hbm_gbs_best": alg_bytes / (t_best * 1e-3) / 1e9,
             },
@@ -782,6 +896,7 @@ def run_ours(args):
                            "note": "same outputs; each includes its one host sync for the key count"},
             "texture_gradient": tex_results,
             "l2_red_adds_per_s": red,
+            "traffic_counts_red": {"plain": rc_plain, "best": rc_best},
             "differentiation_large": large,
             "divergent_accumulation_ms": {"items": n_items, "records": rows,
                                           "by_distinct_destinations_per_warp": scat},

@@ -38,7 +38,7 @@ extern "C" {
 #define GSR_EINVAL     (-1)  /* bad argument (null pointer, size, option)   */
 #define GSR_ECAPACITY  (-2)  /* duplicated keys exceed key_capacity          */
 #define GSR_ECUDA      (-3)  /* CUDA runtime / launch error                  */
-#define GSR_ETIMEOUT   (-4)  /* a bounded device wait gave up                */
+#define GSR_ETIMEOUT   (-4)  /* reserved: no call waits on the device today   */
 #define GSR_ESCRATCH   (-5)  /* scratch buffer smaller than required         */
 #define GSR_ELIMIT     (-6)  /* size beyond gsr_bin_sort_static's fixed limit */
 
@@ -117,7 +117,9 @@ typedef struct gsr_backward_opts {
  * All pointers are device pointers with the meaning and layout they have in
  * gsr_backward; final_T / n_contrib may be NULL when store_T is 0, and so may
  * block_mask (the view's forward block masks, see gsr_forward); 16x16
- * tiles. */
+ * tiles.  splat2d and grad2d must start on 16 bytes (the hybrid tier sends
+ * 16-byte vector reds into grad2d); the library cannot check descriptors
+ * that live in device memory, so the caller must. */
 typedef struct gsr_view {
     int32_t width, height;
     const uint32_t* tile_ranges;
@@ -378,6 +380,9 @@ int gsr_forward_l1(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h
  *   Read by the configurations whose warps own those 8x8 blocks
  *   (lane_layout 1, pixels_per_thread 2); the others compute the test
  *   themselves.  Masks of other lists or splats give wrong gradients.
+ *   grad2d: [n,GSR_REC] starting on 16 bytes (sparse warps of the hybrid
+ *   tier add a record's first 8 values with two 16-byte vector reds);
+ *   GSR_EINVAL otherwise.
  */
 int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                  const uint32_t* tile_ranges, const uint32_t* point_list,
@@ -475,6 +480,27 @@ int gsr_backward_stats(int32_t width, int32_t height, int32_t tile_w, int32_t ti
                        uint64_t* hist, gsr_stream_t stream);
 
 /*
+ * Global red counts of one backward launch: the traversal of gsr_backward
+ * with the tier and threshold of opts (PLAIN, WARP or HYBRID; store_T = 1),
+ * every global red replaced by counting it, nothing else written.  Gives the
+ * L2 atomic traffic of a tier (Sec. III-A: the atomic operations per
+ * iteration; Sec. IV-B: the balancing threshold moves warps between the SM
+ * and the L2).  counts: device uint64 [39], overwritten:
+ *   [0] scalar red warp instructions, [1] red.v4 warp instructions,
+ *   [2] floats added at the L2, [3] lane-level red operations (the requests
+ *   before any coalescing), [4] (warp, splat) steps walked, [5] of those
+ *   with at least one active lane, [6 + a] steps with exactly a active
+ *   lanes, a = 0..32 (the per-warp activity of Sec. III-B, Fig. 5, for
+ *   this configuration).
+ * Other arguments as gsr_backward (no upstream gradient or grad2d needed).
+ */
+int gsr_backward_red_counts(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                            const uint32_t* tile_ranges, const uint32_t* point_list, const float* splat2d,
+                            const float* final_T, const int32_t* n_contrib, const gsr_backward_opts* opts,
+                            const uint8_t* block_mask, const uint32_t* tile_order, uint64_t* counts,
+                            gsr_stream_t stream);
+
+/*
  * Backward projection: chain rule from grad2d to the 3D parameters through
  * the conic inverse, the EWA Jacobian (exact derivative, zero through an
  * active frustum clamp), the covariance R S S^T R^T, the quaternion
@@ -555,18 +581,27 @@ int gsr_scatter_add9(int64_t n, const uint32_t* idx, const float* vals, float* o
                      int32_t method, int32_t threshold, gsr_stream_t stream);
 
 /*
- * Microbenchmark of the L2 atomic (red) path, the roofline of the PLAIN tier
- * (Sec. II-A: atomics are processed by the ROP units at the L2 slices).
- *   pattern 0: every lane adds to its own address (coalesced, distinct);
- *   pattern 1: all 32 lanes of a warp add to one address (contended);
- *   pattern 2: 9 lanes of a warp add to 9 consecutive floats of a 48-byte
- *              record (the reduced tiers' access);
- *   pattern 3: as 1 but 9 adds per lane to 9 consecutive floats (PLAIN).
+ * Microbenchmark of the L2 atomic (red) path, the roofline of the atomic
+ * accumulation (Sec. II-A, Sec. III-A: atomics are processed by the atomic
+ * units at the L2 slices).  Each pattern is one way warps send adds:
+ *   0: every lane adds 1 float to its own address (coalesced, distinct);
+ *   1: all 32 lanes of a warp add to one address (contended);
+ *   2: 9 lanes of a warp add to the 9 floats of one 48-byte record (the
+ *      reduced tiers' one red per dense warp step);
+ *   3: every lane adds the same record's 9 floats (the PLAIN tier's warp
+ *      with all lanes active);
+ *   4: every lane adds 4 floats to its own 16-byte slot (red.v4, distinct);
+ *   5: every lane sends two red.v4 and one scalar red to one record per warp
+ *      (the hybrid tier's sparse warp with all lanes active);
+ *   6: every lane adds 9 floats to its own record (PLAIN without contention).
+ * active_lanes (1..32): in the patterns with one address or record per warp
+ * (1, 3, 5) only lanes 0..active_lanes-1 send (a warp step with that many
+ * active pixels); the other patterns use every lane.
  * Issues `iters` rounds over a grid of `blocks` x 256 threads; buffer holds
- * buffer_floats floats (device, accumulated into).  Adds performed are
- * reported in *adds (host).
+ * buffer_floats floats (device, 16-byte aligned, accumulated into).  Floats
+ * added are reported in *adds (host).
  */
-int gsr_bench_red(int32_t pattern, int32_t blocks, int32_t iters, float* buffer,
+int gsr_bench_red(int32_t pattern, int32_t active_lanes, int32_t blocks, int32_t iters, float* buffer,
                   int64_t buffer_floats, int64_t* adds, gsr_stream_t stream);
 
 #ifdef __cplusplus

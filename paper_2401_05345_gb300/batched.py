@@ -115,6 +115,8 @@ class BatchedViews:
             d.n_contrib = vb.n_contrib.data_ptr() if vb.n_contrib is not None else None
             d.dL_dimage = self.dimg[i].data_ptr()
             d.grad2d = vb.grad2d.data_ptr()
+            if d.splat2d % 16 or d.grad2d % 16:  # the library cannot check device-resident descriptors
+                raise ValueError(f"view {i}: splat2d and grad2d must start on 16 bytes")
             # the batched backward always follows render_all, whose forward
             # writes each view's block masks
             d.block_mask = vb.block_mask.data_ptr()

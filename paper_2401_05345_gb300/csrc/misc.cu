@@ -81,28 +81,44 @@ __global__ void activate_backward_kernel(long long n, const float* __restrict__ 
     }
 }
 
-// pattern 0: own address per lane; 1: one address per warp; 2: 9 lanes to a
-// 48-byte record; 3: 9 adds per lane into one record per warp.
-__global__ void __launch_bounds__(256) red_bench_kernel(int pattern, int iters, float* __restrict__ buf,
+// Access patterns of gsr_bench_red (see gsr.h): 0 own float per lane,
+// 1 one float per warp, 2 nine lanes into one record per warp, 3 nine floats
+// per lane into one record per warp, 4 own 16-byte slot per lane (v4),
+// 5 two v4 and one scalar per lane into one record per warp, 6 nine floats
+// per lane into the lane's own record.  Lanes >= `lanes` stay idle in the
+// patterns with one address or record per warp (1, 3, 5).
+__global__ void __launch_bounds__(256) red_bench_kernel(int pattern, int lanes, int iters, float* __restrict__ buf,
                                                         long long nfloats) {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gwarp = gtid >> 5;
     const int lane = threadIdx.x & 31;
     const long long nrec = nfloats / GSR_REC;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (int it = 0; it < iters; ++it) {
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const long long nwarps = nthreads >> 5;
+    const bool idle = (pattern == 1 || pattern == 3 || pattern == 5) && lane >= lanes;
+    for (int it = 0; it < iters && !idle; ++it) {
         const long long w = (gwarp + (long long)it * nwarps) % nrec;  // record touched by this warp
         float* rec = buf + w * GSR_REC;
+        const long long t = gtid + (long long)it * nthreads;          // this lane's running index
         if (pattern == 0) {
-            long long a = (gtid + (long long)it * gridDim.x * blockDim.x) % nfloats;
-            red_add(buf + a, 1.0f);
+            red_add(buf + t % nfloats, 1.0f);
         } else if (pattern == 1) {
             red_add(rec, 1.0f);
         } else if (pattern == 2) {
             if (lane < 9) red_add(rec + lane, 1.0f);
-        } else {
+        } else if (pattern == 3) {
 #pragma unroll
             for (int q = 0; q < 9; ++q) red_add(rec + q, 1.0f);
+        } else if (pattern == 4) {
+            red_add_v4(buf + 4 * (t % (nfloats / 4)), 1.0f, 1.0f, 1.0f, 1.0f);
+        } else if (pattern == 5) {
+            red_add_v4(rec, 1.0f, 1.0f, 1.0f, 1.0f);
+            red_add_v4(rec + 4, 1.0f, 1.0f, 1.0f, 1.0f);
+            red_add(rec + 8, 1.0f);
+        } else {
+            float* own = buf + (t % nrec) * GSR_REC;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) red_add(own + q, 1.0f);
         }
     }
 }
@@ -153,14 +169,19 @@ extern "C" int gsr_adam_step(int64_t n, float* param, const float* grad, float* 
     return check_launch();
 }
 
-extern "C" int gsr_bench_red(int32_t pattern, int32_t blocks, int32_t iters, float* buffer,
+extern "C" int gsr_bench_red(int32_t pattern, int32_t active_lanes, int32_t blocks, int32_t iters, float* buffer,
                              int64_t buffer_floats, int64_t* adds, gsr_stream_t stream) {
-    if (pattern < 0 || pattern > 3 || blocks <= 0 || iters <= 0 || !buffer || buffer_floats < 32 * GSR_REC || !adds)
+    if (pattern < 0 || pattern > 6 || blocks <= 0 || iters <= 0 || !buffer || buffer_floats < 32 * GSR_REC || !adds)
         return GSR_EINVAL;
-    long long threads = (long long)blocks * 256, warps = threads / 32;
-    long long per_iter = pattern == 0 ? threads : pattern == 1 ? threads : pattern == 2 ? warps * 9 : threads * 9;
+    if (active_lanes < 1 || active_lanes > 32) return GSR_EINVAL;
+    if (!aligned16(buffer)) return GSR_EINVAL;  // 16-byte records and slots (vector reds)
+    const long long threads = (long long)blocks * 256, warps = threads / 32;
+    const bool per_warp = pattern == 1 || pattern == 3 || pattern == 5;
+    const long long lanes = per_warp ? warps * active_lanes : threads;  // lanes that send
+    const long long per_lane[7] = {1, 1, 0, 9, 4, 9, 9};
+    const long long per_iter = pattern == 2 ? warps * 9 : lanes * per_lane[pattern];
     *adds = per_iter * iters;
-    red_bench_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(pattern, iters, buffer, buffer_floats);
+    red_bench_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(pattern, active_lanes, iters, buffer, buffer_floats);
     return check_launch();
 }
 

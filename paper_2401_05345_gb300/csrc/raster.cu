@@ -399,7 +399,8 @@ extern "C" int gsr_backward(int32_t width, int32_t height, int32_t tile_w, int32
     gsr_backward_opts o = {GSR_REDUCE_WARP, 0, 0, 1, 1, {0, 0, 0}};
     if (opts) o = *opts;
     if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !bg || !dL_dimage || !grad2d) return GSR_EINVAL;
-    if (!aligned16(splat2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
+    // grad2d records take 16-byte vector reds (sparse warps of the hybrid tier)
+    if (!aligned16(splat2d) || !aligned16(grad2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
     if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
     if (check_bwd_opts(o) != GSR_OK) return GSR_EINVAL;
     if (o.store_T && (!final_T || !n_contrib)) return GSR_EINVAL;
@@ -454,6 +455,38 @@ extern "C" int gsr_backward_stats(int32_t width, int32_t height, int32_t tile_w,
     return check_launch();
 }
 
+extern "C" int gsr_backward_red_counts(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                                       const uint32_t* tile_ranges, const uint32_t* point_list,
+                                       const float* splat2d, const float* final_T, const int32_t* n_contrib,
+                                       const gsr_backward_opts* opts, const uint8_t* block_mask,
+                                       const uint32_t* tile_order, uint64_t* counts, gsr_stream_t stream_) {
+    if (width <= 0 || height <= 0 || !tile_ranges || !splat2d || !final_T || !n_contrib || !opts || !counts)
+        return GSR_EINVAL;
+    if (!aligned16(splat2d) || !aligned8(tile_ranges) || !aligned8(counts)) return GSR_EINVAL;
+    if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
+    const gsr_backward_opts o = *opts;
+    if (check_bwd_opts(o) != GSR_OK || !o.store_T) return GSR_EINVAL;
+    if (o.reduce_mode != GSR_REDUCE_PLAIN && o.reduce_mode != GSR_REDUCE_WARP && o.reduce_mode != GSR_REDUCE_HYBRID)
+        return GSR_EINVAL;
+    BwdArgs a = {};
+    a.g = RasterGeom{width, height, (width + 15) / 16, (height + 15) / 16};
+    a.ranges = reinterpret_cast<const uint2*>(tile_ranges);
+    a.point_list = point_list;
+    a.splat2d = splat2d;
+    a.final_T = final_T;
+    a.n_contrib = n_contrib;
+    a.threshold = o.threshold;
+    a.order = tile_order;
+    a.block_mask = block_mask;
+    a.counts = reinterpret_cast<unsigned long long*>(counts);
+    a.count_tier = o.reduce_mode;
+    cudaStream_t s = (cudaStream_t)stream_;
+    cudaError_t e = cudaMemsetAsync(counts, 0, kCountSlots * sizeof(uint64_t), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    launch_bwd_mode<kModeCount>(o.pixels_per_thread == 2 ? 2 : 1, o.lane_layout, true, a.g.gx * a.g.gy, a, s);
+    return check_launch();
+}
+
 extern "C" int gsr_backward_deterministic(int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                                           const uint32_t* tile_ranges, const uint32_t* point_list,
                                           const float* splat2d, const int32_t* radius, int32_t n,
@@ -468,7 +501,7 @@ extern "C" int gsr_backward_deterministic(int32_t width, int32_t height, int32_t
         return GSR_EINVAL;
     if (n > 0 && (!radius || !entry_offsets || !partial || !point_list)) return GSR_EINVAL;
     if (partial_entries < 0) return GSR_EINVAL;
-    if (!aligned16(splat2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
+    if (!aligned16(splat2d) || !aligned16(grad2d) || !aligned8(tile_ranges)) return GSR_EINVAL;
     if (tile_w != 16 || tile_h != 16) return GSR_EINVAL;
     if ((o.lane_layout != 0 && o.lane_layout != 1) || (o.store_T != 0 && o.store_T != 1)) return GSR_EINVAL;
     if (o.pixels_per_thread < 0 || o.pixels_per_thread > 2) return GSR_EINVAL;

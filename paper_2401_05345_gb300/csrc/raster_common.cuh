@@ -235,7 +235,19 @@ struct BwdArgs {
     int n;                // Gaussians (entry_off has n + 1 values)
     uint32_t partial_cap; // entries partial holds
     const uint8_t* block_mask;  // per-entry cull masks from the forward, or NULL
+    // count mode only
+    unsigned long long* counts;  // kCountSlots totals, see kModeCount
+    int count_tier;              // tier whose global reds are counted (PLAIN, WARP or HYBRID)
 };
+
+// Count mode: the traversal of a tier (count_tier, threshold) with every
+// global red replaced by counting it.  counts[0] scalar red warp
+// instructions, [1] vector (v4) red warp instructions, [2] floats added at
+// L2, [3] lane-level red operations (what the L2 receives before any
+// coalescing), [4] (warp, splat) steps walked, [5] of those with an active
+// lane, [6 + a] steps with exactly a active lanes (a = 0..32).
+constexpr int kModeCount = 6;
+constexpr int kCountSlots = 6 + 33;
 
 // Deterministic tier: per-warp partial sums are combined in warp order and
 // written, without atomics, to one 9-float slot per (tile, splat) list entry
@@ -435,9 +447,10 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
     int mylast = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-        g0[q] = inside[q] ? p.dL_dimage[pix[q]] : 0.0f;
-        g1[q] = inside[q] ? p.dL_dimage[HW + pix[q]] : 0.0f;
-        g2[q] = inside[q] ? p.dL_dimage[2 * HW + pix[q]] : 0.0f;
+        const bool rd = inside[q] && MODE != kModeCount;  // the count mode takes no upstream gradient
+        g0[q] = rd ? p.dL_dimage[pix[q]] : 0.0f;
+        g1[q] = rd ? p.dL_dimage[HW + pix[q]] : 0.0f;
+        g2[q] = rd ? p.dL_dimage[2 * HW + pix[q]] : 0.0f;
         T[q] = Tf[q];
         S[q] = Tf[q] * (p.bg0 * g0[q] + p.bg1 * g1[q] + p.bg2 * g2[q]);
         mylast = max(mylast, last[q]);
@@ -453,6 +466,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
     const int maxlast = sm.maxlast;
     const int rparam = reduce9_param(lane);
     float* __restrict__ grad = p.grad2d;
+    unsigned long long cnt_red = 0, cnt_red4 = 0, cnt_add = 0, cnt_lane = 0, cnt_step = 0, cnt_act = 0;
 
     for (int top = maxlast; top > 0; top -= B) {
         const int cnt = min(B, top);
@@ -495,6 +509,22 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                         if (q == 0) pair_grads<true>(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
                         else pair_grads<false>(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
                         any |= act;
+                    }
+                    if (MODE == kModeCount) {
+                        const unsigned m = __ballot_sync(kFull, any);
+                        const unsigned long long a = (unsigned long long)__popc(m);
+                        if (lane == 0) atomicAdd(&p.counts[6 + a], 1ull);
+                        cnt_step += 1;
+                        if (a == 0) continue;
+                        cnt_act += 1;
+                        if (p.count_tier == GSR_REDUCE_PLAIN) {  // 9 scalar atomics per active lane
+                            cnt_red += 9; cnt_add += 9 * a; cnt_lane += 9 * a;
+                        } else if (p.count_tier == GSR_REDUCE_WARP || (int)a >= p.threshold) {  // one 9-lane red
+                            cnt_red += 1; cnt_add += 9; cnt_lane += 9;
+                        } else {  // two v4 reds and one scalar per active lane
+                            cnt_red += 1; cnt_red4 += 2; cnt_add += 9 * a; cnt_lane += 3 * a;
+                        }
+                        continue;
                     }
                     float* rec = grad + (size_t)sm.id[k] * GSR_REC;
                     if (MODE == kModeDet) {
@@ -574,6 +604,14 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                 }
             }
         }
+    }
+    if (MODE == kModeCount && lane == 0 && cnt_step) {
+        atomicAdd(&p.counts[0], cnt_red);
+        atomicAdd(&p.counts[1], cnt_red4);
+        atomicAdd(&p.counts[2], cnt_add);
+        atomicAdd(&p.counts[3], cnt_lane);
+        atomicAdd(&p.counts[4], cnt_step);
+        atomicAdd(&p.counts[5], cnt_act);
     }
 }
 

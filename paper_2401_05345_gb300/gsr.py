@@ -111,6 +111,8 @@ def lib():
     L.gsr_backward.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, POINTER(c_float), P, P, P, P,
                                POINTER(BackwardOpts), P, P, P]
     L.gsr_backward_stats.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, P, c_int32, P, P]
+    L.gsr_backward_red_counts.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P, P, P,
+                                          POINTER(BackwardOpts), P, P, P, P]
     L.gsr_backward_project.argtypes = [c_int32, c_int32, P, P, P, P, P, POINTER(Camera), P, P, P, P, P,
                                        P, P, P]
     L.gsr_backward_project_store.argtypes = L.gsr_backward_project.argtypes
@@ -124,7 +126,7 @@ def lib():
                                              POINTER(c_float), P, P, P, P, c_int64, P, POINTER(BackwardOpts), P, P,
                                              P]
     L.gsr_scatter_add9.argtypes = [c_int64, P, P, P, c_int32, c_int32, c_int32, P]
-    L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
+    L.gsr_bench_red.argtypes = [c_int32, c_int32, c_int32, c_int32, P, c_int64, POINTER(c_int64), P]
     L.gsr_cube_forward.argtypes = [c_int32, c_int32, P, c_int32, P, P, P]
     L.gsr_cube_backward.argtypes = [c_int32, c_int32, P, P, c_int32, P, c_int32, c_int32, P]
     for name in ("gsr_preprocess", "gsr_bin_scratch_bytes", "gsr_bin_sort", "gsr_bin_sort_static",
@@ -286,6 +288,20 @@ def gsr_backward_stats(width, height, tile_w, tile_h, tile_ranges, point_list, s
                                                           lane_layout, _ptr(hist), _stream(stream)))
 
 
+RED_COUNT_NAMES = ("red_instructions", "red_v4_instructions", "adds", "lane_reds", "warp_steps",
+                   "warp_steps_active")
+
+
+def gsr_backward_red_counts(width, height, tile_w, tile_h, tile_ranges, point_list, splat2d, final_T, n_contrib,
+                            opts, counts, stream=None, tile_order=None, block_mask=None):
+    """counts: int64 tensor [39]: the totals named by RED_COUNT_NAMES, then
+    the steps with 0..32 active lanes."""
+    _check("gsr_backward_red_counts",
+           lib().gsr_backward_red_counts(width, height, tile_w, tile_h, _ptr(tile_ranges), _ptr(point_list),
+                                         _ptr(splat2d), _ptr(final_T), _ptr(n_contrib), ctypes.byref(opts),
+                                         _ptr(block_mask), _ptr(tile_order), _ptr(counts), _stream(stream)))
+
+
 def gsr_backward_project(n, sh_degree, mean, scale, quat, opacity, feat, cam, radius, grad2d, dmean,
                          dscale, dquat, dopacity, dfeat, stream=None, accumulate=True):
     """accumulate=False calls gsr_backward_project_store (outputs written,
@@ -328,9 +344,9 @@ def gsr_scatter_add9(n, idx, vals, out, stride=GSR_REC, method="serial", thresho
                                                       _stream(stream)))
 
 
-def gsr_bench_red(pattern, blocks, iters, buffer, stream=None) -> int:
+def gsr_bench_red(pattern, blocks, iters, buffer, stream=None, active_lanes=32) -> int:
     adds = c_int64(0)
-    _check("gsr_bench_red", lib().gsr_bench_red(pattern, blocks, iters, _ptr(buffer), buffer.numel(),
+    _check("gsr_bench_red", lib().gsr_bench_red(pattern, active_lanes, blocks, iters, _ptr(buffer), buffer.numel(),
                                                 ctypes.byref(adds), _stream(stream)))
     return int(adds.value)
 

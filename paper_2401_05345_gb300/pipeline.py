@@ -178,6 +178,18 @@ class ViewBuffers:
                          bg, self.final_T, self.n_contrib, dL_dimage, self.grad2d, opts, stream,
                          tile_order=self.tile_order, block_mask=self._mask())
 
+    def red_counts(self, opts, stream=None) -> dict:
+        """The global red traffic one ``backward`` with ``opts`` issues
+        (gsr_backward_red_counts; PLAIN, WARP or HYBRID, stored T)."""
+        c = torch.zeros(39, dtype=torch.int64, device=self.device)
+        gsr.gsr_backward_red_counts(self.W, self.H, self.tw, self.th, self.tile_ranges, self.point_list, self.splat2d,
+                                    self.final_T, self.n_contrib, opts, c, stream, tile_order=self.tile_order,
+                                    block_mask=self._mask())
+        v = [int(x) for x in c.cpu()]
+        out = dict(zip(gsr.RED_COUNT_NAMES, v))
+        out["active_lane_hist"] = v[6:]
+        return out
+
     def backward_deterministic(self, bg, dL_dimage, opts=None, stream=None):
         """Backward without float atomics (bit-identical run to run); keeps
         its per-entry partial buffer between calls, sized by the key capacity
@@ -219,6 +231,11 @@ class Renderer:
         self.dimg = torch.zeros_like(self.vb.image)
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
 
+    def project(self, sc: SceneTensors, stream=None):
+        """The step's first stage: the 2D splat records of ``sc`` (with the 2D
+        gradient records zeroed in the same pass)."""
+        self.vb.preprocess(sc, zero_grad=True, stream=stream)
+
     def step(self, sc: SceneTensors, target: torch.Tensor, bg, grads: SceneTensors, stream=None,
              on_backward=None, accumulate=True, sync_bin=True):
         """Runs the whole path; ``grads`` accumulates the 3D gradients (or,
@@ -230,7 +247,7 @@ class Renderer:
         (if it returns False the step has to be redone)."""
         vb = self.vb
         self.loss.zero_()
-        vb.preprocess(sc, zero_grad=True, stream=stream)
+        self.project(sc, stream)
         if sync_bin:
             vb.bin(stream)
         else:

@@ -92,7 +92,43 @@ def test_argument_errors_are_reported_before_any_launch(lib):
     assert lib.gsr_bin_scratch_bytes(10, 64, 64, 16, 16, -1, ctypes.byref(out)) == gsr.GSR_EINVAL
     assert lib.gsr_adam_step(10, p, p, p, p, 1e-3, 0.9, 0.999, 1e-8, 0, None) == gsr.GSR_EINVAL
     n = ctypes.c_int64(0)
-    assert lib.gsr_bench_red(9, 1, 1, p, 1024, ctypes.byref(n), None) == gsr.GSR_EINVAL
+    assert lib.gsr_bench_red(9, 32, 1, 1, p, 1024, ctypes.byref(n), None) == gsr.GSR_EINVAL
+    assert lib.gsr_bench_red(7, 32, 1, 1, p, 1024, ctypes.byref(n), None) == gsr.GSR_EINVAL
+    assert lib.gsr_bench_red(4, 32, 1, 1, ctypes.c_void_p(20), 1024, ctypes.byref(n), None) == gsr.GSR_EINVAL
+    for lanes in (0, 33):
+        assert lib.gsr_bench_red(3, lanes, 1, 1, p, 1024, ctypes.byref(n), None) == gsr.GSR_EINVAL
+
+
+def test_grad2d_alignment_is_checked(lib):
+    """grad2d takes 16-byte vector reds: a record buffer that starts off a
+    16-byte boundary is refused on the host (not a misaligned access on the
+    device)."""
+    from paper_2401_05345_gb300 import gsr
+    bg = (ctypes.c_float * 3)(0, 0, 0)
+    p = ctypes.c_void_p(16)
+    opts = gsr.backward_opts("hybrid", 24, 1, True, 2)
+    for off in (4, 8, 12):
+        g = ctypes.c_void_p(16 + off)
+        assert lib.gsr_backward(32, 32, 16, 16, p, p, p, bg, p, p, p, g, ctypes.byref(opts), None, None,
+                                None) == gsr.GSR_EINVAL
+        assert lib.gsr_backward_deterministic(32, 32, 16, 16, p, p, p, p, 10, p, bg, p, p, p, p, 100, g,
+                                              ctypes.byref(opts), None, None, None) == gsr.GSR_EINVAL
+
+
+def test_red_counts_argument_errors(lib):
+    from paper_2401_05345_gb300 import gsr
+    p = ctypes.c_void_p(16)
+
+    def rc(opts, counts=p, final=(p, p)):
+        return lib.gsr_backward_red_counts(32, 32, 16, 16, p, p, p, *final, ctypes.byref(opts), None, None, counts,
+                                           None)
+    for bad in (gsr.backward_opts("block"), gsr.backward_opts("cluster"), gsr.backward_opts("warp", store_T=False),
+                gsr.backward_opts("plain", pixels_per_thread=2)):
+        assert rc(bad) == gsr.GSR_EINVAL
+    good = gsr.backward_opts("hybrid", 24, 1, True, 2)
+    assert rc(good, counts=None) == gsr.GSR_EINVAL
+    assert rc(good, counts=ctypes.c_void_p(20)) == gsr.GSR_EINVAL
+    assert rc(good, final=(None, p)) == gsr.GSR_EINVAL
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):

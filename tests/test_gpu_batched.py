@@ -71,7 +71,8 @@ def test_batched_graph_matches_oracle(dev, orc):
             torch.cuda.synchronize()
             for i, ref in enumerate(refs):
                 got = bv.vbs[i].grad2d.cpu().numpy()[:, :9]
-                check_scaled(f"view {i} {BT.gsr_opts_tuple(opts)}", got, ref["grad2d"], ref["gscale"], ref["gallow"])
+                check_scaled(f"view {i} {BT.gsr_opts_tuple(opts)}", got, ref["grad2d"], ref["gscale"], ref["gallow"],
+                             lit=ref["glit"])
 
 
 def test_work_order_is_longest_first(dev):

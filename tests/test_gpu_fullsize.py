@@ -134,10 +134,11 @@ def test_fullsize_forward_on_sampled_tiles(dev, full):
     for t in full["tile_sample"]:
         ys, xs = _tile_pixels(full, t)
         check_scaled(f"image tile {t}", img[:, ys, xs], out["image"][:, ys, xs],
-                     np.abs(out["image"][:, ys, xs]) * out["pix_widen"][None, ys, xs], out["iallow"][:, ys, xs])
+                     np.abs(out["image"][:, ys, xs]) * out["pix_widen"][None, ys, xs], out["iallow"][:, ys, xs],
+                     lit=np.abs(out["image"][:, ys, xs]))
         check_scaled(f"final_T tile {t}", ft[ys, xs], out["final_T"][ys, xs],
                      out["final_T"][ys, xs] * np.maximum(1.0, 8 * out["terr"][ys, xs] / 1e-5),
-                     out["tallow"][ys, xs])
+                     out["tallow"][ys, xs], lit=out["final_T"][ys, xs])
         ok = (ncn[ys, xs] == out["n_contrib"][ys, xs]) | (
             (out["pix_ambig"][ys, xs] > 0) & (ncn[ys, xs] == out["nc_alt"][ys, xs]))
         assert ok.all(), f"n_contrib differs in tile {t}"
@@ -155,7 +156,8 @@ def test_fullsize_backward_on_sampled_splats(dev, full, tier):
     s = full["splats"]
     out = full["out"]
     assert np.abs(out["grad2d"][s]).max() > 0
-    check_scaled(f"grad2d {tier}", got[s], out["grad2d"][s], out["gscale"][s], out["gallow"][s])
+    check_scaled(f"grad2d {tier}", got[s], out["grad2d"][s], out["gscale"][s], out["gallow"][s],
+                 lit=out["glit"][s])
 
 
 def test_fullsize_backward_projection(dev, orc, full):
@@ -196,4 +198,5 @@ def test_fullsize_deterministic_backward(dev, full):
     np.testing.assert_array_equal(res[0], res[1])
     s = full["splats"]
     out = full["out"]
-    check_scaled("grad2d deterministic", res[0][s, :9], out["grad2d"][s], out["gscale"][s], out["gallow"][s])
+    check_scaled("grad2d deterministic", res[0][s, :9], out["grad2d"][s], out["gscale"][s], out["gallow"][s],
+                 lit=out["glit"][s])

@@ -189,9 +189,9 @@ def gpu_forward(dev, st_):
 
 def check_forward(name, got, out):
     check_scaled(f"{name} image", got["image"], out["image"], np.abs(out["image"]) * out["pix_widen"][None],
-                 out["iallow"])
+                 out["iallow"], lit=np.abs(out["image"]))
     check_scaled(f"{name} final_T", got["final_T"], out["final_T"],
-                 out["final_T"] * np.maximum(1.0, 8 * out["terr"] / 1e-5), out["tallow"])
+                 out["final_T"] * np.maximum(1.0, 8 * out["terr"] / 1e-5), out["tallow"], lit=out["final_T"])
     nc = got["n_contrib"]
     ok = (nc == out["n_contrib"]) | ((out["pix_ambig"] > 0) & (nc == out["nc_alt"]))
     assert ok.all(), f"{name} n_contrib: {(~ok).sum()} pixels differ"
@@ -232,12 +232,11 @@ def test_backward_matches_oracle(dev, orc, name, tier, store_T):
                      T(st_["g"]), grad, opts)
     got = N(grad)
     out = st_["out"]
-    worst = check_scaled(f"{name} {tier} grad2d", got[:, :9], out["grad2d"], out["gscale"], out["gallow"])
+    # at most 0.5 % of the elements may need an allowance or the widening
+    worst = check_scaled(f"{name} {tier} grad2d", got[:, :9], out["grad2d"], out["gscale"], out["gallow"],
+                         lit=out["glit"])
     assert np.all(got[:, 9:] == 0.0)
-    # the literal tolerance (no widening, no allowance) holds for almost all
-    lit = np.abs(got[:, :9] - out["grad2d"]) <= 1e-5 * out["glit"] + 1e-7
-    assert lit.mean() > 0.995, lit.mean()
-    print(f"{name} {tier} store_T={store_T}: worst/bound {worst:.3f}, literal-pass {lit.mean():.5f}")
+    print(f"{name} {tier} store_T={store_T}: worst/bound {worst:.3f}")
 
 
 def test_backward_accumulates_into_existing_values(dev, orc):
