@@ -84,6 +84,49 @@ __device__ __forceinline__ bool eval_splat_all(float u, float v, float A, float 
     return e.sigma >= 0.0f && e.alpha >= kAlphaMin;
 }
 
+// ---- two pixels of one column as float2 pairs -----------------------------
+// Blackwell's packed FP32 instructions (FFMA2 / FMUL2 / FADD2) evaluate both
+// components in one instruction, each rounded exactly as the scalar
+// operation: the pair functions below give, per component, the bits of the
+// scalar splat evaluation above.
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+struct SplatEval2 {
+    float dx, dxx;                   // shared by the two pixels (same column)
+    float2 dy, dyy, dxy, sigma, G, alpha;
+    bool capped0, capped1;
+};
+
+// Pixels (px, py0) and (px, py1), given as px and npy = (-py0, -py1).
+__device__ __forceinline__ void splat_sigma2(float u, float v, float A, float B, float C, float px, float2 npy,
+                                             SplatEval2& e) {
+    e.dx = __fsub_rn(u, px);
+    e.dxx = __fmul_rn(e.dx, e.dx);
+    e.dy = __fadd2_rn(bc2(v), npy);  // v - py: the negation is exact
+    e.dyy = __fmul2_rn(e.dy, e.dy);
+    e.dxy = __fmul2_rn(bc2(e.dx), e.dy);
+    const float2 q = __ffma2_rn(bc2(C), e.dyy, bc2(__fmul_rn(A, e.dxx)));
+    e.sigma = __ffma2_rn(bc2(0.5f), q, __fmul2_rn(bc2(B), e.dxy));
+}
+
+__device__ __forceinline__ void splat_alpha2(float o, SplatEval2& e) {
+    e.G = make_float2(__expf(-e.sigma.x), __expf(-e.sigma.y));
+    const float2 oG = __fmul2_rn(bc2(o), e.G);
+    e.capped0 = oG.x > kAlphaMax;
+    e.capped1 = oG.y > kAlphaMax;
+    e.alpha = make_float2(e.capped0 ? kAlphaMax : oG.x, e.capped1 ? kAlphaMax : oG.y);
+}
+
+// eval_splat_all for both pixels: whether each pair passes.
+__device__ __forceinline__ void eval_splat2_all(float u, float v, float A, float B, float C, float o, float px,
+                                                float2 npy, SplatEval2& e, bool& hit0, bool& hit1) {
+    splat_sigma2(u, v, A, B, C, px, npy, e);
+    splat_alpha2(o, e);
+    hit0 = e.sigma.x >= 0.0f && e.alpha.x >= kAlphaMin;
+    hit1 = e.sigma.y >= 0.0f && e.alpha.y >= kAlphaMin;
+}
+
 // pair step of the transposing reduce-scatter: lanes with bit b set keep y
 // and send x, the others keep x and send y; the kept value gains the
 // partner's copy of it.

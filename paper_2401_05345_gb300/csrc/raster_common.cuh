@@ -173,6 +173,10 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
         last[q] = 0;
         C[q][0] = C[q][1] = C[q][2] = 0.0f;
     }
+    // two pixels per thread share their column (Shape::pixel): their
+    // transmittance and colour run as float2 pairs
+    float2 T2 = bc2(1.0f), C2[3] = {bc2(0.0f), bc2(0.0f), bc2(0.0f)};
+    const float2 npy = make_float2(-py[0], -py[PPT - 1]);
     for (int base = 0; base < n; base += SH::B) {
         if (__syncthreads_count(all_done) == SH::NT) break;
         const int cnt = min(SH::B, n - base);
@@ -188,30 +192,64 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
                 bits &= bits - 1u;
                 const float4 a = s_a[k], b = s_b[k];
                 const float cz = COLOR ? s_c[k] : 0.0f;
-#pragma unroll
-                for (int q = 0; q < PPT; ++q) {
-                    // no branches: a pixel that is done or skips the splat
-                    // keeps T, last and C (its blend weight is 0)
-                    SplatEval e;
-                    const bool hit = eval_splat_all(a.x, a.y, a.z, a.w, b.x, b.y, px[q], py[q], e) && !done[q];
-                    const float testT = __fmul_rn(T[q], __fsub_rn(1.0f, e.alpha));
-                    const bool stop = hit && testT < kTMin;
-                    const bool take = hit && !stop;
-                    done[q] = done[q] || stop;
+                // no branches: a pixel that is done or skips the splat keeps
+                // T, last and C (its blend weight is 0)
+                if constexpr (PPT == 2) {
+                    SplatEval2 e;
+                    bool hit0, hit1;
+                    eval_splat2_all(a.x, a.y, a.z, a.w, b.x, b.y, px[0], npy, e, hit0, hit1);
+                    hit0 = hit0 && !done[0];
+                    hit1 = hit1 && !done[1];
+                    const float2 testT = __fmul2_rn(T2, __fadd2_rn(bc2(1.0f), neg2(e.alpha)));
+                    const bool stop0 = hit0 && testT.x < kTMin, stop1 = hit1 && testT.y < kTMin;
+                    const bool take0 = hit0 && !stop0, take1 = hit1 && !stop1;
+                    done[0] = done[0] || stop0;
+                    done[1] = done[1] || stop1;
                     if (COLOR) {
-                        const float wgt = take ? __fmul_rn(e.alpha, T[q]) : 0.0f;
-                        C[q][0] = __fmaf_rn(b.z, wgt, C[q][0]);
-                        C[q][1] = __fmaf_rn(b.w, wgt, C[q][1]);
-                        C[q][2] = __fmaf_rn(cz, wgt, C[q][2]);
+                        const float2 aT = __fmul2_rn(e.alpha, T2);
+                        const float2 wgt = make_float2(take0 ? aT.x : 0.0f, take1 ? aT.y : 0.0f);
+                        C2[0] = __ffma2_rn(bc2(b.z), wgt, C2[0]);
+                        C2[1] = __ffma2_rn(bc2(b.w), wgt, C2[1]);
+                        C2[2] = __ffma2_rn(bc2(cz), wgt, C2[2]);
                     }
-                    T[q] = take ? testT : T[q];
-                    last[q] = take ? base + k + 1 : last[q];
+                    T2 = make_float2(take0 ? testT.x : T2.x, take1 ? testT.y : T2.y);
+                    last[0] = take0 ? base + k + 1 : last[0];
+                    last[1] = take1 ? base + k + 1 : last[1];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) {
+                        SplatEval e;
+                        const bool hit = eval_splat_all(a.x, a.y, a.z, a.w, b.x, b.y, px[q], py[q], e) && !done[q];
+                        const float testT = __fmul_rn(T[q], __fsub_rn(1.0f, e.alpha));
+                        const bool stop = hit && testT < kTMin;
+                        const bool take = hit && !stop;
+                        done[q] = done[q] || stop;
+                        if (COLOR) {
+                            const float wgt = take ? __fmul_rn(e.alpha, T[q]) : 0.0f;
+                            C[q][0] = __fmaf_rn(b.z, wgt, C[q][0]);
+                            C[q][1] = __fmaf_rn(b.w, wgt, C[q][1]);
+                            C[q][2] = __fmaf_rn(cz, wgt, C[q][2]);
+                        }
+                        T[q] = take ? testT : T[q];
+                        last[q] = take ? base + k + 1 : last[q];
+                    }
                 }
             }
             all_done = true;
 #pragma unroll
             for (int q = 0; q < PPT; ++q) all_done &= done[q];
             wdone = __all_sync(kFull, all_done);
+        }
+    }
+    if constexpr (PPT == 2) {
+        T[0] = T2.x;
+        T[1] = T2.y;
+        if (COLOR) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                C[0][ch] = C2[ch].x;
+                C[1][ch] = C2[ch].y;
+            }
         }
     }
 }
@@ -398,6 +436,43 @@ __device__ __forceinline__ void pair_grads(const SplatEval& e, float4 a, float4 
     }
 }
 
+// pair_grads for the two pixels of one column as float2 pairs (Blackwell's
+// packed FFMA2 / FMUL2 / FADD2): per component the operations of pair_grads,
+// so the bits of two scalar calls.  act0 / act1 select the active pairs
+// (alpha and G enter as 0 otherwise); the 9 sums of the two pixels are
+// written to v.
+__device__ __forceinline__ void pair_grads2(const SplatEval2& e, bool act0, bool act1, float4 a, float4 b, float cb,
+                                            float2 g0, float2 g1, float2 g2, float2& T, float2& S, float* v) {
+    const float2 al = make_float2(act0 ? e.alpha.x : 0.0f, act1 ? e.alpha.y : 0.0f);
+    // G for dL/do: 0 where the pair is inactive or alpha is capped
+    const float2 Gd = make_float2(act0 && !e.capped0 ? e.G.x : 0.0f, act1 && !e.capped1 ? e.G.y : 0.0f);
+    const float2 d = __fadd2_rn(bc2(1.0f), neg2(al));
+    float2 inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv.x) : "f"(d.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv.y) : "f"(d.y));
+    inv = __ffma2_rn(inv, __ffma2_rn(neg2(d), inv, bc2(1.0f)), inv);
+    const float2 Tj = __fmul2_rn(T, inv);
+    const float2 cg = __ffma2_rn(bc2(b.z), g0, __ffma2_rn(bc2(b.w), g1, __fmul2_rn(bc2(cb), g2)));
+    const float2 dal = __ffma2_rn(Tj, cg, neg2(__fmul2_rn(S, inv)));
+    const float2 w = __fmul2_rn(al, Tj);
+    S = __ffma2_rn(cg, w, S);
+    T = Tj;
+    const float2 dop = __fmul2_rn(Gd, dal);
+    const float2 dsig = __fmul2_rn(bc2(-b.y), dop);
+    const float2 hd = __fmul2_rn(bc2(0.5f), dsig);
+    const float2 du = __ffma2_rn(bc2(a.z), bc2(e.dx), __fmul2_rn(bc2(a.w), e.dy));
+    const float2 dv = __ffma2_rn(bc2(a.w), bc2(e.dx), __fmul2_rn(bc2(b.x), e.dy));
+    v[6] = fmaf(w.y, g0.y, w.x * g0.x);
+    v[7] = fmaf(w.y, g1.y, w.x * g1.x);
+    v[8] = fmaf(w.y, g2.y, w.x * g2.x);
+    v[5] = dop.x + dop.y;
+    v[0] = fmaf(du.y, dsig.y, du.x * dsig.x);
+    v[1] = fmaf(dv.y, dsig.y, dv.x * dsig.x);
+    v[2] = fmaf(e.dxx, hd.y, e.dxx * hd.x);
+    v[3] = fmaf(e.dxy.y, dsig.y, e.dxy.x * dsig.x);
+    v[4] = fmaf(e.dyy.y, hd.y, e.dyy.x * hd.x);
+}
+
 // Backward of one tile: the gradient-computation step (Sec. III-A) for the
 // tile's pixels, accumulated by the tier MODE.  All threads of the CTA call
 // it; shared storage is reused across calls.
@@ -466,6 +541,11 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
     const int maxlast = sm.maxlast;
     const int rparam = reduce9_param(lane);
     float* __restrict__ grad = p.grad2d;
+    // two pixels per thread share their column (Shape::pixel): packed state
+    const float2 npy2 = make_float2(-fpy[0], -fpy[PPT - 1]);
+    float2 T2 = make_float2(T[0], T[PPT - 1]), S2 = make_float2(S[0], S[PPT - 1]);
+    const float2 g0_2 = make_float2(g0[0], g0[PPT - 1]), g1_2 = make_float2(g1[0], g1[PPT - 1]),
+                 g2_2 = make_float2(g2[0], g2[PPT - 1]);
     unsigned long long cnt_red = 0, cnt_red4 = 0, cnt_add = 0, cnt_lane = 0, cnt_step = 0, cnt_act = 0;
 
     for (int top = maxlast; top > 0; top -= B) {
@@ -499,16 +579,26 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& p, const int tile, 
                     // and adds only zeros
                     float v[9];
                     bool any = false;
+                    if constexpr (PPT == 2) {
+                        SplatEval2 e;
+                        bool act0, act1;
+                        eval_splat2_all(a.x, a.y, a.z, a.w, b.x, b.y, fpx[0], npy2, e, act0, act1);
+                        act0 = act0 && pos < last[0];
+                        act1 = act1 && pos < last[1];
+                        pair_grads2(e, act0, act1, a, b, cb, g0_2, g1_2, g2_2, T2, S2, v);
+                        any = act0 || act1;
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < PPT; ++q) {
-                        SplatEval e;
-                        const bool act =
-                            eval_splat_all(a.x, a.y, a.z, a.w, b.x, b.y, fpx[q], fpy[q], e) && (pos < last[q]);
-                        e.alpha = act ? e.alpha : 0.0f;
-                        e.G = act ? e.G : 0.0f;
-                        if (q == 0) pair_grads<true>(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
-                        else pair_grads<false>(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
-                        any |= act;
+                        for (int q = 0; q < PPT; ++q) {
+                            SplatEval e;
+                            const bool act =
+                                eval_splat_all(a.x, a.y, a.z, a.w, b.x, b.y, fpx[q], fpy[q], e) && (pos < last[q]);
+                            e.alpha = act ? e.alpha : 0.0f;
+                            e.G = act ? e.G : 0.0f;
+                            if (q == 0) pair_grads<true>(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
+                            else pair_grads<false>(e, a, b, cb, g0[q], g1[q], g2[q], T[q], S[q], v);
+                            any |= act;
+                        }
                     }
                     if (MODE == kModeCount) {
                         const unsigned m = __ballot_sync(kFull, any);
