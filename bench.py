@@ -394,7 +394,7 @@ def large_scene_autograd(dev, flush, reps=5):
         out[f"step_peak_mb_{key}"] = (torch.cuda.max_memory_allocated(dev) - base) / 2 ** 20
     out["per_pixel_state_mb_saved"] = 8.0 * cam.width * cam.height / 2 ** 20
     out["note"] = ("per step: projection, synchronous binning, forward, torch L1, backward, backward projection, "
-                   "torch activation backward; view buffers allocated per call by the Function")
+                   "torch activation backward; the view buffers come from the settings' pool (allocated by the untimed first step)")
     return out
 
 
@@ -475,6 +475,20 @@ def l2_time_model(counts, tier, threshold, lane_rates):
         else:
             t += n * 9 * a / lane_rates["sparse"][a]
     return t
+
+
+def run_leg(argv, timeout_s):
+    """Runs ``python argv`` from the repository root and returns the JSON
+    object of its last output line, or {"error": ...}."""
+    try:
+        r = subprocess.run([sys.executable, *argv], cwd=ROOT, capture_output=True, text=True, timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        return {"error": f"timed out after {timeout_s} s"}
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    if r.returncode != 0 or not lines:
+        tail = (r.stderr or r.stdout).strip().splitlines()[-3:]
+        return {"error": f"exit {r.returncode}: " + " | ".join(tail)}
+    return json.loads(lines[-1])
 
 
 def run_ours(args):
@@ -660,6 +674,15 @@ def run_ours(args):
             vb, bg, R.dimg, gsr.backward_opts("hybrid", thr, lay, True, ppt), 5, flush)
 
     large = large_scene_autograd(dev, flush) if args.workload == "single_view" else None
+    # the batched persistent launch (4 scenes, 32 views) and the serving loop
+    # (16 concurrent scene-fitting jobs), each in a process of its own on this
+    # GPU after the timed steps (a fresh allocator and context per workload)
+    batched_res, serving_res = None, None
+    if args.workload == "single_view" and world == 1:
+        if not args.no_batched:
+            batched_res = run_leg(["-m", "paper_2401_05345_gb300.batched"], 600)
+        if not args.no_serving:
+            serving_res = run_leg(["-m", "paper_2401_05345_gb300.serving", "--steps", str(args.serving_steps)], 900)
 
     # L2 atomic (red) throughput, the roofline of the atomic accumulation:
     # every access pattern at 1-8 CTAs of 256 threads per SM; the peak is
@@ -898,6 +921,8 @@ def run_ours(args):
             "l2_red_adds_per_s": red,
             "traffic_counts_red": {"plain": rc_plain, "best": rc_best},
             "differentiation_large": large,
+            "batched": batched_res,
+            "serving": serving_res,
             "divergent_accumulation_ms": {"items": n_items, "records": rows,
                                           "by_distinct_destinations_per_warp": scat},
             "traffic_counts": {"P_active": p_active, "P_examined": p_exam, "P_ts": vb.n_keys,
@@ -955,6 +980,9 @@ def main():
     ap.add_argument("--opts", default="hybrid-thr24-lay1-ppt2", help="backward tier of a --profile run")
     ap.add_argument("--profile-tiers", action="store_true",
                     help="--profile: then one backward launch per autotune candidate")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched persistent-launch leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serving-steps", type=int, default=125, help="steps per job of the serving leg")
     ap.add_argument("--ingest-traffic", metavar="CSV",
                     help="write profiles/backward_traffic.json from the ncu CSV of a --profile-tiers capture")
     args = ap.parse_args()

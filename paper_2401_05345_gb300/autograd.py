@@ -29,6 +29,19 @@ class RasterSettings:
     store_T: bool = True
     key_capacity: int | None = None
     deterministic: bool = False   # atomic-free backward: bit-identical gradients run to run
+    # view buffers free for reuse, by (Gaussians, device); a forward takes
+    # one (or allocates) and its backward gives it back, so a training loop
+    # allocates once while views rendered before any backward get their own
+    pool: dict = dataclasses.field(default_factory=dict, repr=False, compare=False)
+
+    def take_buffers(self, n, device) -> ViewBuffers:
+        free = self.pool.get((int(n), str(device)))
+        if free:
+            return free.pop()
+        return ViewBuffers(n, self.cam, device, self.key_capacity, self.store_T)
+
+    def give_back(self, vb: ViewBuffers):
+        self.pool.setdefault((int(vb.n), str(vb.device)), []).append(vb)
 
 
 class _Rasterize(torch.autograd.Function):
@@ -36,10 +49,9 @@ class _Rasterize(torch.autograd.Function):
     def forward(ctx, mean, scale, quat, opacity, feat, sh_degree, settings):
         sc = SceneTensors(mean.contiguous(), scale.contiguous(), quat.contiguous(), opacity.contiguous(),
                           feat.contiguous(), int(sh_degree))
-        vb = ViewBuffers(sc.n, settings.cam, mean.device, settings.key_capacity, settings.store_T)
+        vb = settings.take_buffers(sc.n, mean.device)
         vb.preprocess(sc, zero_grad=True)
         vb.bin()
-        vb.release_scratch()
         vb.forward(settings.bg)
         ctx.vb = vb
         ctx.settings = settings
@@ -63,6 +75,7 @@ class _Rasterize(torch.autograd.Function):
         g = sc.zeros_like_params()
         vb.backward_project(sc, g)
         ctx.vb = None
+        st.give_back(vb)
         return g.mean, g.scale, g.quat, g.opacity, g.feat, None, None
 
 

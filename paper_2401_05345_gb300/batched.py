@@ -209,29 +209,26 @@ def autotune_batched(bv: BatchedViews, reps=3, flush=None):
     return best[0], best[1], best[2], table
 
 
-def main():
-    """Batched-backward benchmark: the 4-scene / 32-view workload, autotuned
-    persistent launch replayed from a CUDA graph, against one backward launch
-    per view with the same tier and with the plain atomicAdd tier."""
-    import json
-
+def benchmark(dev, flush=None):
+    """Batched-backward measurement on the 4-scene / 32-view workload: the
+    autotuned persistent launch replayed from a CUDA graph, against one
+    backward launch per view with the same tier and with the plain atomicAdd
+    tier (median of 5, L2 flushed before each when ``flush`` is given)."""
     from . import scenes as S
-    dev = torch.device("cuda")
     scenes, jobs = S.batched_workload(0)
     st = [SceneTensors.from_scene(s, dev) for s in scenes]
     bv = BatchedViews(st, jobs, dev, (0.0, 0.0, 0.0))
     targets = [torch.from_numpy(S.target_image(i, cam.width, cam.height)).to(dev) for i, (_, cam) in enumerate(jobs)]
     bv.render_all(targets)
     torch.cuda.synchronize()
-    flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev)
-    flush = lambda: flush_buf.fill_(1.0)  # noqa: E731  (256 MiB: more than the L2)
     opts, cps, best_ms, table = autotune_batched(bv, reps=5, flush=flush)
 
     def per_view(o, reps=5):
         ts = []
         for _ in range(reps):
             bv.zero_grad2d()
-            flush()
+            if flush:
+                flush()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             bv.backward_per_view(o)
@@ -240,13 +237,21 @@ def main():
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
     keys = sum(vb.n_keys for vb in bv.vbs)
-    print(json.dumps({
-        "workload": f"{len(scenes)} scenes ({', '.join(str(s.n) for s in scenes)} Gaussians, SH3), {len(jobs)} views "
-                    f"at 256x256 / 800x800 / 1297x840 / 1920x1080, {keys} list entries",
-        "graph_persistent_ms": best_ms, "best": f"{gsr_opts_tuple(opts)} ctas_per_sm {cps}",
-        "per_view_launches_same_tier_ms": per_view(opts),
-        "per_view_launches_plain_ms": per_view(gsr.backward_opts("plain", 0, 1)),
-        "autotune_ms": table}))
+    same, plain = per_view(opts), per_view(gsr.backward_opts("plain", 0, 1))
+    return {"workload": f"{len(scenes)} scenes ({', '.join(str(s.n) for s in scenes)} Gaussians, SH3), {len(jobs)} "
+                        f"views at 256x256 / 800x800 / 1297x840 / 1920x1080, {keys} list entries",
+            "graph_persistent_ms": best_ms, "best": f"{gsr_opts_tuple(opts)} ctas_per_sm {cps}",
+            "per_view_launches_same_tier_ms": same, "per_view_launches_plain_ms": plain,
+            "speedup_graph_vs_per_view_plain": plain / best_ms, "speedup_graph_vs_per_view_same_tier": same / best_ms,
+            "autotune_ms": table}
+
+
+def main():
+    """Prints the batched-backward measurement (see ``benchmark``)."""
+    import json
+    dev = torch.device("cuda")
+    flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    print(json.dumps(benchmark(dev, lambda: flush_buf.fill_(1.0))))  # 256 MiB: more than the L2
 
 
 if __name__ == "__main__":

@@ -392,7 +392,10 @@ rects_kernel(int n, Geom g, const float* __restrict__ splat2d, const int* __rest
         int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
         if (k < n) {
             const uint32_t id = order[k];
-            const int r = radius[id];
+            // an id out of range means the depth sort found inconsistent
+            // counts (flagged): the Gaussian is left out, nothing is read
+            if (id >= (uint32_t)n) atomicOr(&info[1], 2u);
+            const int r = id < (uint32_t)n ? radius[id] : 0;
             if (r > 0) {
                 const float2 uv = *reinterpret_cast<const float2*>(splat2d + (size_t)id * GSR_REC);
                 tile_rect(uv.x, uv.y, r, g.gx, g.gy, g.twl, g.thl, x0, x1, y0, y1);
@@ -571,7 +574,7 @@ __device__ __forceinline__ void walk_rows(WarpBatch& wb, int lane, int n, uint32
 __global__ void __launch_bounds__(kPlaceThreads)
 chunk_hist_kernel(int n, int nb, Geom g, int t0, int tw, const uint2* __restrict__ rects,
                   const uint32_t* __restrict__ apre, const uint32_t* __restrict__ boff,
-                  const uint32_t* __restrict__ wstart, const uint32_t* __restrict__ info, uint32_t* __restrict__ m) {
+                  const uint32_t* __restrict__ wstart, uint32_t* __restrict__ info, uint32_t* __restrict__ m) {
     extern __shared__ uint32_t h[];  // [(tw + 1) / 2] packed 16-bit counts (a block holds < 65536 entries)
     __shared__ WarpBatch s_wb[kPlaceWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -583,10 +586,12 @@ chunk_hist_kernel(int n, int nb, Geom g, int t0, int tw, const uint2* __restrict
     const int nwarps = nb * kPlaceWarps;
     const uint32_t ew = warp_entries(total, nwarps);
     const unsigned long long e0l = (unsigned long long)(b * kPlaceWarps + w) * ew;
-    if (e0l < total) {
+    const int kw = e0l < total ? (int)wstart[b * kPlaceWarps + w] : n;
+    if (e0l < total && (unsigned)kw >= (unsigned)n) atomicOr(&info[1], 4u);  // flagged: the ranges stay empty
+    if (e0l < total && (unsigned)kw < (unsigned)n) {  // a start out of range: counts inconsistent, nothing read
         const uint32_t e0 = (uint32_t)e0l;
         const uint32_t e1 = total - e0 < ew ? total : e0 + ew;
-        const int k = (int)wstart[b * kPlaceWarps + w];
+        const int k = kw;
         walk_rows<false>(s_wb[w], lane, n, e0, e1, k, rects, nullptr, nullptr, entry_prefix(apre, boff, k), g, t0,
                          [&](bool ok, const RowWork& r) {
                              if (!ok) return;
@@ -626,10 +631,11 @@ place_kernel(int n, int nb, Geom g, int t0, int tw, uint32_t cap, const uint32_t
     const uint32_t total = info[4];
     const uint32_t ew = warp_entries(total, nb * kPlaceWarps);
     const unsigned long long e0l = (unsigned long long)(b * kPlaceWarps + w) * ew;
-    const bool mine = e0l < total;
+    const int kw = e0l < total ? (int)wstart[b * kPlaceWarps + w] : n;
+    const bool mine = e0l < total && (unsigned)kw < (unsigned)n;
     const uint32_t e0 = mine ? (uint32_t)e0l : 0u;
     const uint32_t e1 = !mine ? 0u : (total - e0 < ew ? total : e0 + ew);
-    const int k = mine ? (int)wstart[b * kPlaceWarps + w] : 0;
+    const int k = mine ? kw : 0;
     const uint32_t pk = mine ? entry_prefix(apre, boff, k) : 0u;
     WarpBatch& wb = s_wb[w];
     uint32_t* wc = s_cnt + (size_t)w * tw2;

@@ -134,7 +134,7 @@ extern "C" const char* gsr_status_string(int status) {
         case GSR_EINVAL: return "invalid argument";
         case GSR_ECAPACITY: return "duplicated keys exceed key_capacity";
         case GSR_ECUDA: return "CUDA error";
-        case GSR_ETIMEOUT: return "bounded device wait timed out";
+        case GSR_ETIMEOUT: return "reserved status (no call waits on the device)";
         case GSR_ESCRATCH: return "scratch buffer too small";
         case GSR_ELIMIT: return "size exceeds the fixed limit of the allocation-free variant";
         default: return "unknown status";

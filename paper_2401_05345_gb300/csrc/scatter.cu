@@ -13,12 +13,15 @@ __device__ __forceinline__ void load9(const float* __restrict__ v, float* x) {
 }
 
 // PLAIN: one atomic add per parameter per item.
-// SERIAL: lanes with the same destination are found with match_any; a group
-//   of at least `threshold` lanes is summed by its lowest lane, which pulls
-//   each peer's 9 values in turn (all parameters per peer) and sends the
-//   record's reds; smaller groups send each lane's reds to L2.  The reduced
-//   methods send a record as two vector reds and one scalar red when rows are
-//   16-byte aligned, else as 9 scalar reds.
+// SERIAL: the lanes of a warp that share a destination form a group (a
+//   match mask); a group of at least `threshold` lanes is reduced at the SM
+//   (Sec. V-A1: one sum per destination instead of one atomic per lane),
+//   smaller groups send each lane's reds to L2.  A reduced group shares its 9
+//   parameters among its own lanes: every lane stages its values in shared
+//   memory, and the lane of rank r in a group of g sums parameters r, r + g,
+//   ... over the group's members (in lane order) and sends their reds.
+//   Unreduced lanes send a record as two vector reds and one scalar red when
+//   rows are 16-byte aligned, else as 9 scalar reds.
 // SORTED: the warp's (destination, lane) pairs are sorted with a bitonic
 //   network in registers, each lane fetches the values of its sorted
 //   position, and a 5-step segmented shuffle scan leaves every group's total
@@ -58,28 +61,28 @@ scatter9_kernel(long long n, const uint32_t* __restrict__ idx, const float* __re
         }
         return;
     }
-    if (METHOD == 1) {
+    if constexpr (METHOD == 1) {
+        __shared__ float s_x[8][32 * 9];  // per warp: lane-major values (stride 9: no bank conflicts)
+        float* wx = s_x[threadIdx.x >> 5];
         const unsigned act = __ballot_sync(kFull, valid);
         const unsigned same = __match_any_sync(kFull, d) & act;
+        const int g = __popc(same);
+        const bool reduced = valid && g >= threshold;
+        const unsigned red_lanes = __ballot_sync(kFull, reduced);
         if (!valid) return;
         float* rec = out + (size_t)d * stride;
-        if (__popc(same) >= threshold) {
-            const int leader = __ffs(same) - 1;
-            unsigned peers = same & ~(1u << leader);
-            // every lane of the group takes part in each pull (the same
-            // sequence of sources in the whole group), the leader keeps the sums
-            while (peers) {
-                const int src = __ffs(peers) - 1;
-                peers &= peers - 1u;
-#pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const float y = __shfl_sync(same, x[q], src);
-                    if (lane == leader) x[q] += y;
-                }
-            }
-            if (lane == leader) red9<VEC>(rec, x);
-        } else {
+        if (!reduced) {
             red9<VEC>(rec, x);
+            return;
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) wx[lane * 9 + q] = x[q];
+        __syncwarp(red_lanes);
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        for (int q = rank; q < 9; q += g) {
+            float sum = 0.0f;
+            for (unsigned m = same; m; m &= m - 1u) sum += wx[(__ffs(m) - 1) * 9 + q];
+            red_add(rec + q, sum);
         }
         return;
     }

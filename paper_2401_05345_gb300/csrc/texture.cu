@@ -98,6 +98,7 @@ cube_backward_kernel(int W, int H, const float* __restrict__ dirs, const float* 
                      float* __restrict__ grad, int threshold) {
     __shared__ uint32_t s_key[METHOD == GSR_TEX_BLOCK ? kTexSlots : 1];
     __shared__ float4 s_val[METHOD == GSR_TEX_BLOCK ? kTexSlots : 1];
+    __shared__ float4 s_stage[METHOD == GSR_TEX_SERIAL ? kTexThreads / 32 : 1][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int gxt = (W + kTexTile - 1) / kTexTile;
     const int px = (blockIdx.x % gxt) * kTexTile + (w & 1) * 8 + (lane & 7);
@@ -135,28 +136,29 @@ cube_backward_kernel(int W, int H, const float* __restrict__ dirs, const float* 
         } else if (METHOD == GSR_TEX_PLAIN_V4) {
             if (valid) red_add_v4(dst, a, b, c, 0.0f);
         } else if (METHOD == GSR_TEX_SERIAL) {
+            // lanes with the same texel form a group (match mask); a group of
+            // at least `threshold` lanes is reduced at the SM (Sec. V-A1):
+            // its lanes stage their values in shared memory and the group's
+            // lowest lane adds them in lane order and sends one v4 red;
+            // smaller groups send one v4 red per lane
             const unsigned peers = __match_any_sync(kFull, key) & vmask;
-            if (valid) {
-                if (__popc(peers) >= threshold) {
-                    // the group's lanes pull the same sequence of peers; the
-                    // lowest lane keeps the sums and issues one red
-                    const int leader = __ffs(peers) - 1;
-                    unsigned rest = peers & ~(1u << leader);
-                    float sa = a, sb = b, sc = c;
-                    while (rest) {
-                        const int src = __ffs(rest) - 1;
-                        rest &= rest - 1u;
-                        const float xa = __shfl_sync(peers, a, src);
-                        const float xb = __shfl_sync(peers, b, src);
-                        const float xc = __shfl_sync(peers, c, src);
-                        sa += xa;
-                        sb += xb;
-                        sc += xc;
+            const bool reduced = valid && __popc(peers) >= threshold;
+            const unsigned rl = __ballot_sync(kFull, reduced);
+            if (valid && !reduced) red_add_v4(dst, a, b, c, 0.0f);
+            if (reduced) {
+                s_stage[w][lane] = make_float4(a, b, c, 0.0f);
+                __syncwarp(rl);
+                if (lane == __ffs(peers) - 1) {
+                    float sa = 0.0f, sb = 0.0f, sc = 0.0f;
+                    for (unsigned m = peers; m; m &= m - 1u) {
+                        const float4 v = s_stage[w][__ffs(m) - 1];
+                        sa += v.x;
+                        sb += v.y;
+                        sc += v.z;
                     }
-                    if (lane == leader) red_add_v4(dst, sa, sb, sc, 0.0f);
-                } else {
-                    red_add_v4(dst, a, b, c, 0.0f);
+                    red_add_v4(dst, sa, sb, sc, 0.0f);
                 }
+                __syncwarp(rl);  // read before the next tap restages
             }
         } else if (METHOD == GSR_TEX_SORTED) {
             uint32_t sk = key, src = (uint32_t)lane;

@@ -146,7 +146,8 @@ class ViewBuffers:
 
     def apply_bin_status(self, cnt, status) -> bool:
         """``check_bin`` on a (key count, status) pair the caller already
-        copied to the host."""
+        copied to the host.  Grown buffers are allocated and zeroed on the
+        current stream: make it the stream of their next use."""
         cnt, status = int(cnt), int(status)
         self.n_keys = cnt
         if status == 0:

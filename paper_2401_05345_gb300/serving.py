@@ -14,6 +14,14 @@ admitted.
   the ``slots`` CUDA streams is idle, the oldest ready request (its job
   admitted and not already stepping) is issued on it, so steps of different
   jobs overlap on the device and new arrivals join while others run.
+* Checkpoint and readmission: with ``evict_after`` set, a new waiting job
+  that does not fit and has waited that long makes the scheduler evict idle
+  admitted jobs (oldest admission first, each after at least ``quantum``
+  steps since its admission) when that frees enough memory.  An evicted
+  job's parameters, Adam moments and Adam step count go to pinned host
+  memory; it rejoins the waiting list and is restored from that checkpoint
+  when it is admitted again, so its steps continue exactly where they
+  stopped.
 * Latency of a request = device completion time - arrival time (queueing
   included); p50 / p99 and steps/s are reported.
 
@@ -46,6 +54,10 @@ class Job:
     done_steps: int = 0
     busy: bool = False
     payload: object = None     # executor data (scene, camera, targets)
+    waiting_since: float = 0.0  # when the job last entered the waiting list
+    admitted_at: float = 0.0
+    steps_at_admit: int = 0
+    evictions: int = 0
 
 
 @dataclasses.dataclass(order=True)
@@ -66,11 +78,16 @@ class Result:
 
 
 class Scheduler:
-    """Admission by footprint and continuous batching over ``slots``."""
+    """Admission by footprint and continuous batching over ``slots``;
+    eviction of idle admitted jobs for a waiting one (``evict_after``
+    seconds of waiting, None = never; an admitted job runs ``quantum`` steps
+    before it may be evicted)."""
 
-    def __init__(self, budget_bytes: int, slots: int):
+    def __init__(self, budget_bytes: int, slots: int, evict_after=None, quantum: int = 1):
         self.budget = int(budget_bytes)
         self.slots = int(slots)
+        self.evict_after = evict_after
+        self.quantum = max(1, int(quantum))
         self.jobs: dict[int, Job] = {}
         self.used = 0
         self.pending: list[Request] = []      # arrived, not issued (heap by arrival)
@@ -84,11 +101,13 @@ class Scheduler:
             job.state = "refused"
             self.events.append(f"refuse {job.job_id}")
             return False
+        job.waiting_since = job.arrival
         self.waiting.append(job.job_id)
         return True
 
-    def admit(self, on_admit):
-        """First-fit admission in arrival order."""
+    def admit(self, on_admit, now=0.0):
+        """First-fit admission in arrival order (evicted jobs rejoin at the
+        end of the list)."""
         still = []
         for jid in self.waiting:
             job = self.jobs[jid]
@@ -97,12 +116,53 @@ class Scheduler:
             if self.used + job.footprint <= self.budget:
                 on_admit(job)
                 job.state = "admitted"
+                job.admitted_at = now
+                job.steps_at_admit = job.done_steps
                 self.used += job.footprint
                 self.peak_used = max(self.peak_used, self.used)
                 self.events.append(f"admit {jid}")
             else:
                 still.append(jid)
         self.waiting = still
+
+    def maybe_evict(self, now, on_evict):
+        """Evicts idle admitted jobs for the first new waiting job (one that
+        has not run yet) that does not fit, once it has waited
+        ``evict_after`` seconds and if that frees enough memory for it.
+        Evicted jobs wait for memory like any other, so two jobs never evict
+        each other in turn.  Returns the evicted jobs."""
+        if self.evict_after is None:
+            return []
+        for jid in self.waiting:
+            job = self.jobs[jid]
+            if job.state != "waiting" or self.used + job.footprint <= self.budget:
+                continue  # admit() takes the ones that fit
+            if job.done_steps or job.evictions:
+                continue
+            if now - job.waiting_since < self.evict_after:
+                return []
+            cands = sorted((j for j in self.jobs.values()
+                            if j.state == "admitted" and not j.busy and j.done_steps < j.steps
+                            and j.done_steps - j.steps_at_admit >= self.quantum),
+                           key=lambda j: (j.admitted_at, j.job_id))
+            free, chosen = self.budget - self.used, []
+            for c in cands:
+                if free >= job.footprint:
+                    break
+                chosen.append(c)
+                free += c.footprint
+            if free < job.footprint:
+                return []
+            for c in chosen:
+                on_evict(c)
+                c.state = "waiting"
+                c.evictions += 1
+                c.waiting_since = now
+                self.used -= c.footprint
+                self.waiting.append(c.job_id)
+                self.events.append(f"evict {c.job_id}")
+            return chosen
+        return []
 
     def arrive(self, req: Request):
         job = self.jobs[req.job_id]
@@ -174,11 +234,28 @@ def percentile(xs, q):
     return float(np.percentile(np.asarray(xs, np.float64), q))
 
 
-def summarize(results, wall_s):
+def summarize(results, wall_s, requests=None):
+    """Latency percentiles and throughput.  With ``requests``, also the
+    time-averaged offered rate and a steady-state window: the span between
+    the 10th and the 90th percentile of arrival times, with the completions
+    per second inside it and the latency of the requests that arrived in it."""
     lat = [1e3 * (r.completed - r.arrival) for r in results]
-    return {"requests": len(results), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
-            "mean_ms": float(np.mean(lat)) if lat else float("nan"),
-            "steps_per_s": len(results) / wall_s if wall_s > 0 else float("nan"), "wall_s": wall_s}
+    out = {"requests": len(results), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+           "mean_ms": float(np.mean(lat)) if lat else float("nan"),
+           "steps_per_s": len(results) / wall_s if wall_s > 0 else float("nan"), "wall_s": wall_s}
+    if requests:
+        arr = np.sort(np.asarray([q.arrival for q in requests], np.float64))
+        span = arr[-1] - arr[0]
+        out["offered_per_s"] = (len(arr) - 1) / span if span > 0 else float("inf")
+        t_a, t_b = np.percentile(arr, 10), np.percentile(arr, 90)
+        if t_b > t_a:
+            done = np.asarray([r.completed for r in results], np.float64)
+            lw = [x for x, r in zip(lat, results) if t_a <= r.arrival <= t_b]
+            out["steady"] = {"window_s": float(t_b - t_a),
+                             "completed_per_s": float(((done >= t_a) & (done <= t_b)).sum() / (t_b - t_a)),
+                             "offered_per_s": float(((arr >= t_a) & (arr <= t_b)).sum() / (t_b - t_a)),
+                             "p50_ms": percentile(lw, 50), "p99_ms": percentile(lw, 99)}
+    return out
 
 
 def serve(scheduler: Scheduler, requests, executor, cancel_at=None, poll_sleep=0.0):
@@ -201,7 +278,10 @@ def serve(scheduler: Scheduler, requests, executor, cancel_at=None, poll_sleep=0
             if tc <= now and not scheduler.jobs[jid].busy:
                 scheduler.cancel(jid, executor.unload)
                 del cancel_at[jid]
-        scheduler.admit(executor.load)
+        evict = getattr(executor, "evict", None)
+        if evict is not None:
+            scheduler.maybe_evict(now, evict)
+        scheduler.admit(executor.load, now)
         while free_slots:
             r = scheduler.next_ready()
             if r is None:
@@ -285,6 +365,9 @@ class GpuExecutor:
         self.copy_stream = torch.cuda.Stream(device=device)
         self._unloading = []  # (job id, pinned host copy, event, device state)
         self._final_params = {}
+        self.checkpoints = {}  # job id -> (pinned host [P | M | V], Adam step count, copy event)
+        self._evicting = []    # (copy event, device state kept until the copy has finished)
+        self.evictions = 0
         self.t0_event = torch.cuda.Event(enable_timing=True)
         self.t0_event.record()
         self.t0_host = time.perf_counter()
@@ -303,9 +386,18 @@ class GpuExecutor:
         data = job.payload if isinstance(job.payload, JobData) else prepare_job_data(*job.payload)
         n, sizes, offs = data.n, data.sizes, data.offsets
         self._reap()
+        ckpt = self.checkpoints.pop(job.job_id, None)
         with torch.cuda.stream(self.copy_stream):
             P = torch.empty(data.params.numel(), dtype=torch.float32, device=self.device)
-            P.copy_(data.params, non_blocking=True)
+            if ckpt is None:
+                P.copy_(data.params, non_blocking=True)
+                M, V = torch.zeros_like(P), torch.zeros_like(P)
+            else:  # readmitted: parameters and moments from the checkpoint (ordered after its copy)
+                m = P.numel()
+                P.copy_(ckpt[0][:m], non_blocking=True)
+                M, V = torch.empty_like(P), torch.empty_like(P)
+                M.copy_(ckpt[0][m:2 * m], non_blocking=True)
+                V.copy_(ckpt[0][2 * m:], non_blocking=True)
             views = [P[offs[i]:offs[i] + sizes[i]] for i in range(5)]
             G = torch.zeros_like(P)
             gv = [G[offs[i]:offs[i] + sizes[i]] for i in range(5)]
@@ -314,7 +406,7 @@ class GpuExecutor:
                 d = torch.empty(t.shape, dtype=torch.float32, device=self.device)
                 d.copy_(t, non_blocking=True)
                 targets.append(d)
-            st = dict(P=P, G=G, M=torch.zeros_like(P), V=torch.zeros_like(P), pv=views, gv=gv, n=n,
+            st = dict(P=P, G=G, M=M, V=V, pv=views, gv=gv, n=n,
                       sh=data.sh_degree, scale=torch.empty(3 * n, device=self.device),
                       opac=torch.empty(n, device=self.device), dscale=torch.empty(3 * n, device=self.device),
                       dopac=torch.empty(n, device=self.device),
@@ -322,7 +414,8 @@ class GpuExecutor:
                                                    max(1024, int(self.key_capacity_per_gaussian * n))),
                       targets=targets, loss=torch.zeros(1, device=self.device),
                       loss_host=torch.zeros(1).pin_memory(),
-                      bin_host=torch.zeros(2, dtype=torch.int32).pin_memory(), adam_step=0)
+                      bin_host=torch.zeros(2, dtype=torch.int32).pin_memory(),
+                      adam_step=0 if ckpt is None else ckpt[1])
             st["dimg"] = torch.empty_like(st["vb"].image)
             st["ready"] = torch.cuda.Event()
             st["ready"].record(self.copy_stream)
@@ -345,9 +438,32 @@ class GpuExecutor:
             ev.record(self.copy_stream)
         self._unloading.append((job.job_id, host, ev, st))
 
+    def evict(self, job):
+        """Checkpoints an admitted, idle job: its parameters, Adam moments
+        and Adam step count go to pinned host memory (queued on the copy
+        stream after the job's last step); its device state is released once
+        that copy has finished.  ``load`` restores the job from it."""
+        torch = self.torch
+        st = self.loaded.pop(job.job_id)
+        m = st["P"].numel()
+        host = torch.empty(3 * m, dtype=torch.float32).pin_memory()
+        with torch.cuda.stream(self.copy_stream):
+            if "done" in st:
+                self.copy_stream.wait_event(st["done"])
+            host[:m].copy_(st["P"], non_blocking=True)
+            host[m:2 * m].copy_(st["M"], non_blocking=True)
+            host[2 * m:].copy_(st["V"], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.copy_stream)
+        self.checkpoints[job.job_id] = (host, st["adam_step"], ev)
+        self._evicting.append((ev, st))
+        self.evictions += 1
+
     def _reap(self, wait=False):
         """Moves finished final-parameter copies to final_params and drops
-        those jobs' device state."""
+        those jobs' device state (and that of evicted jobs whose checkpoint
+        copy has finished)."""
+        self._evicting = [(ev, st) for ev, st in self._evicting if not ev.query()]
         keep = []
         for jid, host, ev, st in self._unloading:
             if wait:
@@ -418,7 +534,11 @@ class GpuExecutor:
         st = h.st
         if h.phase == 1:
             cnt, status = (int(x) for x in st["bin_host"])
-            if st["vb"].apply_bin_status(cnt, status):
+            # grown key buffers are allocated (and zeroed) on the step's own
+            # stream, ordered before the rerun that uses them
+            with self.torch.cuda.stream(h.stream):
+                fitted = st["vb"].apply_bin_status(cnt, status)
+            if fitted:
                 self._phase2(h)
             else:  # key buffers grown: the lists of this step were empty, run it again
                 self.rebins += 1
@@ -478,56 +598,76 @@ def make_jobs(spec, seed=0):
 
 
 def run_serving(spec, slots, budget_bytes, opts, rate_per_job, seed=0, device="cuda", jobs=None,
-                deterministic=False, key_capacity_per_gaussian=16):
+                deterministic=False, key_capacity_per_gaussian=16, evict_after=None, quantum=1):
     ex = GpuExecutor(device, slots, opts, deterministic=deterministic,
                      key_capacity_per_gaussian=key_capacity_per_gaussian)
     jobs = jobs if jobs is not None else make_jobs(spec, seed)
     for j in jobs:
-        j.state, j.done_steps, j.busy = "waiting", 0, False
-    sch = Scheduler(budget_bytes, slots)
+        j.state, j.done_steps, j.busy, j.evictions = "waiting", 0, False, 0
+    sch = Scheduler(budget_bytes, slots, evict_after, quantum)
     for j in jobs:
         sch.add_job(j)
     reqs = poisson_requests(jobs, rate_per_job, seed + 999)
     wall0 = time.perf_counter()
     res = serve(sch, reqs, ex)
     wall = time.perf_counter() - wall0
-    return res, summarize(res, wall), ex, sch
+    return res, summarize(res, wall, reqs), ex, sch
+
+
+def job_spec(n_jobs, steps, seed=0, min_n=100_000, max_n=2_000_000, gap_s=0.05):
+    """The serving workload: N log-uniform in [min_n, max_n], SH degree 3,
+    alternating 1297x840 and 1920x1080 views, jobs arriving ``gap_s`` apart
+    on average (exponential gaps)."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(math.log(min_n), math.log(max_n), size=n_jobs)).astype(int)
+    arrivals = np.cumsum(rng.exponential(gap_s, size=n_jobs))
+    res_list = [(1297, 840), (1920, 1080)]
+    return [(int(ns[i]), steps, float(arrivals[i]), *res_list[i % 2]) for i in range(n_jobs)]
+
+
+SATURATED = 1e9  # requests per second per job: every request is there when its job arrives
+
+
+def benchmark(n_jobs=16, steps=125, rate=10.0, slots=4, budget_gb=24.0, seed=0):
+    """The serving measurement: continuous batching with the hybrid tier at
+    a Poisson load of ``rate`` requests/s per job and saturated, and the jobs
+    run one at a time with the plain atomicAdd tier, saturated (at the
+    offered load one job at a time serves only as fast as that job's own
+    requests arrive, about n_jobs * steps / rate seconds)."""
+    import torch
+
+    from . import gsr
+    spec = job_spec(n_jobs, steps, seed)
+    jobs = make_jobs(spec, seed)
+    budget = int(budget_gb * (1 << 30))
+    hybrid = gsr.backward_opts("hybrid", 24, 1, True, 2)
+    _, offered, _, sch = run_serving(spec, slots, budget, hybrid, rate, seed, jobs=jobs)
+    torch.cuda.synchronize()
+    _, sat, _, _ = run_serving(spec, slots, budget, hybrid, SATURATED, seed, jobs=jobs)
+    torch.cuda.synchronize()
+    one_budget = max(j.footprint for j in jobs)
+    _, seq, _, _ = run_serving(spec, 1, one_budget, gsr.backward_opts("plain", 0, 1), SATURATED, seed, jobs=jobs)
+    torch.cuda.synchronize()
+    return {"workload": f"{n_jobs} jobs, N log-uniform 100k-2M ({sum(j.n for j in jobs)} Gaussians in all), SH3, "
+                        f"1297x840 / 1920x1080, {steps} steps (render, L1, backward, backward projection, Adam) "
+                        f"each, jobs arriving about 50 ms apart",
+            "continuous_batching_hybrid": dict(offered, rate_per_job=rate, slots=slots, budget_gb=budget_gb,
+                                               peak_admitted_gb=sch.peak_used / (1 << 30)),
+            "continuous_batching_hybrid_saturated": sat,
+            "one_at_a_time_plain_saturated": seq}
 
 
 def main():
     import argparse
-
-    import torch
-
-    from . import gsr
-    ap = argparse.ArgumentParser(description="serving benchmark: 16 concurrent scene-fitting jobs")
+    ap = argparse.ArgumentParser(description="serving benchmark: concurrent scene-fitting jobs")
     ap.add_argument("--jobs", type=int, default=16)
-    ap.add_argument("--steps", type=int, default=12)
+    ap.add_argument("--steps", type=int, default=125)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=24.0)
-    ap.add_argument("--rate", type=float, default=20.0, help="step requests per second per job")
-    ap.add_argument("--min-n", type=int, default=100_000)
-    ap.add_argument("--max-n", type=int, default=2_000_000)
+    ap.add_argument("--rate", type=float, default=10.0, help="step requests per second per job")
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
-    rng = np.random.default_rng(args.seed)
-    ns = np.exp(rng.uniform(math.log(args.min_n), math.log(args.max_n), size=args.jobs)).astype(int)
-    arrivals = np.cumsum(rng.exponential(0.05, size=args.jobs))
-    res_list = [(1297, 840), (1920, 1080)]
-    spec = [(int(ns[i]), args.steps, float(arrivals[i]), *res_list[i % 2]) for i in range(args.jobs)]
-    jobs = make_jobs(spec, args.seed)
-    budget = int(args.budget_gb * (1 << 30))
-    _, cont, _, sch = run_serving(spec, args.slots, budget, gsr.backward_opts("hybrid", 24, 1, True, 2), args.rate,
-                                  args.seed, jobs=jobs)
-    torch.cuda.synchronize()
-    one_budget = max(j.footprint for j in jobs)
-    _, seq, _, _ = run_serving(spec, 1, one_budget, gsr.backward_opts("plain", 0, 1), args.rate, args.seed,
-                               jobs=jobs)
-    print(json.dumps({"workload": f"{args.jobs} jobs, N log-uniform {args.min_n}-{args.max_n}, SH3, "
-                                  f"1297x840 / 1920x1080, {args.steps} steps each, Poisson {args.rate}/s per job",
-                      "continuous_batching_hybrid": dict(cont, slots=args.slots, budget_gb=args.budget_gb,
-                                                         peak_admitted_gb=sch.peak_used / (1 << 30)),
-                      "one_at_a_time_plain": seq}))
+    print(json.dumps(benchmark(args.jobs, args.steps, args.rate, args.slots, args.budget_gb, args.seed)))
 
 
 if __name__ == "__main__":

@@ -317,3 +317,32 @@ def test_recompute_keeps_less_state(dev):
     a = ViewBuffers(1000, cam, dev, 1024, store_T=True)
     b = ViewBuffers(1000, cam, dev, 1024, store_T=False)
     assert a.device_bytes() - b.device_bytes() == 8 * 1920 * 1080
+
+
+def test_view_buffers_are_reused_between_steps(dev):
+    """The Function takes its view buffers from the settings' pool and gives
+    them back in the backward: a training loop allocates them once, and two
+    views rendered before one backward keep separate buffers."""
+    scene, cam = crop_workload()
+    w = torch.from_numpy(weights(cam.height, cam.width)).to(dev)
+    model = AG.GaussianModel(scene, dev)
+    st = AG.RasterSettings(cam, (0.1, 0.2, 0.3), gsr.backward_opts("warp", 0, 1, True, 2), True, deterministic=True)
+    grads = []
+    for _ in range(2):
+        model.zero_grad(set_to_none=True)
+        (model(st) * w).sum().backward()
+        grads.append([p.grad.clone() for p in model.parameters()])
+    (pool,) = st.pool.values()
+    assert len(pool) == 1
+    first = pool[0]
+    for a, b in zip(*grads):
+        assert torch.equal(a, b)
+    model.zero_grad(set_to_none=True)
+    img1 = model(st)
+    img2 = model(st)
+    assert len(pool) == 0
+    ((img1 + img2) * w).sum().backward()
+    assert len(pool) == 2 and any(vb is first for vb in pool)
+    torch.testing.assert_close(img1, img2, rtol=0, atol=0)
+    for a, p in zip(grads[0], model.parameters()):
+        assert torch.equal(p.grad, 2 * a)

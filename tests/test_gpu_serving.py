@@ -84,3 +84,27 @@ def test_key_buffer_overflow_reruns_the_render_phase(dev):
     for j in jobs:
         np.testing.assert_array_equal(ex_small.final_params[j.job_id], ex_ok.final_params[j.job_id])
         np.testing.assert_allclose(ex_small.loss_log[j.job_id], ex_ok.loss_log[j.job_id], rtol=1e-5)
+
+
+def test_evicted_job_resumes_bit_identical(dev):
+    """Checkpoint and readmission: the first job is evicted after two of its
+    steps for a larger one that does not fit beside it, goes to pinned host
+    memory (parameters, Adam moments, Adam step count) and is restored from
+    there once the larger job is done.  With the atomic-free backward, both
+    jobs end with the parameters of their runs alone, bit for bit."""
+    spec = [(20000, 6, 0.0, 160, 120), (40000, 3, 0.002, 200, 150)]
+    jobs = SV.make_jobs(spec, seed=9)
+    budget = max(j.footprint for j in jobs) + 1   # one job at a time
+    opts = gsr.backward_opts("warp", 0, 1, True, 2)
+    res, _, ex, sch = SV.run_serving(None, 2, budget, opts, 400.0, seed=9, device=dev, jobs=jobs,
+                                     deterministic=True, evict_after=0.0, quantum=2)
+    assert ex.evictions == 1 and "evict 0" in sch.events and sch.events.count("admit 0") == 2
+    assert len(res) == 9 and sch.peak_used <= budget
+    steps0 = [r.step for r in sorted(res, key=lambda r: r.completed) if r.job_id == 0]
+    assert steps0 == list(range(6))
+    for j in jobs:
+        alone = dataclasses.replace(j, state="waiting", done_steps=0, busy=False, evictions=0)
+        _, _, ex1, _ = SV.run_serving(None, 1, j.footprint, opts, 400.0, seed=9, device=dev, jobs=[alone],
+                                      deterministic=True)
+        np.testing.assert_array_equal(ex1.final_params[j.job_id], ex.final_params[j.job_id])
+        np.testing.assert_allclose(ex1.loss_log[j.job_id], ex.loss_log[j.job_id], rtol=1e-5)

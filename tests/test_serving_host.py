@@ -124,3 +124,88 @@ def test_footprint_model_matches_the_recorded_per_gaussian_state():
     a = SV.job_footprint(1000, 3, 16, 16)
     b = SV.job_footprint(2000, 3, 16, 16)
     assert b - a >= 944 * 1000
+
+
+class EvictingExecutor(FakeExecutor):
+    """Fake executor that also checkpoints: records evictions and which jobs
+    were loaded back from a checkpoint."""
+
+    def __init__(self, **kw):
+        super().__init__(**kw)
+        self.evicted, self.ckpt, self.restored = [], set(), []
+
+    def evict(self, job):
+        assert job.job_id not in self.inflight_jobs, "evicting a job with a step in flight"
+        self.evicted.append(job.job_id)
+        self.ckpt.add(job.job_id)
+
+    def load(self, job):
+        super().load(job)
+        if job.job_id in self.ckpt:
+            self.ckpt.discard(job.job_id)
+            self.restored.append(job.job_id)
+
+
+def test_eviction_makes_room_and_the_job_resumes():
+    """Job 1 does not fit beside job 0: after waiting evict_after seconds it
+    has job 0 checkpointed out (once job 0 ran its quantum of steps and is
+    idle), runs, and job 0 is readmitted from its checkpoint and finishes
+    every step exactly once, in order."""
+    js = [SV.Job(0, 1, 12, 0.0, 60), SV.Job(1, 1, 3, 0.001, 70)]
+    sch = SV.Scheduler(100, 2, evict_after=0.005, quantum=2)
+    for j in js:
+        sch.add_job(j)
+    ex = EvictingExecutor(step_s=0.002)
+    res = SV.serve(sch, SV.poisson_requests(js, 5000.0, 7), ex)
+    assert ex.evicted == [0] and ex.restored == [0]
+    ev = sch.events
+    assert ev.index("evict 0") < ev.index("admit 1") < ev.index("release 1") < len(ev) - 1 - ev[::-1].index("admit 0")
+    steps0 = [s for (j, s, _) in ex.issued if j == 0]
+    assert steps0 == list(range(12))
+    assert len(res) == 15 and sch.peak_used <= 100
+    n_before = sum(1 for (j, s, t) in ex.issued if j == 0 and t < min(t1 for (j1, _, t1) in ex.issued if j1 == 1))
+    assert n_before >= 2  # the quantum ran before the eviction
+
+
+def test_no_eviction_without_a_waiting_limit_or_enough_memory():
+    # evict_after None: job 1 waits for job 0 to finish
+    js = [SV.Job(0, 1, 6, 0.0, 60), SV.Job(1, 1, 2, 0.001, 70)]
+    sch = SV.Scheduler(100, 2)
+    for j in js:
+        sch.add_job(j)
+    ex = EvictingExecutor(step_s=0.002)
+    SV.serve(sch, SV.poisson_requests(js, 5000.0, 8), ex)
+    assert ex.evicted == [] and sch.events.index("release 0") < sch.events.index("admit 1")
+    # evicting every idle job would not free enough (job 1 has a step in
+    # flight): nobody is evicted
+    sch = SV.Scheduler(100, 2, evict_after=0.0)
+    sch.add_job(SV.Job(0, 1, 5, 0.0, 40))
+    sch.add_job(SV.Job(1, 1, 5, 0.0, 40))
+    sch.admit(lambda j: None)
+    for j in sch.jobs.values():
+        j.done_steps = 1
+    sch.jobs[1].busy = True
+    big = SV.Job(2, 1, 5, 0.0, 70)
+    sch.add_job(big)
+    assert sch.maybe_evict(1.0, lambda j: None) == [] and sch.used == 80
+    sch.jobs[1].busy = False  # now the two idle jobs free enough: both go, oldest admission first
+    out = sch.maybe_evict(1.0, lambda j: None)
+    assert [j.job_id for j in out] == [0, 1] and sch.used == 0
+    sch.admit(lambda j: None, 1.0)
+    assert big.state == "admitted" and sch.jobs[0].state == "waiting"
+    # an evicted job does not evict others in its turn
+    assert sch.maybe_evict(2.0, lambda j: None) == []
+
+
+def test_busy_and_fresh_jobs_are_not_evicted():
+    sch = SV.Scheduler(100, 2, evict_after=0.0, quantum=3)
+    sch.add_job(SV.Job(0, 1, 9, 0.0, 60))
+    sch.admit(lambda j: None)
+    j0 = sch.jobs[0]
+    sch.add_job(SV.Job(1, 1, 2, 0.0, 70))
+    j0.done_steps = 2                      # fewer steps than the quantum since admission
+    assert sch.maybe_evict(1.0, lambda j: None) == []
+    j0.done_steps, j0.busy = 3, True      # a step in flight
+    assert sch.maybe_evict(1.0, lambda j: None) == []
+    j0.busy = False
+    assert [j.job_id for j in sch.maybe_evict(1.0, lambda j: None)] == [0]
