@@ -304,12 +304,14 @@ def traffic_from_profile(kernel_hash, opts_name, n_pairs):
     return float(e["dram_bytes_per_launch"])
 
 
-def ingest_traffic(csv_path):
+def ingest_traffic(csv_path, single_opts=None):
     """Writes profiles/backward_traffic.json from the ncu CSV of a
-    ``--profile --profile-tiers`` run captured with
-    ``--metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum -k regex:backward_kernel``:
-    the last launches of the capture are the tier launches, one per autotune
-    candidate in order (the cluster tier's own kernel does not match)."""
+    ``--profile`` run captured with
+    ``--metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum -k regex:backward_kernel``.
+    With ``single_opts`` (a tier name) the capture holds one launch of that
+    tier; otherwise it is a ``--profile-tiers`` run whose last launches are
+    the tier launches, one per autotune candidate in order (the cluster
+    tier's own kernel does not match)."""
     import csv
 
     from paper_2401_05345_gb300 import autotune, gsr
@@ -330,7 +332,8 @@ def ingest_traffic(csv_path):
                  "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}.get(unit, 1.0)
         launches.setdefault(int(d["ID"]), {})[d["Metric Name"]] = v * scale
     # the cluster tier's kernel (backward_cluster_kernel) is not in the capture
-    names = [autotune.opts_name(o) for o in autotune.default_candidates() if o.reduce_mode != gsr.REDUCE_CLUSTER]
+    names = [single_opts] if single_opts else [
+        autotune.opts_name(o) for o in autotune.default_candidates() if o.reduce_mode != gsr.REDUCE_CLUSTER]
     ids = sorted(launches)
     if len(ids) < len(names):
         raise SystemExit(f"{len(ids)} backward launches in {csv_path}, {len(names)} tiers expected")
@@ -957,10 +960,11 @@ def run_ours(args):
 
 
 # Kernels of libgsr launched per step: preprocess; binning (depth keys, three
-# column scans and three radix scatter passes, rectangles, slice bounds,
-# block x tile counts, column scan + ranges, placement); tile order; forward
-# with the L1 loss in its epilogue, backward, backward projection.
-LAUNCHES_PER_STEP = 17
+# column scans and three radix scatter passes, the last also writing the tile
+# rectangles; entry counts, slice bounds, block x tile counts, column scan +
+# ranges + tile order, placement); forward with the L1 loss in its epilogue,
+# backward, backward projection.
+LAUNCHES_PER_STEP = 16
 
 
 def main():
@@ -987,7 +991,7 @@ def main():
                     help="write profiles/backward_traffic.json from the ncu CSV of a --profile-tiers capture")
     args = ap.parse_args()
     if args.ingest_traffic:
-        return ingest_traffic(args.ingest_traffic)
+        return ingest_traffic(args.ingest_traffic, None if args.profile_tiers else args.opts)
     if args.warmup < 3 and not args.profile:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -238,13 +238,17 @@ int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32
  * the step see empty lists); 2 inconsistent internal counts (not expected).
  * The caller reads count_dev after the step (e.g. with the loss) and, on
  * status 1, grows the buffers and redoes the step.  Makes the whole step
- * capturable in a CUDA graph.  Returns GSR_OK or an argument error.
+ * capturable in a CUDA graph.  tile_order: NULL, or DEVICE uint32 [tiles]
+ * that receives the longest-first tile order of the new ranges (what
+ * gsr_tile_order computes), formed by the last block of the binning's own
+ * column scan instead of a launch of its own.  Returns GSR_OK or an
+ * argument error.
  */
 int gsr_bin_sort_async(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                        const float* splat2d, const int32_t* radius, int64_t key_capacity,
                        void* scratch, size_t scratch_bytes, uint32_t* point_list,
                        uint32_t* tile_ranges, uint64_t* keys_out, uint32_t* count_dev,
-                       gsr_stream_t stream);
+                       uint32_t* tile_order, gsr_stream_t stream);
 
 /*
  * The same binning (same outputs, same arguments and errors) computed with

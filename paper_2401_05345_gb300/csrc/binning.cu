@@ -81,8 +81,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_wsum
 }
 
 // Depth keys (FP32 bits of the camera depth, positive, so their unsigned
-// order is the numeric order; culled Gaussians get the largest key) and ids;
-// per-tile counts of the first digit.
+// order is the numeric order) and ids; per-tile counts of the first digit.
+// A culled Gaussian gets the key 2^31 + its id: above every finite depth (so
+// culled Gaussians sort after all others, in any order, and bin nowhere) and
+// distinct, so their digits spread over the count matrices instead of all
+// adding to one counter per pass.
 __global__ void __launch_bounds__(kRsThreads)
 depth_keys_kernel(int n, const float* __restrict__ splat2d, const int* __restrict__ radius,
                   uint32_t* __restrict__ keys, uint32_t* __restrict__ ids, uint32_t* __restrict__ counts0) {
@@ -98,7 +101,7 @@ depth_keys_kernel(int n, const float* __restrict__ splat2d, const int* __restric
         const bool valid = i < n;
         uint32_t k = 0xffffffffu;
         if (valid) {
-            k = radius[i] > 0 ? __float_as_uint(splat2d[(size_t)i * GSR_REC + 9]) : 0xffffffffu;
+            k = radius[i] > 0 ? __float_as_uint(splat2d[(size_t)i * GSR_REC + 9]) : (0x80000000u | (uint32_t)i);
             keys[i] = k;
             ids[i] = (uint32_t)i;
         }
@@ -120,7 +123,7 @@ depth_keys_kernel(int n, const float* __restrict__ splat2d, const int* __restric
 __global__ void __launch_bounds__(1024)
 colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restrict__ tot,
                uint32_t* __restrict__ start, uint32_t* __restrict__ ranges, uint32_t* __restrict__ info,
-               uint32_t cap, uint32_t* __restrict__ count_out) {
+               uint32_t cap, uint32_t* __restrict__ count_out, uint32_t* __restrict__ order) {
     __shared__ uint32_t s_seg[32][33];
     __shared__ bool s_last;
     const int cx = threadIdx.x & 31, seg = threadIdx.x >> 5;
@@ -236,6 +239,10 @@ colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restric
             count_out[1] = status;
         }
     }
+    if (order) {  // the longest-first tile order of the ranges just written
+        __syncthreads();
+        tile_order_block(cols, reinterpret_cast<const uint2*>(ranges), order, &s_seg[0][0]);
+    }
 }
 
 // One scatter pass of the depth sort.  The tile's keys are ranked stably
@@ -245,12 +252,28 @@ colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restric
 //   (keys of smaller digits) + (keys of its digit in earlier tiles)
 //   + (its rank inside the tile).
 // With NEXT, each written key also adds one to its next digit's count in
-// the tile it lands in (the next pass's count matrix).
-template <int SHIFT, int BITS, int NSHIFT, int NBITS, bool NEXT>
+// the tile it lands in (the next pass's count matrix).  With RECTS (the last
+// pass), each key's Gaussian also has its tile rectangle computed (its
+// position and radius gathered as soon as its id is loaded, so the latency
+// overlaps the ranking) and written beside it: rects[pos], packed 16-bit
+// corners, empty when culled.
+struct RectOut {
+    const float* splat2d;
+    const int* radius;
+    Geom g;
+    uint2* rects;
+};
+
+__device__ __forceinline__ uint2 pack_rect(int x0, int x1, int y0, int y1) {
+    return make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
+}
+
+template <int SHIFT, int BITS, int NSHIFT, int NBITS, bool NEXT, bool RECTS>
 __global__ void __launch_bounds__(kRsThreads)
 radix_scatter_kernel(int n, const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                      uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* __restrict__ colpre,
-                     const uint32_t* __restrict__ tot, uint32_t* __restrict__ cnext, uint32_t* __restrict__ err) {
+                     const uint32_t* __restrict__ tot, uint32_t* __restrict__ cnext, uint32_t* __restrict__ err,
+                     RectOut ro) {
     constexpr int NB = 1 << BITS;
     constexpr int DPT = NB / kRsThreads;  // digits owned by each thread
     __shared__ uint16_t s_w[kRsWarps][NB];
@@ -266,6 +289,24 @@ radix_scatter_kernel(int n, const uint32_t* __restrict__ kin, const uint32_t* __
         const long long idx = first + 32 * i;
         key[i] = idx < n ? kin[idx] : 0xffffffffu;
         val[i] = idx < n ? vin[idx] : 0u;
+    }
+    uint2 rect[RECTS ? kRsItems : 1];
+    if constexpr (RECTS) {
+#pragma unroll
+        for (int i = 0; i < kRsItems; ++i) {
+            int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+            if (first + 32 * i < n) {
+                const uint32_t id = val[i];
+                if (id >= (uint32_t)n) atomicOr(err, 2u);  // inconsistent counts upstream: nothing is read
+                const int r = id < (uint32_t)n ? ro.radius[id] : 0;
+                if (r > 0) {
+                    const float2 uv = *reinterpret_cast<const float2*>(ro.splat2d + (size_t)id * GSR_REC);
+                    tile_rect(uv.x, uv.y, r, ro.g.gx, ro.g.gy, ro.g.twl, ro.g.thl, x0, x1, y0, y1);
+                    if (x1 <= x0 || y1 <= y0) x0 = x1 = y0 = y1 = 0;
+                }
+            }
+            rect[i] = pack_rect(x0, x1, y0, y1);
+        }
     }
     // digit totals and this tile's column prefixes of the digits d = tid*DPT + j:
     // independent of the ranking, so their loads are issued before it
@@ -320,6 +361,7 @@ radix_scatter_kernel(int n, const uint32_t* __restrict__ kin, const uint32_t* __
             }
             kout[pos] = key[i];
             vout[pos] = val[i];
+            if (RECTS) ro.rects[pos] = rect[i];
             if (NEXT) {
                 constexpr uint32_t NNB = 1u << NBITS;
                 atomicAdd(&cnext[(size_t)(pos / kRsTile) * NNB + ((key[i] >> NSHIFT) & (NNB - 1))], 1u);
@@ -374,38 +416,31 @@ __device__ __forceinline__ uint32_t rect_area(uint2 r) {
     return (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
 }
 
-// Rectangles of the depth-ordered Gaussians (packed 16-bit corners, empty
-// when culled) and the exclusive prefix of their areas inside each block of
-// 2048; the last block to finish turns the block sums into block offsets
-// and stores the entry total in info[4].
+// Entry counts (rectangle areas) of the depth-ordered Gaussians and their
+// exclusive prefix inside each block of 2048; the last block to finish turns
+// the block sums into block offsets and stores the entry total in info[4].
+// The rectangles come from the last depth-sort pass.
 __global__ void __launch_bounds__(kRsThreads)
-rects_kernel(int n, Geom g, const float* __restrict__ splat2d, const int* __restrict__ radius,
-             const uint32_t* __restrict__ order, uint2* __restrict__ rects, uint32_t* __restrict__ apre,
-             uint32_t* __restrict__ bsum, int nblk, uint32_t* __restrict__ info) {
+areas_kernel(int n, const uint2* __restrict__ rects, uint32_t* __restrict__ apre, uint32_t* __restrict__ bsum,
+             int nblk, uint32_t* __restrict__ info) {
     __shared__ uint32_t s_wsum[kRsWarps];
     __shared__ bool s_last;
     const int k0 = blockIdx.x * kRectBlock + threadIdx.x * kRectPer;
     uint32_t area[kRectPer], sum = 0;
+    if (k0 + kRectPer <= n) {  // a thread's 8 rectangles: 64 contiguous bytes, four 16-byte loads
+        const uint4* r4 = reinterpret_cast<const uint4*>(rects + k0);
 #pragma unroll
-    for (int i = 0; i < kRectPer; ++i) {
-        const int k = k0 + i;
-        int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-        if (k < n) {
-            const uint32_t id = order[k];
-            // an id out of range means the depth sort found inconsistent
-            // counts (flagged): the Gaussian is left out, nothing is read
-            if (id >= (uint32_t)n) atomicOr(&info[1], 2u);
-            const int r = id < (uint32_t)n ? radius[id] : 0;
-            if (r > 0) {
-                const float2 uv = *reinterpret_cast<const float2*>(splat2d + (size_t)id * GSR_REC);
-                tile_rect(uv.x, uv.y, r, g.gx, g.gy, g.twl, g.thl, x0, x1, y0, y1);
-                if (x1 <= x0 || y1 <= y0) x0 = x1 = y0 = y1 = 0;
-            }
-            rects[k] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
+        for (int j = 0; j < kRectPer / 2; ++j) {
+            const uint4 q = r4[j];
+            area[2 * j] = rect_area(make_uint2(q.x, q.y));
+            area[2 * j + 1] = rect_area(make_uint2(q.z, q.w));
         }
-        area[i] = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
-        sum += area[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < kRectPer; ++i) area[i] = k0 + i < n ? rect_area(rects[k0 + i]) : 0u;
     }
+#pragma unroll
+    for (int i = 0; i < kRectPer; ++i) sum += area[i];
     uint32_t btot;
     uint32_t run = block_excl_scan(sum, s_wsum, &btot);
 #pragma unroll
@@ -776,9 +811,18 @@ void bin_layout(int n, const Geom& g, long long cap, char* base, BinScratch& s) 
 }
 
 int colscan(int rows, int cols, uint32_t* m, uint32_t* tot, uint32_t* start, uint32_t* ranges, uint32_t* info,
-            cudaStream_t st, uint32_t cap = 0xffffffffu, uint32_t* count_out = nullptr) {
-    colscan_kernel<<<(cols + 31) / 32, 1024, 0, st>>>(rows, cols, m, tot, start, ranges, info, cap, count_out);
+            cudaStream_t st, uint32_t cap = 0xffffffffu, uint32_t* count_out = nullptr, uint32_t* order = nullptr) {
+    static_assert(kOrderThreads == 1024, "the column scan's last block computes the tile order");
+    colscan_kernel<<<(cols + 31) / 32, 1024, 0, st>>>(rows, cols, m, tot, start, ranges, info, cap, count_out,
+                                                      order);
     return check_launch();
+}
+
+// The longest-first tile order alone (a view without Gaussians).
+__global__ void __launch_bounds__(kOrderThreads)
+order_kernel(int tiles, const uint2* __restrict__ ranges, uint32_t* __restrict__ order) {
+    __shared__ uint32_t cnt[kOrderBuckets];
+    tile_order_block(tiles, ranges, order, cnt);
 }
 
 int smem_optin(const void* fn, size_t bytes) {
@@ -812,7 +856,7 @@ namespace {
 int bin_sort_impl(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h, const float* splat2d,
                   const int32_t* radius, int64_t key_capacity, void* scratch, size_t scratch_bytes,
                   uint32_t* point_list, uint32_t* tile_ranges, uint64_t* keys_out, int64_t* n_keys,
-                  uint32_t* count_dev, gsr_stream_t stream_) {
+                  uint32_t* count_dev, uint32_t* tile_order, gsr_stream_t stream_) {
     Geom g;
     if (n < 0 || key_capacity < 0 || key_capacity >= 0xffffffffll || (!n_keys && !count_dev) ||
         !make_geom(width, height, tile_w, tile_h, g))
@@ -830,7 +874,13 @@ int bin_sort_impl(int32_t n, int32_t width, int32_t height, int32_t tile_w, int3
     if (n == 0) {
         e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)g.tiles, st);
         if (e == cudaSuccess && count_dev) e = cudaMemsetAsync(count_dev, 0, 2 * sizeof(uint32_t), st);
-        return e == cudaSuccess ? GSR_OK : cuda_fail(e);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (tile_order) {  // every list empty: the order of the (empty) ranges
+            order_kernel<<<1, kOrderThreads, 0, st>>>(g.tiles, reinterpret_cast<const uint2*>(tile_ranges),
+                                                      tile_order);
+            return check_launch();
+        }
+        return GSR_OK;
     }
     e = cudaMemsetAsync(s.c1, 0, s.zero_bytes, st);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -840,16 +890,18 @@ int bin_sort_impl(int32_t n, int32_t width, int32_t height, int32_t tile_w, int3
     depth_keys_kernel<<<rt, kRsThreads, 0, st>>>(n, splat2d, radius, s.ka, s.va, s.c0);
     if ((rc = check_launch()) != GSR_OK) return rc;
     if ((rc = colscan(rt, 1 << kRsB0, s.c0, s.t0, nullptr, nullptr, nullptr, st)) != GSR_OK) return rc;
-    radix_scatter_kernel<0, kRsB0, kRsS1, kRsB1, true><<<rt, kRsThreads, 0, st>>>(n, s.ka, s.va, s.kb, s.vb, s.c0,
-                                                                                  s.t0, s.c1, s.info + 1);
+    const RectOut no_rects = {nullptr, nullptr, g, nullptr};
+    radix_scatter_kernel<0, kRsB0, kRsS1, kRsB1, true, false><<<rt, kRsThreads, 0, st>>>(
+        n, s.ka, s.va, s.kb, s.vb, s.c0, s.t0, s.c1, s.info + 1, no_rects);
     if ((rc = check_launch()) != GSR_OK) return rc;
     if ((rc = colscan(rt, 1 << kRsB1, s.c1, s.t1, nullptr, nullptr, nullptr, st)) != GSR_OK) return rc;
-    radix_scatter_kernel<kRsS1, kRsB1, kRsS2, kRsB2, true><<<rt, kRsThreads, 0, st>>>(n, s.kb, s.vb, s.ka, s.va,
-                                                                                      s.c1, s.t1, s.c2, s.info + 1);
+    radix_scatter_kernel<kRsS1, kRsB1, kRsS2, kRsB2, true, false><<<rt, kRsThreads, 0, st>>>(
+        n, s.kb, s.vb, s.ka, s.va, s.c1, s.t1, s.c2, s.info + 1, no_rects);
     if ((rc = check_launch()) != GSR_OK) return rc;
     if ((rc = colscan(rt, 1 << kRsB2, s.c2, s.t2, nullptr, nullptr, nullptr, st)) != GSR_OK) return rc;
-    radix_scatter_kernel<kRsS2, kRsB2, 0, 1, false><<<rt, kRsThreads, 0, st>>>(n, s.ka, s.va, s.kb, s.vb, s.c2,
-                                                                               s.t2, nullptr, s.info + 1);
+    // the last pass also writes each Gaussian's tile rectangle in depth order
+    radix_scatter_kernel<kRsS2, kRsB2, 0, 1, false, true><<<rt, kRsThreads, 0, st>>>(
+        n, s.ka, s.va, s.kb, s.vb, s.c2, s.t2, nullptr, s.info + 1, RectOut{splat2d, radius, g, s.rects});
     if ((rc = check_launch()) != GSR_OK) return rc;
     const uint32_t* order = s.vb;
     const uint32_t* dkeys = s.kb;
@@ -858,7 +910,7 @@ int bin_sort_impl(int32_t n, int32_t width, int32_t height, int32_t tile_w, int3
     //    every placement warp, per block x tile counts, column scan, tile
     //    starts and ranges
     const int nr = rect_blocks(n);
-    rects_kernel<<<nr, kRsThreads, 0, st>>>(n, g, splat2d, radius, order, s.rects, s.apre, s.bsum, nr, s.info);
+    areas_kernel<<<nr, kRsThreads, 0, st>>>(n, s.rects, s.apre, s.bsum, nr, s.info);
     if ((rc = check_launch()) != GSR_OK) return rc;
     const int nwarps = s.nb * kPlaceWarps;
     bounds_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, nwarps, s.rects, s.apre, s.bsum, s.info, s.wstart);
@@ -873,7 +925,8 @@ int bin_sort_impl(int32_t n, int32_t width, int32_t height, int32_t tile_w, int3
         if ((rc = check_launch()) != GSR_OK) return rc;
     }
     const uint32_t cap = (uint32_t)key_capacity;
-    if ((rc = colscan(s.nb, g.tiles, s.m, s.ttot, s.tstart, tile_ranges, s.info, st, cap, count_dev)) != GSR_OK)
+    if ((rc = colscan(s.nb, g.tiles, s.m, s.ttot, s.tstart, tile_ranges, s.info, st, cap, count_dev, tile_order)) !=
+        GSR_OK)
         return rc;
     if (count_dev) {  // placement checks the count on the device
         const size_t psm = place_smem(tw);
@@ -922,15 +975,15 @@ extern "C" int gsr_bin_sort(int32_t n, int32_t width, int32_t height, int32_t ti
                             gsr_stream_t stream) {
     if (!n_keys) return GSR_EINVAL;
     return bin_sort_impl(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity, scratch, scratch_bytes,
-                         point_list, tile_ranges, keys_out, n_keys, nullptr, stream);
+                         point_list, tile_ranges, keys_out, n_keys, nullptr, nullptr, stream);
 }
 
 extern "C" int gsr_bin_sort_async(int32_t n, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
                                   const float* splat2d, const int32_t* radius, int64_t key_capacity,
                                   void* scratch, size_t scratch_bytes, uint32_t* point_list,
                                   uint32_t* tile_ranges, uint64_t* keys_out, uint32_t* count_dev,
-                                  gsr_stream_t stream) {
+                                  uint32_t* tile_order, gsr_stream_t stream) {
     if (!count_dev) return GSR_EINVAL;
     return bin_sort_impl(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity, scratch, scratch_bytes,
-                         point_list, tile_ranges, keys_out, nullptr, count_dev, stream);
+                         point_list, tile_ranges, keys_out, nullptr, count_dev, tile_order, stream);
 }

@@ -174,6 +174,57 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
                  : "memory");
 }
 
+// Longest-first tile order (one CTA of kOrderThreads): a counting sort of
+// the tile ids by decreasing bucket of their list length, the bucket being
+// floor(log2 len) with the next two bits below the leading one (0 for empty
+// lists).  cnt: kOrderBuckets words of shared memory.  The CTA's global
+// writes to ranges before the call must be followed by __syncthreads().
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderBuckets = 128;
+
+__device__ __forceinline__ int order_bucket(uint32_t len) {
+    if (len == 0) return 0;
+    const int l2 = 31 - __clz(len);
+    return l2 < 2 ? 1 + l2 : 4 * l2 + (int)((len >> (l2 - 2)) & 3u);
+}
+
+__device__ __forceinline__ void tile_order_block(int tiles, const uint2* ranges, uint32_t* __restrict__ order,
+                                                 uint32_t* cnt) {
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        atomicAdd(&cnt[kOrderBuckets - 1 - order_bucket(r.y - r.x)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the bucket counts, in place
+        constexpr int PER = kOrderBuckets / 32;
+        uint32_t v[PER], s = 0;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            v[j] = cnt[threadIdx.x * PER + j];
+            s += v[j];
+        }
+        uint32_t incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(kFull, incl, o);
+            if ((int)threadIdx.x >= o) incl += x;
+        }
+        uint32_t run = incl - s;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            cnt[threadIdx.x * PER + j] = run;
+            run += v[j];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        order[atomicAdd(&cnt[kOrderBuckets - 1 - order_bucket(r.y - r.x)], 1u)] = (uint32_t)t;
+    }
+}
+
 // Bitonic sort of the warp's (key, src) pairs in ascending (key, src) order;
 // lane L ends with the L-th pair.
 __device__ __forceinline__ void warp_sort_pairs(uint32_t& key, uint32_t& src, int lane) {

@@ -9,53 +9,11 @@
 namespace gsr {
 namespace {
 
-// Bucket of a tile list of `len` entries for gsr_tile_order: floor(log2 len)
-// with the next two bits below the leading one (0 for empty lists).
-__device__ __forceinline__ int order_bucket(uint32_t len) {
-    if (len == 0) return 0;
-    const int l2 = 31 - __clz(len);
-    return l2 < 2 ? 1 + l2 : 4 * l2 + (int)((len >> (l2 - 2)) & 3u);
-}
-
-// One CTA: a counting sort of the tiles by decreasing bucket.
-constexpr int kOrderThreads = 1024;
-constexpr int kOrderBuckets = 128;
+// One CTA: the longest-first tile order (tile_order_block).
 __global__ void __launch_bounds__(kOrderThreads)
 tile_order_kernel(int tiles, const uint2* __restrict__ ranges, uint32_t* __restrict__ order) {
     __shared__ uint32_t cnt[kOrderBuckets];
-    for (int b = threadIdx.x; b < kOrderBuckets; b += kOrderThreads) cnt[b] = 0;
-    __syncthreads();
-    for (int t = threadIdx.x; t < tiles; t += kOrderThreads) {
-        const uint2 r = ranges[t];
-        atomicAdd(&cnt[kOrderBuckets - 1 - order_bucket(r.y - r.x)], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive scan of the bucket counts, in place
-        constexpr int PER = kOrderBuckets / 32;
-        uint32_t v[PER], s = 0;
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            v[j] = cnt[threadIdx.x * PER + j];
-            s += v[j];
-        }
-        uint32_t incl = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t x = __shfl_up_sync(kFull, incl, o);
-            if ((int)threadIdx.x >= o) incl += x;
-        }
-        uint32_t run = incl - s;
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            cnt[threadIdx.x * PER + j] = run;
-            run += v[j];
-        }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < tiles; t += kOrderThreads) {
-        const uint2 r = ranges[t];
-        order[atomicAdd(&cnt[kOrderBuckets - 1 - order_bucket(r.y - r.x)], 1u)] = (uint32_t)t;
-    }
+    tile_order_block(tiles, ranges, order, cnt);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -101,7 +101,7 @@ def lib():
     L.gsr_bin_scratch_bytes_library.argtypes = L.gsr_bin_scratch_bytes.argtypes
     L.gsr_bin_sort_library.argtypes = L.gsr_bin_sort.argtypes
     L.gsr_bin_sort_async.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, c_int64, P, c_size_t,
-                                     P, P, P, P, P]
+                                     P, P, P, P, P, P]
     L.gsr_bin_sort_static.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, P, P, c_int64, P, P, P,
                                       POINTER(c_int64), P]
     L.gsr_tile_order.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P]
@@ -202,13 +202,14 @@ def gsr_bin_sort(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity
 
 
 def gsr_bin_sort_async(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity, scratch, point_list,
-                       tile_ranges, count_dev, keys_out=None, stream=None):
+                       tile_ranges, count_dev, keys_out=None, stream=None, tile_order=None):
     """Binning without a host sync; count_dev (int32 [2] on the device)
-    receives (key count, status 0 ok / 1 over capacity / 2 inconsistent)."""
+    receives (key count, status 0 ok / 1 over capacity / 2 inconsistent);
+    tile_order (optional, int32 [tiles]) the longest-first tile order."""
     _check("gsr_bin_sort_async", lib().gsr_bin_sort_async(
         n, width, height, tile_w, tile_h, _ptr(splat2d), _ptr(radius), key_capacity, _ptr(scratch),
         scratch.numel() * scratch.element_size(), _ptr(point_list), _ptr(tile_ranges), _ptr(keys_out),
-        _ptr(count_dev), _stream(stream)))
+        _ptr(count_dev), _ptr(tile_order), _stream(stream)))
 
 
 def gsr_bin_sort_static(n, width, height, tile_w, tile_h, splat2d, radius, key_capacity, point_list,

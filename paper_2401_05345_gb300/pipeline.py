@@ -127,10 +127,11 @@ class ViewBuffers:
             self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
         if getattr(self, "bin_count", None) is None:
             self.bin_count = torch.zeros(2, dtype=torch.int32, device=self.device)
+        # the binning also leaves the longest-first tile order of its lists
+        self.mask_valid = False
         gsr.gsr_bin_sort_async(self.n, self.W, self.H, self.tw, self.th, self.splat2d, self.radius,
                                self.key_capacity, self.scratch, self.point_list, self.tile_ranges, self.bin_count,
-                               None, stream)
-        self.order_tiles(stream)
+                               None, stream, tile_order=self.tile_order)
 
     def order_tiles(self, stream=None):
         """Longest-first tile order of the current lists (gsr_tile_order);
@@ -268,7 +269,7 @@ class Renderer:
 
 class StepGraph:
     """One view's training step (``Renderer.step`` with asynchronous binning)
-    captured once in a CUDA graph and replayed.  The step's 17 kernel
+    captured once in a CUDA graph and replayed.  The step's 16 kernel
     launches, the loss reset and the gradient zeroing go to the GPU as one
     graph launch, so no launch gap separates the short binning kernels.
 

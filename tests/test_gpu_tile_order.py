@@ -75,3 +75,37 @@ def test_order_on_a_grid_of_66049_tiles(dev):
         res.append(grad.cpu().numpy())
     np.testing.assert_array_equal(res[0], res[1])
     assert np.abs(res[0]).max() > 0
+
+
+@pytest.mark.parametrize("size,n", [((4112, 4112), 30_000), ((300, 200), 3_000), ((64, 48), 0)])
+def test_async_binning_leaves_the_tile_order(dev, size, n):
+    """gsr_bin_sort_async with a tile_order output (the last block of its
+    column scan forms the order): a permutation with non-increasing buckets,
+    the same bucket sequence as gsr_tile_order; a view without Gaussians
+    gets one too."""
+    W, H = size
+    cam = S.front_camera(W, H)
+    vb = pipeline.ViewBuffers(n, cam, dev)
+    if n:
+        vb.preprocess(pipeline.SceneTensors.from_scene(S.gmm_scene(12, n, 32, (-3.5, 0.5), 1), dev))
+    for attempt in range(2):  # an overflow grows the key buffers: bin again
+        vb.tile_order.fill_(-1)
+        vb.bin_async()
+        torch.cuda.synchronize()
+        if vb.check_bin():
+            break
+    else:
+        raise AssertionError("binning did not fit the grown key buffers")
+    tiles = vb.gx * vb.gy
+    o = vb.tile_order.cpu().numpy()
+    assert sorted(o.tolist()) == list(range(tiles))
+    rg = vb.tile_ranges.cpu().numpy().astype(np.int64)
+    b = np.array([_bucket(int(x)) for x in rg[o, 1] - rg[o, 0]])
+    assert np.all(np.diff(b) <= 0)
+    o2 = torch.empty_like(vb.tile_order)
+    gsr.gsr_tile_order(W, H, 16, 16, vb.tile_ranges, o2)
+    torch.cuda.synchronize()
+    b2 = np.array([_bucket(int(x)) for x in rg[o2.cpu().numpy(), 1] - rg[o2.cpu().numpy(), 0]])
+    np.testing.assert_array_equal(b, b2)
+    if n:
+        assert vb.n_keys > 0 and b[0] > 0
