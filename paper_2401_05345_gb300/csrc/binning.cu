@@ -8,7 +8,7 @@
 //    first pass from the key-generation kernel, for the later ones added by
 //    the previous pass's scatter as it writes each key), a column scan of
 //    the [tile][digit] count matrix, and a scatter that ranks the tile's keys
-//    with warp match masks.  No block waits on another.
+//    with per-bit warp ballots.  No block waits on another.
 // 2. Tile lists.  Walking the Gaussians in that order and appending each one
 //    to the lists of the tiles its rectangle covers gives every tile's list
 //    already in (depth, id) order, so the entries never go through a sort
@@ -16,10 +16,12 @@
 //    entries, in depth order (tiles row-major inside a rectangle), are cut
 //    into equal slices, one per warp of the placement grid (a Gaussian may
 //    straddle two slices: it has one entry per tile, so order per tile is
-//    kept).  One kernel counts each block's entries per tile, a column scan
-//    over the blocks gives every (block, tile) pair its first slot (and the
-//    tile ranges), and a second pass writes the entries, 32 per round per
-//    warp, ranking equal tiles within a round by lane.
+//    kept).  One kernel counts each block's entries per tile (its
+//    rectangles summed in a 2D difference array, then prefix-summed), a
+//    column scan over the blocks gives every (block, tile) pair its first
+//    slot (and the tile ranges), and a second pass writes the entries, one
+//    rectangle row per lane and 32 rows per round per warp; rows of one tile
+//    row that overlap take turns in lane (depth) order.
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -80,6 +82,20 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_wsum
     return woff + incl - v;
 }
 
+// The lanes of `active` whose label has the same low BITS bits as this
+// lane's: one ballot per bit, each keeping the lanes that agree on it.
+template <int BITS>
+__device__ __forceinline__ unsigned match_low_bits(uint32_t label, unsigned active) {
+    unsigned m = active;
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const bool bit = (label >> b) & 1u;
+        const unsigned v = __ballot_sync(kFull, bit);
+        m &= bit ? v : ~v;
+    }
+    return m;
+}
+
 // Depth keys (FP32 bits of the camera depth, positive, so their unsigned
 // order is the numeric order) and ids; per-tile counts of the first digit.
 // A culled Gaussian gets the key 2^31 + its id: above every finite depth (so
@@ -91,23 +107,27 @@ depth_keys_kernel(int n, const float* __restrict__ splat2d, const int* __restric
                   uint32_t* __restrict__ keys, uint32_t* __restrict__ ids, uint32_t* __restrict__ counts0) {
     constexpr int NB = 1 << kRsB0;
     __shared__ uint32_t h[NB];
-    for (int i = threadIdx.x; i < NB; i += kRsThreads) h[i] = 0;
-    __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long first = (long long)blockIdx.x * kRsTile + w * 32 * kRsItems + lane;
-#pragma unroll 4
+    int rad[kRsItems];
+    float dep[kRsItems];
+#pragma unroll
+    for (int it = 0; it < kRsItems; ++it) {  // every load issued before the first use
+        const long long i = first + 32 * it;
+        rad[it] = i < n ? radius[i] : 0;
+        dep[it] = i < n ? splat2d[(size_t)i * GSR_REC + 9] : 0.0f;
+    }
+    for (int i = threadIdx.x; i < NB; i += kRsThreads) h[i] = 0;
+    __syncthreads();
+#pragma unroll
     for (int it = 0; it < kRsItems; ++it) {
         const long long i = first + 32 * it;
-        const bool valid = i < n;
-        uint32_t k = 0xffffffffu;
-        if (valid) {
-            k = radius[i] > 0 ? __float_as_uint(splat2d[(size_t)i * GSR_REC + 9]) : (0x80000000u | (uint32_t)i);
+        if (i < n) {
+            const uint32_t k = rad[it] > 0 ? __float_as_uint(dep[it]) : (0x80000000u | (uint32_t)i);
             keys[i] = k;
             ids[i] = (uint32_t)i;
+            atomicAdd(&h[k & (NB - 1)], 1u);
         }
-        const uint32_t d = k & (NB - 1);
-        const unsigned peers = __match_any_sync(kFull, d) & __ballot_sync(kFull, valid);
-        if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < NB; i += kRsThreads) counts0[(size_t)blockIdx.x * NB + i] = h[i];
@@ -158,7 +178,10 @@ colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restric
         }
         s_seg[cx][seg] = incl - x;
         const int cc = blockIdx.x * 32 + seg;
-        if (cx == 31 && cc < cols) tot[cc] = incl;
+        if (cx == 31 && cc < cols) {
+            tot[cc] = incl;
+            if (ranges) __threadfence();  // the totals are what the last block reads
+        }
     }
     __syncthreads();
     if (c < cols) {
@@ -181,7 +204,6 @@ colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restric
     }
     if (!ranges) return;
     // last block: exclusive scan of the column totals
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(&info[2], 1u) == gridDim.x - 1;
     __syncthreads();
@@ -247,7 +269,7 @@ colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restric
 
 // One scatter pass of the depth sort.  The tile's keys are ranked stably
 // (warp-striped: warp w holds keys w*512 .. w*512+511 of the tile, item i of
-// lane l is key 32 i + l of that run) with match masks per warp, per-warp
+// lane l is key 32 i + l of that run) with per-bit ballots per warp, per-warp
 // digit counts are scanned across the warps, and every key goes to
 //   (keys of smaller digits) + (keys of its digit in earlier tiles)
 //   + (its rank inside the tile).
@@ -322,8 +344,18 @@ radix_scatter_kernel(int n, const uint32_t* __restrict__ kin, const uint32_t* __
     for (int i = 0; i < kRsItems; ++i) {
         const bool valid = first + 32 * i < n;
         const uint32_t d = (key[i] >> SHIFT) & (NB - 1);
-        const unsigned peers = __match_any_sync(kFull, d) & __ballot_sync(kFull, valid);
-        const uint32_t pre = s_w[w][d];
+        // A round's 32 digits are usually distinct.  Each lane claims its
+        // digit by writing its lane into the counter's spare high bits (a
+        // warp holds 256 keys, so a count needs 10 bits) and reads the claim
+        // back; only a round where some claim was overwritten compares the
+        // digits bit by bit.  The new count clears the claim.
+        const uint32_t pre = valid ? s_w[w][d] : 0u;
+        __syncwarp();
+        if (valid) s_w[w][d] = (uint16_t)(pre | 0x8000u | ((uint32_t)lane << 10));
+        __syncwarp();
+        const unsigned act = __ballot_sync(kFull, valid);
+        const unsigned lost = __ballot_sync(kFull, valid && ((s_w[w][d] >> 10) & 31u) != (uint32_t)lane);
+        const unsigned peers = lost ? match_low_bits<BITS>(d, act) : (1u << lane) & act;
         __syncwarp();
         if (valid && lane == 31 - __clz(peers)) s_w[w][d] = (uint16_t)(pre + __popc(peers));
         rank[i] = pre + __popc(peers & lt);
@@ -338,9 +370,14 @@ radix_scatter_kernel(int n, const uint32_t* __restrict__ kin, const uint32_t* __
     uint32_t run = block_excl_scan(hs, s_wsum, &all);
 #pragma unroll
     for (int j = 0; j < DPT; ++j) {
-        const int d = tid * DPT + j;
-        s_base[d] = run + cp[j];
+        s_base[tid * DPT + j] = run + cp[j];
         run += hv[j];
+    }
+    // the warps' exclusive offsets, digits strided over the block so that a
+    // warp's lanes touch 32 consecutive 16-bit counters
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+        const int d = j * kRsThreads + tid;
         uint32_t wr = 0;
 #pragma unroll
         for (int q = 0; q < kRsWarps; ++q) {
@@ -448,10 +485,11 @@ areas_kernel(int n, const uint2* __restrict__ rects, uint32_t* __restrict__ apre
         if (k0 + i < n) apre[k0 + i] = run;
         run += area[i];
     }
-    if (threadIdx.x == 0) bsum[blockIdx.x] = btot;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&info[3], 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) {  // the last block reads only the block sums
+        bsum[blockIdx.x] = btot;
+        __threadfence();
+        s_last = atomicAdd(&info[3], 1u) == gridDim.x - 1;
+    }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -487,19 +525,32 @@ __device__ __forceinline__ uint32_t warp_entries(uint32_t total, int nwarps) {
     return ew > 0 ? ew : 1u;
 }
 
-// For every warp j of the placement grid: the Gaussian that holds entry
-// j * Ew, its first entry (each boundary lies in exactly one rectangle).
-__global__ void __launch_bounds__(256)
-bounds_kernel(int n, int nwarps, const uint2* __restrict__ rects, const uint32_t* __restrict__ apre,
-              const uint32_t* __restrict__ boff, const uint32_t* __restrict__ info, uint32_t* __restrict__ wstart) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const uint32_t area = rect_area(rects[k]);
-    if (area == 0) return;
-    const uint32_t ew = warp_entries(info[4], nwarps);
-    const uint32_t p = entry_prefix(apre, boff, k);
-    for (uint32_t j = (p + ew - 1) / ew; (unsigned long long)j * ew < (unsigned long long)p + area; ++j)
-        if (j < (uint32_t)nwarps) wstart[j] = (uint32_t)k;
+// The Gaussian that holds entry e: the last k whose entry prefix is <= e
+// (the prefixes do not decrease with k, and a Gaussian with no entries
+// shares its prefix with the next one, so the last is the holder).  The warp
+// probes 32 points per step, first over the rectangle blocks' offsets, then
+// inside the block.
+__device__ __forceinline__ int entry_owner(int n, int nblk, const uint32_t* __restrict__ apre,
+                                           const uint32_t* __restrict__ boff, uint32_t e, int lane) {
+    int lo = 0, hi = nblk;  // boff[lo] <= e throughout (boff[0] = 0)
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) / 32;
+        const int p = lo + lane * step;
+        const unsigned ok = __ballot_sync(kFull, p < hi && boff[p] <= e);
+        lo += (31 - __clz(ok)) * step;
+        hi = min(hi, lo + step);
+    }
+    const uint32_t r = e - boff[lo];
+    int klo = lo << kRectShift;  // apre[klo] = 0 <= r throughout
+    int khi = min(n, klo + kRectBlock);
+    while (khi - klo > 1) {
+        const int step = (khi - klo + 31) / 32;
+        const int p = klo + lane * step;
+        const unsigned ok = __ballot_sync(kFull, p < khi && apre[p] <= r);
+        klo += (31 - __clz(ok)) * step;
+        khi = min(khi, klo + step);
+    }
+    return klo;
 }
 
 // Per-warp staging of 32 consecutive depth-ordered Gaussians: their
@@ -604,48 +655,119 @@ __device__ __forceinline__ void walk_rows(WarpBatch& wb, int lane, int n, uint32
     }
 }
 
-// Counts, per placement block, the entries of every tile in the window
-// [t0, t0 + tw): m[b][t0 + t].
+// Window of the entry counts: tile columns [c0, c0 + cw) x rows [r0, r0 + rh),
+// cw * rh <= kMaxWindowTiles.
+struct CountWindow {
+    int c0, cw, r0, rh;
+};
+
+// Adds the tile rectangle [x0, x1) x [y0, y1), clipped to the window, to the
+// window's 2D difference array d (row-major, cw wide): +1 at its first
+// corner and one past its last, -1 at the other two; corners past the
+// window's right or bottom edge change no counted cell and are left out.
+__device__ __forceinline__ void diff_rect(int* d, const CountWindow& cwin, int x0, int x1, int y0, int y1) {
+    x0 = max(x0 - cwin.c0, 0); x1 = min(x1 - cwin.c0, cwin.cw);
+    y0 = max(y0 - cwin.r0, 0); y1 = min(y1 - cwin.r0, cwin.rh);
+    if (x0 >= x1 || y0 >= y1) return;
+    atomicAdd(&d[y0 * cwin.cw + x0], 1);
+    if (x1 < cwin.cw) atomicAdd(&d[y0 * cwin.cw + x1], -1);
+    if (y1 < cwin.rh) {
+        atomicAdd(&d[y1 * cwin.cw + x0], -1);
+        if (x1 < cwin.cw) atomicAdd(&d[y1 * cwin.cw + x1], 1);
+    }
+}
+
+// Counts, per placement block, the entries of every tile in a window:
+// m[b][tile].  A warp takes its slice's Gaussians 32 at a time, one per
+// lane, and adds each one's entries as rectangles to a 2D difference array
+// of the window (a Gaussian that straddles a slice boundary keeps the tail
+// of one row, whole rows and the head of another: up to three rectangles);
+// prefix sums along the rows and then down the columns turn it into the
+// counts.
 __global__ void __launch_bounds__(kPlaceThreads)
-chunk_hist_kernel(int n, int nb, Geom g, int t0, int tw, const uint2* __restrict__ rects,
+chunk_hist_kernel(int n, int nb, int nblk, Geom g, CountWindow cwin, const uint2* __restrict__ rects,
                   const uint32_t* __restrict__ apre, const uint32_t* __restrict__ boff,
-                  const uint32_t* __restrict__ wstart, uint32_t* __restrict__ info, uint32_t* __restrict__ m) {
-    extern __shared__ uint32_t h[];  // [(tw + 1) / 2] packed 16-bit counts (a block holds < 65536 entries)
-    __shared__ WarpBatch s_wb[kPlaceWarps];
+                  uint32_t* __restrict__ wstart, const uint32_t* __restrict__ info, uint32_t* __restrict__ m) {
+    extern __shared__ int d[];  // [rh][cw]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int tw2 = (tw + 1) / 2;
-    for (int q = threadIdx.x; q < tw2; q += kPlaceThreads) h[q] = 0;
+    const int cells = cwin.cw * cwin.rh;
+    for (int q = threadIdx.x; q < cells; q += kPlaceThreads) d[q] = 0;
     __syncthreads();
     const int b = blockIdx.x;
     const uint32_t total = info[4];
-    const int nwarps = nb * kPlaceWarps;
-    const uint32_t ew = warp_entries(total, nwarps);
+    const uint32_t ew = warp_entries(total, nb * kPlaceWarps);
     const unsigned long long e0l = (unsigned long long)(b * kPlaceWarps + w) * ew;
-    const int kw = e0l < total ? (int)wstart[b * kPlaceWarps + w] : n;
-    if (e0l < total && (unsigned)kw >= (unsigned)n) atomicOr(&info[1], 4u);  // flagged: the ranges stay empty
-    if (e0l < total && (unsigned)kw < (unsigned)n) {  // a start out of range: counts inconsistent, nothing read
+    if (e0l < total) {
         const uint32_t e0 = (uint32_t)e0l;
+        const int kw = entry_owner(n, nblk, apre, boff, e0, lane);  // also the placement warp's start
+        if (lane == 0) wstart[b * kPlaceWarps + w] = (uint32_t)kw;
         const uint32_t e1 = total - e0 < ew ? total : e0 + ew;
-        const int k = kw;
-        walk_rows<false>(s_wb[w], lane, n, e0, e1, k, rects, nullptr, nullptr, entry_prefix(apre, boff, k), g, t0,
-                         [&](bool ok, const RowWork& r) {
-                             if (!ok) return;
-                             const int lo = max(r.row_t0 + r.xs, 0), hi = min(r.row_t0 + r.xe, tw);
-                             for (int q = lo >> 1; 2 * q < hi; ++q)
-                                 atomicAdd(&h[q], (2 * q >= lo ? 1u : 0u) + (2 * q + 1 < hi ? 0x10000u : 0u));
-                         });
+        for (int k = kw; k < n; k += 32) {
+            const int kk = k + lane;
+            uint32_t p = 0xffffffffu;
+            int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+            if (kk < n) {
+                p = entry_prefix(apre, boff, kk);
+                unpack_rect(rects[kk], x0, x1, y0, y1);
+            }
+            if (__ballot_sync(kFull, p < e1) == 0u) break;  // prefixes increase with k
+            const uint32_t wd = (uint32_t)(x1 - x0), area = wd * (uint32_t)(y1 - y0);
+            if (p >= e1 || area == 0u || p + area <= e0) continue;
+            const uint32_t a = e0 > p ? e0 - p : 0u;
+            const uint32_t z = e1 - p < area ? e1 - p : area;  // entries [a, z) of this Gaussian are the slice's
+            if (a == 0u && z == area) {
+                diff_rect(d, cwin, x0, x1, y0, y1);
+                continue;
+            }
+            const int ra = (int)(a / wd), ca = (int)(a % wd), rz = (int)(z / wd), cz = (int)(z % wd);
+            if (ra == rz) {
+                diff_rect(d, cwin, x0 + ca, x0 + cz, y0 + ra, y0 + ra + 1);
+                continue;
+            }
+            int rf = ra;
+            if (ca > 0) {
+                diff_rect(d, cwin, x0 + ca, x1, y0 + ra, y0 + ra + 1);
+                rf = ra + 1;
+            }
+            if (rz > rf) diff_rect(d, cwin, x0, x1, y0 + rf, y0 + rz);
+            if (cz > 0) diff_rect(d, cwin, x0, x0 + cz, y0 + rz, y0 + rz + 1);
+        }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < tw; t += kPlaceThreads)
-        m[(size_t)b * g.tiles + t0 + t] = (h[t >> 1] >> (16 * (t & 1))) & 0xffffu;
+    // prefix sums along each row (a warp per row, 32 cells at a time) ...
+    for (int y = w; y < cwin.rh; y += kPlaceWarps) {
+        int carry = 0;
+        for (int x = 0; x < cwin.cw; x += 32) {
+            const int i = y * cwin.cw + x + lane;
+            int v = x + lane < cwin.cw ? d[i] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(kFull, v, o);
+                if (lane >= o) v += u;
+            }
+            v += carry;
+            if (x + lane < cwin.cw) d[i] = v;
+            carry = __shfl_sync(kFull, v, 31);
+        }
+    }
+    __syncthreads();
+    // ... then down each column, written out as the block's counts
+    for (int x = threadIdx.x; x < cwin.cw; x += kPlaceThreads) {
+        int run = 0;
+        size_t o = (size_t)b * g.tiles + (size_t)cwin.r0 * g.gx + cwin.c0 + x;
+        for (int y = 0; y < cwin.rh; ++y, o += g.gx) {
+            run += d[y * cwin.cw + x];
+            m[o] = (uint32_t)run;
+        }
+    }
 }
 
 // Writes the entries of the tiles in the window: block b's entries of tile
 // t start at start[t] + m[b][t] (m already column-scanned); each warp owns a
 // consecutive slice of the block's entries, and its per-tile offsets come
-// from the warps before it.  Entries of one tile in the same round of 32
-// are ranked by lane with a match mask, so every tile receives its entries
-// in depth order.
+// from the warps before it.  Rows of one tile row in the same round of 32
+// are ranked by lane with a match mask on the row index, and overlapping
+// ones take turns, so every tile receives its entries in depth order.
 template <bool KEYS>
 __global__ void __launch_bounds__(kPlaceThreads)
 place_kernel(int n, int nb, Geom g, int t0, int tw, uint32_t cap, const uint32_t* __restrict__ order,
@@ -906,23 +1028,29 @@ int bin_sort_impl(int32_t n, int32_t width, int32_t height, int32_t tile_w, int3
     const uint32_t* order = s.vb;
     const uint32_t* dkeys = s.kb;
 
-    // 2. rectangles and entry prefixes in depth order, the first Gaussian of
-    //    every placement warp, per block x tile counts, column scan, tile
+    // 2. entry prefixes in depth order; per block x tile counts (which also
+    //    find the first Gaussian of every placement warp); column scan, tile
     //    starts and ranges
     const int nr = rect_blocks(n);
     areas_kernel<<<nr, kRsThreads, 0, st>>>(n, s.rects, s.apre, s.bsum, nr, s.info);
     if ((rc = check_launch()) != GSR_OK) return rc;
-    const int nwarps = s.nb * kPlaceWarps;
-    bounds_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, nwarps, s.rects, s.apre, s.bsum, s.info, s.wstart);
-    if ((rc = check_launch()) != GSR_OK) return rc;
     const int tw = window_tiles(g);
-    const size_t hsm = sizeof(uint32_t) * (size_t)tw;
-    if ((rc = smem_optin((const void*)chunk_hist_kernel, hsm)) != GSR_OK) return rc;
-    for (int t0 = 0; t0 < g.tiles; t0 += tw) {
-        const int wt = g.tiles - t0 < tw ? g.tiles - t0 : tw;
-        chunk_hist_kernel<<<s.nb, kPlaceThreads, hsm, st>>>(n, s.nb, g, t0, wt, s.rects, s.apre, s.bsum, s.wstart,
-                                                            s.info, s.m);
-        if ((rc = check_launch()) != GSR_OK) return rc;
+    {   // count windows: whole tile rows (row pieces when a row is longer than a window)
+        CountWindow cwin;
+        cwin.cw = g.gx < kMaxWindowTiles ? g.gx : kMaxWindowTiles;
+        const int rows = kMaxWindowTiles / cwin.cw;
+        const size_t hsm = sizeof(int) * (size_t)cwin.cw * (size_t)(rows < g.gy ? rows : g.gy);
+        if ((rc = smem_optin((const void*)chunk_hist_kernel, hsm)) != GSR_OK) return rc;
+        for (cwin.r0 = 0; cwin.r0 < g.gy; cwin.r0 += rows) {
+            cwin.rh = g.gy - cwin.r0 < rows ? g.gy - cwin.r0 : rows;
+            for (int c0 = 0; c0 < g.gx; c0 += kMaxWindowTiles) {
+                cwin.c0 = c0;
+                cwin.cw = g.gx - c0 < kMaxWindowTiles ? g.gx - c0 : kMaxWindowTiles;
+                chunk_hist_kernel<<<s.nb, kPlaceThreads, hsm, st>>>(n, s.nb, nr, g, cwin, s.rects, s.apre,
+                                                                    s.bsum, s.wstart, s.info, s.m);
+                if ((rc = check_launch()) != GSR_OK) return rc;
+            }
+        }
     }
     const uint32_t cap = (uint32_t)key_capacity;
     if ((rc = colscan(s.nb, g.tiles, s.m, s.ttot, s.tstart, tile_ranges, s.info, st, cap, count_dev, tile_order)) !=

@@ -96,6 +96,24 @@ __device__ __forceinline__ int srow(int f) { return (f / NF) * (NF + 1) + f % NF
 
 template <int NF, int CH, bool VEC>
 __device__ __forceinline__ void stage_rows_in(const float* __restrict__ g, int rows, float* s) {
+    if constexpr (VEC && NF % 4 == 0) {
+        if (rows == CH) {  // a full chunk: every 16-byte load in flight at once
+            constexpr int Q = NF / 4;
+            const float4* g4 = reinterpret_cast<const float4*>(g);
+            float4 x[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) x[q] = g4[threadIdx.x + q * CH];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int f = 4 * (threadIdx.x + q * CH);
+                s[srow<NF>(f)] = x[q].x;
+                s[srow<NF>(f + 1)] = x[q].y;
+                s[srow<NF>(f + 2)] = x[q].z;
+                s[srow<NF>(f + 3)] = x[q].w;
+            }
+            return;
+        }
+    }
     const int total = rows * NF;
     int f0 = 0;
     if (VEC) {

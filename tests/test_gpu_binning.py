@@ -2,8 +2,10 @@
 the oracle's key sort, bit for bit, on synthetic splat records that stress
 what a sort can get wrong: equal depths (stability, id order), culled and
 off-screen splats, ragged sizes around the sort's 2048-key tiles, tile
-grids wider than one row window of the counting sort (8x8 tiles at
-4000x840: 500 x 105 tiles, three placement windows), non-square tiles,
+grids larger than one window of the counting sort (8x8 tiles at
+4000x840: 500 x 105 tiles, seven row windows of the counts and seven
+placement windows; at 70000x16 a tile row of 8750 tiles is longer than a
+window), non-square tiles,
 splats larger than the image.  The CUB-based
 comparison entry point must give the same bytes."""
 import numpy as np
@@ -81,6 +83,7 @@ CASES = [
     ("tiles_32x16", 6, 20_000, 500, 333, (32, 16), 7, 0.1, 2),
     ("tiles_8x32", 7, 20_000, 333, 500, (8, 32), 0, 0.1, 1),
     ("many_radix_tiles", 8, 150_000, 800, 800, (16, 16), 40, 0.3, 0),
+    ("row_longer_than_a_window", 9, 20_000, 70_000, 16, (8, 8), 0, 0.1, 2),
 ]
 
 
