@@ -227,12 +227,15 @@ colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restric
         }
         if (lane == 31) s_seg[0][w] = incl;
         __syncthreads();
-        uint32_t woff = 0, btot = 0;
-        for (int q = 0; q < 32; ++q) {
-            const uint32_t x = s_seg[0][q];
-            woff += q < w ? x : 0u;
-            btot += x;
+        // the 32 warp sums, scanned across one warp's lanes by every warp
+        const uint32_t ws = s_seg[0][lane];
+        uint32_t wincl = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, wincl, o);
+            if (lane >= o) wincl += t;
         }
+        const uint32_t woff = __shfl_sync(kFull, wincl - ws, w), btot = __shfl_sync(kFull, wincl, 31);
         __syncthreads();
         uint32_t run = carry + woff + incl - s;
 #pragma unroll

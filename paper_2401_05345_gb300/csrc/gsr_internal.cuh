@@ -127,33 +127,30 @@ __device__ __forceinline__ void eval_splat2_all(float u, float v, float A, float
     hit1 = e.sigma.y >= 0.0f && e.alpha.y >= kAlphaMin;
 }
 
-// pair step of the transposing reduce-scatter: lanes with bit b set keep y
-// and send x, the others keep x and send y; the kept value gains the
-// partner's copy of it.
-__device__ __forceinline__ float pair_step(float x, float y, bool b, int off) {
-    float send = b ? x : y;
-    float keep = b ? y : x;
-    return keep + __shfl_xor_sync(kFull, send, off);
-}
-
 // Sums 9 per-lane values over the full warp in 12 shuffles (instead of the
 // 45 of nine butterflies): every halving step exchanges half of the values
 // still held, so lanes end up owning different parameters.  On return, lane
 // L holds the warp total of parameter reduce9_param(L) when that is <= 8.
+// The adds of one level are independent and go in pairs through the packed
+// FP32 unit (each component rounds as a scalar add would).
 __device__ __forceinline__ float reduce9(const float v[9], int lane) {
-    bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-    float w0 = pair_step(v[0], v[1], b4, 16);
-    float w1 = pair_step(v[2], v[3], b4, 16);
-    float w2 = pair_step(v[4], v[5], b4, 16);
-    float w3 = pair_step(v[6], v[7], b4, 16);
-    float w4 = pair_step(v[8], 0.0f, b4, 16);
-    float x0 = pair_step(w0, w1, b3, 8);
-    float x1 = pair_step(w2, w3, b3, 8);
-    float x2 = pair_step(w4, 0.0f, b3, 8);
-    float y0 = pair_step(x0, x1, b2, 4);
-    float y1 = pair_step(x2, 0.0f, b2, 4);
-    float z = pair_step(y0, y1, b1, 2);
-    return z + __shfl_xor_sync(kFull, z, 1);
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    // a lane keeps one value of each pair and sends the other to its partner
+    auto send = [](float x, float y, bool b) { return b ? x : y; };
+    auto keep = [](float x, float y, bool b) { return b ? y : x; };
+    auto xch = [](float x, int off) { return __shfl_xor_sync(kFull, x, off); };
+    const float2 w01 = __fadd2_rn(make_float2(keep(v[0], v[1], b4), keep(v[2], v[3], b4)),
+                                  make_float2(xch(send(v[0], v[1], b4), 16), xch(send(v[2], v[3], b4), 16)));
+    const float2 w23 = __fadd2_rn(make_float2(keep(v[4], v[5], b4), keep(v[6], v[7], b4)),
+                                  make_float2(xch(send(v[4], v[5], b4), 16), xch(send(v[6], v[7], b4), 16)));
+    const float w4 = keep(v[8], 0.0f, b4) + xch(send(v[8], 0.0f, b4), 16);
+    const float2 x01 = __fadd2_rn(make_float2(keep(w01.x, w01.y, b3), keep(w23.x, w23.y, b3)),
+                                  make_float2(xch(send(w01.x, w01.y, b3), 8), xch(send(w23.x, w23.y, b3), 8)));
+    const float x2 = keep(w4, 0.0f, b3) + xch(send(w4, 0.0f, b3), 8);
+    const float2 y01 = __fadd2_rn(make_float2(keep(x01.x, x01.y, b2), keep(x2, 0.0f, b2)),
+                                  make_float2(xch(send(x01.x, x01.y, b2), 4), xch(send(x2, 0.0f, b2), 4)));
+    const float z = keep(y01.x, y01.y, b1) + xch(send(y01.x, y01.y, b1), 2);
+    return z + xch(z, 1);
 }
 
 // Parameter index owned by lane L after reduce9 (>= 9: padding / duplicate).

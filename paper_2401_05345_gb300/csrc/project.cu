@@ -551,7 +551,7 @@ int backward_project_impl(int32_t n, int32_t sh_degree, const float* mean, const
         return GSR_EINVAL;
     if (!aligned16(grad2d)) return GSR_EINVAL;
     Cam k = make_cam(*cam);
-    const int blocks = (n + 127) / 128;
+    const int blocks = (n + kChunk - 1) / kChunk;
     cudaStream_t st = (cudaStream_t)stream;
     const bool vec = aligned16(feat) && aligned16(dfeat);
 #define GSR_BP(D)                                                                                                  \
