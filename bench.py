@@ -338,10 +338,11 @@ def ingest_traffic(csv_path, single_opts=None):
     if len(ids) < len(names):
         raise SystemExit(f"{len(ids)} backward launches in {csv_path}, {len(names)} tiers expected")
     kh = kernel_source_hash()
+    run = ("bench.py --profile --steps 1 --warmup 3, one launch of the benched tier (-s 7 -c 1)" if single_opts
+           else "bench.py --profile --profile-tiers")
     out = {"kernel_hash": kh,
            "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-                     "--clock-control none -k regex:backward_kernel (cold L2 per launch) of "
-                     "bench.py --profile --profile-tiers"}
+                     "--clock-control none -k regex:backward_kernel (cold L2 per launch) of " + run}
     for name, i in zip(names, ids[-len(names):]):
         m = launches[i]
         rd, wr = m["dram__bytes_read.sum"], m["dram__bytes_write.sum"]

@@ -197,22 +197,28 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
                 if constexpr (PPT == 2) {
                     SplatEval2 e;
                     bool hit0, hit1;
-                    eval_splat2_all(a.x, a.y, a.z, a.w, b.x, b.y, px[0], npy, e, hit0, hit1);
-                    hit0 = hit0 && !done[0];
-                    hit1 = hit1 && !done[1];
-                    const float2 testT = __fmul2_rn(T2, __fadd2_rn(bc2(1.0f), neg2(e.alpha)));
+                    splat_sigma2(a.x, a.y, a.z, a.w, b.x, px[0], npy, e);
+                    // alpha as in splat_alpha2, with the cap as a min (no capped
+                    // flags: only the backward needs them)
+                    const float2 oG = __fmul2_rn(bc2(b.y), make_float2(__expf(-e.sigma.x), __expf(-e.sigma.y)));
+                    const float2 alpha = make_float2(fminf(oG.x, kAlphaMax), fminf(oG.y, kAlphaMax));
+                    hit0 = e.sigma.x >= 0.0f && alpha.x >= kAlphaMin && !done[0];
+                    hit1 = e.sigma.y >= 0.0f && alpha.y >= kAlphaMin && !done[1];
+                    const float2 testT = __fmul2_rn(T2, __fadd2_rn(bc2(1.0f), neg2(alpha)));
                     const bool stop0 = hit0 && testT.x < kTMin, stop1 = hit1 && testT.y < kTMin;
                     const bool take0 = hit0 && !stop0, take1 = hit1 && !stop1;
                     done[0] = done[0] || stop0;
                     done[1] = done[1] || stop1;
+                    // a pixel that does not take the splat blends it with alpha 0:
+                    // weight 0 and T * (1 - 0) = T exactly, so T needs no select
+                    const float2 ae = make_float2(take0 ? alpha.x : 0.0f, take1 ? alpha.y : 0.0f);
                     if (COLOR) {
-                        const float2 aT = __fmul2_rn(e.alpha, T2);
-                        const float2 wgt = make_float2(take0 ? aT.x : 0.0f, take1 ? aT.y : 0.0f);
+                        const float2 wgt = __fmul2_rn(ae, T2);
                         C2[0] = __ffma2_rn(bc2(b.z), wgt, C2[0]);
                         C2[1] = __ffma2_rn(bc2(b.w), wgt, C2[1]);
                         C2[2] = __ffma2_rn(bc2(cz), wgt, C2[2]);
                     }
-                    T2 = make_float2(take0 ? testT.x : T2.x, take1 ? testT.y : T2.y);
+                    T2 = __fmul2_rn(T2, __fadd2_rn(bc2(1.0f), neg2(ae)));
                     last[0] = take0 ? base + k + 1 : last[0];
                     last[1] = take1 ? base + k + 1 : last[1];
                 } else {
