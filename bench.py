@@ -962,10 +962,10 @@ def run_ours(args):
 
 # Kernels of libgsr launched per step: preprocess; binning (depth keys, three
 # column scans and three radix scatter passes, the last also writing the tile
-# rectangles; entry counts, slice bounds, block x tile counts, column scan +
-# ranges + tile order, placement); forward with the L1 loss in its epilogue,
-# backward, backward projection.
-LAUNCHES_PER_STEP = 16
+# rectangles; entry prefixes, block x tile counts with the slice starts,
+# column scan + ranges + tile order, placement); forward with the L1 loss in
+# its epilogue, backward, backward projection.
+LAUNCHES_PER_STEP = 15
 
 
 def main():

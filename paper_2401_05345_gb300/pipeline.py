@@ -269,7 +269,7 @@ class Renderer:
 
 class StepGraph:
     """One view's training step (``Renderer.step`` with asynchronous binning)
-    captured once in a CUDA graph and replayed.  The step's 16 kernel
+    captured once in a CUDA graph and replayed.  The step's 15 kernel
     launches, the loss reset and the gradient zeroing go to the GPU as one
     graph launch, so no launch gap separates the short binning kernels.
 
