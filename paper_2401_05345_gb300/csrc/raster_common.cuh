@@ -185,11 +185,15 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
         __syncthreads();
         bool wdone = __all_sync(kFull, all_done);
         for (int c0 = 0; c0 < cnt && !wdone; c0 += 32) {
-            const int kq = c0 + lane;
+            // ballot bit 31 - i is entry c0 + i: the next entry is the highest set
+            // bit (one ALU instruction fewer per step than the lowest; the ALU
+            // pipe is what limits this walk)
+            const int kq = c0 + 31 - lane;
             unsigned bits = __ballot_sync(kFull, kq < cnt && ((s_mask[kq] >> w) & 1u));
             while (bits) {
-                const int k = c0 + __ffs(bits) - 1;
-                bits &= bits - 1u;
+                const int lz = __clz(bits);
+                const int k = c0 + lz;
+                bits ^= 0x80000000u >> lz;
                 const float4 a = s_a[k], b = s_b[k];
                 const float cz = COLOR ? s_c[k] : 0.0f;
                 // no branches: a pixel that is done or skips the splat keeps
