@@ -309,7 +309,9 @@ def ingest_traffic(csv_path, single_opts=None):
     ``--profile`` run captured with
     ``--metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum -k regex:backward_kernel``.
     With ``single_opts`` (a tier name) the capture holds one launch of that
-    tier; otherwise it is a ``--profile-tiers`` run whose last launches are
+    tier, whose entry replaces the old one (the other tiers' entries stay,
+    each with the source hash it was taken on); otherwise it is a
+    ``--profile-tiers`` run whose last launches are
     the tier launches, one per autotune candidate in order (the cluster
     tier's own kernel does not match)."""
     import csv
@@ -340,15 +342,19 @@ def ingest_traffic(csv_path, single_opts=None):
     kh = kernel_source_hash()
     run = ("bench.py --profile --steps 1 --warmup 3, one launch of the benched tier (-s 7 -c 1)" if single_opts
            else "bench.py --profile --profile-tiers")
-    out = {"kernel_hash": kh,
-           "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-                     "--clock-control none -k regex:backward_kernel (cold L2 per launch) of " + run}
+    path = os.path.join(ROOT, "profiles", "backward_traffic.json")
+    out = {}
+    if single_opts and os.path.exists(path):  # one tier recaptured: the other tiers' entries are kept
+        with open(path) as f:
+            out = json.load(f)
+    out["kernel_hash"] = kh
+    out["source"] = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                     "--clock-control none -k regex:backward_kernel (cold L2 per launch) of " + run)
     for name, i in zip(names, ids[-len(names):]):
         m = launches[i]
         rd, wr = m["dram__bytes_read.sum"], m["dram__bytes_write.sum"]
         out[name] = {"kernel_hash": kh, "dram_bytes_per_launch": rd + wr, "dram_read": rd, "dram_write": wr,
                      "ncu_us": m["gpu__time_duration.sum"]}
-    path = os.path.join(ROOT, "profiles", "backward_traffic.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(f"wrote {path}: {len(names)} tiers, kernel hash {kh}")
