@@ -258,9 +258,20 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
                   float* __restrict__ splat2d, int* __restrict__ radius, float* __restrict__ gzero) {
     constexpr int K = DEG < 0 ? 1 : (DEG + 1) * (DEG + 1);
     constexpr int NF = 3 * K;
-    __shared__ float s_f[DEG < 0 ? 1 : kChunk * (NF + 1)];
+    // rows of whole 16-byte words: every thread loads its own row into
+    // registers (no staging, no barrier)
+    constexpr bool DIRECT = VEC && DEG >= 1 && NF % 4 == 0;
+    __shared__ float s_f[DEG < 0 || DIRECT ? 1 : kChunk * (NF + 1)];
     const int base = blockIdx.x * kChunk;
     const int i = base + threadIdx.x;
+    float4 fr[DIRECT ? NF / 4 : 1];
+    if constexpr (DIRECT) {
+        if (i < n) {
+            const float4* g4 = reinterpret_cast<const float4*>(feat + (size_t)i * NF);
+#pragma unroll
+            for (int q = 0; q < NF / 4; ++q) fr[q] = g4[q];
+        }
+    }
     // this Gaussian's inputs are requested before the feature staging, so
     // their latency overlaps it
     float mv[3] = {0.f, 0.f, 0.f}, sv[3] = {0.f, 0.f, 0.f}, qv[4] = {1.f, 0.f, 0.f, 0.f}, op = 0.f;
@@ -274,7 +285,7 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
         for (int j = 0; j < 4; ++j) qv[j] = quat[4 * (size_t)i + j];
         op = opacity[i];
     }
-    if constexpr (DEG >= 0) {
+    if constexpr (DEG >= 0 && !DIRECT) {
         stage_rows_in<NF, kChunk, VEC>(feat + (size_t)base * NF, min(kChunk, n - base), s_f);
         __syncthreads();
     }
@@ -312,12 +323,21 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
         float Y[16];
         sh_basis(DEG, dx * il, dy * il, dz * il, Y);
         const float* f = s_f + threadIdx.x * (NF + 1);
+        // feature x of the row (x a compile-time index after unrolling)
+        auto F = [&](int x) -> float {
+            if constexpr (DIRECT) {
+                const float4 w = fr[x >> 2];
+                return (x & 3) == 0 ? w.x : (x & 3) == 1 ? w.y : (x & 3) == 2 ? w.z : w.w;
+            } else {
+                return f[x];
+            }
+        };
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            s0 = fmaf(Y[j], f[3 * j], s0);
-            s1 = fmaf(Y[j], f[3 * j + 1], s1);
-            s2 = fmaf(Y[j], f[3 * j + 2], s2);
+            s0 = fmaf(Y[j], F(3 * j), s0);
+            s1 = fmaf(Y[j], F(3 * j + 1), s1);
+            s2 = fmaf(Y[j], F(3 * j + 2), s2);
         }
         rgb[0] = fmaxf(s0 + 0.5f, 0.f);
         rgb[1] = fmaxf(s1 + 0.5f, 0.f);
