@@ -374,7 +374,10 @@ def test_invalid_arguments_raise(dev):
 def test_unaligned_features_take_the_scalar_path(dev):
     """Feature arrays that start off a 16-byte boundary (e.g. a segment of a
     packed parameter buffer) give the same projection and backward
-    projection as aligned ones."""
+    projection as aligned ones, bit for bit: aligned SH3 rows take the
+    projection's per-thread register path and the backward projection's
+    16-byte staging, unaligned ones the scalar staging of both (1001
+    Gaussians: the last chunk is ragged)."""
     scene = S.gmm_scene(9, 1001, 8, (-3.3, 0.4), 3)
     cam = S.front_camera(96, 80)
     n = scene.n
