@@ -176,7 +176,11 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
     // two pixels per thread share their column (Shape::pixel): their
     // transmittance and colour run as float2 pairs
     float2 T2 = bc2(1.0f), C2[3] = {bc2(0.0f), bc2(0.0f), bc2(0.0f)};
-    const float2 npy = make_float2(-py[0], -py[PPT - 1]);
+    // a pixel that is done (outside the image, or stopped) has a NaN row:
+    // every splat's sigma is then NaN there and fails sigma >= 0, so the
+    // hit test needs no done flag
+    float2 npy = make_float2(inside[0] ? -py[0] : __int_as_float(0x7fc00000),
+                             inside[PPT - 1] ? -py[PPT - 1] : __int_as_float(0x7fc00000));
     for (int base = 0; base < n; base += SH::B) {
         if (__syncthreads_count(all_done) == SH::NT) break;
         const int cnt = min(SH::B, n - base);
@@ -206,13 +210,13 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
                     // flags: only the backward needs them)
                     const float2 oG = __fmul2_rn(bc2(b.y), make_float2(__expf(-e.sigma.x), __expf(-e.sigma.y)));
                     const float2 alpha = make_float2(fminf(oG.x, kAlphaMax), fminf(oG.y, kAlphaMax));
-                    hit0 = e.sigma.x >= 0.0f && alpha.x >= kAlphaMin && !done[0];
-                    hit1 = e.sigma.y >= 0.0f && alpha.y >= kAlphaMin && !done[1];
+                    hit0 = e.sigma.x >= 0.0f && alpha.x >= kAlphaMin;
+                    hit1 = e.sigma.y >= 0.0f && alpha.y >= kAlphaMin;
                     const float2 testT = __fmul2_rn(T2, __fadd2_rn(bc2(1.0f), neg2(alpha)));
                     const bool stop0 = hit0 && testT.x < kTMin, stop1 = hit1 && testT.y < kTMin;
                     const bool take0 = hit0 && !stop0, take1 = hit1 && !stop1;
-                    done[0] = done[0] || stop0;
-                    done[1] = done[1] || stop1;
+                    npy.x = stop0 ? __int_as_float(0x7fc00000) : npy.x;
+                    npy.y = stop1 ? __int_as_float(0x7fc00000) : npy.y;
                     // a pixel that does not take the splat blends it with alpha 0:
                     // weight 0 and T * (1 - 0) = T exactly, so T needs no select
                     const float2 ae = make_float2(take0 ? alpha.x : 0.0f, take1 ? alpha.y : 0.0f);
@@ -245,9 +249,13 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
                     }
                 }
             }
-            all_done = true;
+            if constexpr (PPT == 2) {
+                all_done = isnan(npy.x) && isnan(npy.y);
+            } else {
+                all_done = true;
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) all_done &= done[q];
+                for (int q = 0; q < PPT; ++q) all_done &= done[q];
+            }
             wdone = __all_sync(kFull, all_done);
         }
     }
