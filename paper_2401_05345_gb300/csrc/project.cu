@@ -272,8 +272,9 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
             for (int q = 0; q < NF / 4; ++q) fr[q] = g4[q];
         }
     }
-    // this Gaussian's inputs are requested before the feature staging, so
-    // their latency overlaps it
+    // this Gaussian's other inputs are requested before the feature staging
+    // (with rows in registers: right after the row's loads), so all of
+    // their latencies overlap
     float mv[3] = {0.f, 0.f, 0.f}, sv[3] = {0.f, 0.f, 0.f}, qv[4] = {1.f, 0.f, 0.f, 0.f}, op = 0.f;
     if (i < n) {
 #pragma unroll
