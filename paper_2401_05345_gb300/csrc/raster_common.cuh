@@ -179,8 +179,8 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
     // a pixel that is done (outside the image, or stopped) has a NaN row:
     // every splat's sigma is then NaN there and fails sigma >= 0, so the
     // hit test needs no done flag
-    float2 npy = make_float2(inside[0] ? -py[0] : __int_as_float(0x7fc00000),
-                             inside[PPT - 1] ? -py[PPT - 1] : __int_as_float(0x7fc00000));
+    const float row_done = __int_as_float(0x7fc00000);  // a quiet NaN
+    float2 npy = make_float2(inside[0] ? -py[0] : row_done, inside[PPT - 1] ? -py[PPT - 1] : row_done);
     for (int base = 0; base < n; base += SH::B) {
         if (__syncthreads_count(all_done) == SH::NT) break;
         const int cnt = min(SH::B, n - base);
@@ -215,8 +215,8 @@ __device__ __forceinline__ void walk_front(uint2 rg, const uint32_t* __restrict_
                     const float2 testT = __fmul2_rn(T2, __fadd2_rn(bc2(1.0f), neg2(alpha)));
                     const bool stop0 = hit0 && testT.x < kTMin, stop1 = hit1 && testT.y < kTMin;
                     const bool take0 = hit0 && !stop0, take1 = hit1 && !stop1;
-                    npy.x = stop0 ? __int_as_float(0x7fc00000) : npy.x;
-                    npy.y = stop1 ? __int_as_float(0x7fc00000) : npy.y;
+                    npy.x = stop0 ? row_done : npy.x;
+                    npy.y = stop1 ? row_done : npy.y;
                     // a pixel that does not take the splat blends it with alpha 0:
                     // weight 0 and T * (1 - 0) = T exactly, so T needs no select
                     const float2 ae = make_float2(take0 ? alpha.x : 0.0f, take1 ? alpha.y : 0.0f);
