@@ -271,7 +271,7 @@ colscan_kernel(int rows, int cols, uint32_t* __restrict__ m, uint32_t* __restric
 }
 
 // One scatter pass of the depth sort.  The tile's keys are ranked stably
-// (warp-striped: warp w holds keys w*512 .. w*512+511 of the tile, item i of
+// (warp-striped: warp w holds keys w*256 .. w*256+255 of the tile, item i of
 // lane l is key 32 i + l of that run) with per-bit ballots per warp, per-warp
 // digit counts are scanned across the warps, and every key goes to
 //   (keys of smaller digits) + (keys of its digit in earlier tiles)
