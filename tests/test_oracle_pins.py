@@ -46,6 +46,29 @@ def test_sh_basis_low_orders_closed_form(orc):
     np.testing.assert_allclose(y, [c0, -c1 * d[1], c1 * d[2], -c1 * d[0]], rtol=1e-14)
 
 
+def test_sh_basis_signs_from_the_complex_harmonics(orc):
+    """Every basis function of degree <= 3, sign included, against the
+    complex spherical harmonics of scipy.special (Condon-Shortley phase).
+    The standard real form is sqrt(2) (-1)^m Im Y_l^|m| for m < 0, Y_l^0,
+    and sqrt(2) (-1)^m Re Y_l^m for m > 0; the rasterizer's basis (the 3DGS
+    convention) is that times (-1)^m, at index l^2 + l + m."""
+    sp = pytest.importorskip("scipy.special")
+    if not hasattr(sp, "sph_harm_y"):
+        pytest.skip("scipy.special.sph_harm_y not available")
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        theta, phi = math.acos(d[2]), math.atan2(d[1], d[0])  # polar, azimuth
+        ref = np.zeros(16)
+        for l in range(4):
+            for m in range(-l, l + 1):
+                y = complex(sp.sph_harm_y(l, abs(m), theta, phi))
+                real = y.real if m == 0 else math.sqrt(2) * (-1) ** m * (y.imag if m < 0 else y.real)
+                ref[l * l + l + m] = (-1) ** m * real
+        np.testing.assert_allclose(orc.sh_basis(3, d), ref, rtol=1e-12, atol=1e-14)
+
+
 def test_sh_basis_gradient_fd(orc):
     rng = np.random.default_rng(3)
     for _ in range(5):
