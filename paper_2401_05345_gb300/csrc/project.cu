@@ -250,16 +250,29 @@ __device__ __forceinline__ bool project(const Cam& k, const float* mean, const f
     return true;
 }
 
+// One 32-byte load of read-only data (p 32-byte aligned) into two float4s.
+__device__ __forceinline__ void ld_nc_v8(const float* p, float4& a, float4& b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
+// Load widths the caller's alignment allows (uniform over the launch).
+constexpr int kWideFeat = 1;  // feature rows 32-byte aligned (base 32-byte aligned, rows a multiple of 32 B)
+constexpr int kWideQuat = 2;  // quaternion rows 16-byte aligned
+
 template <int DEG, bool VEC>
 __global__ void __launch_bounds__(kChunk)
 preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict__ scale,
                   const float* __restrict__ quat, const float* __restrict__ opacity,
                   const float* __restrict__ feat, Cam k, int gx, int gy, int tw_log2, int th_log2,
-                  float* __restrict__ splat2d, int* __restrict__ radius, float* __restrict__ gzero) {
+                  float* __restrict__ splat2d, int* __restrict__ radius, float* __restrict__ gzero,
+                  int wide) {
     constexpr int K = DEG < 0 ? 1 : (DEG + 1) * (DEG + 1);
     constexpr int NF = 3 * K;
     // rows of whole 16-byte words: every thread loads its own row into
-    // registers (no staging, no barrier)
+    // registers (no staging, no barrier), 32 bytes a load where the rows
+    // allow it
     constexpr bool DIRECT = VEC && DEG >= 1 && NF % 4 == 0;
     __shared__ float s_f[DEG < 0 || DIRECT ? 1 : kChunk * (NF + 1)];
     const int base = blockIdx.x * kChunk;
@@ -267,9 +280,15 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
     float4 fr[DIRECT ? NF / 4 : 1];
     if constexpr (DIRECT) {
         if (i < n) {
-            const float4* g4 = reinterpret_cast<const float4*>(feat + (size_t)i * NF);
+            const float* row = feat + (size_t)i * NF;
+            if (NF % 8 == 0 && (wide & kWideFeat)) {
 #pragma unroll
-            for (int q = 0; q < NF / 4; ++q) fr[q] = g4[q];
+                for (int q = 0; q < NF / 8; ++q) ld_nc_v8(row + 8 * q, fr[2 * q], fr[2 * q + 1]);
+            } else {
+                const float4* g4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+                for (int q = 0; q < NF / 4; ++q) fr[q] = g4[q];
+            }
         }
     }
     // this Gaussian's other inputs are requested before the feature staging
@@ -282,8 +301,16 @@ preprocess_kernel(int n, const float* __restrict__ mean, const float* __restrict
             mv[j] = mean[3 * (size_t)i + j];
             sv[j] = scale[3 * (size_t)i + j];
         }
+        if (wide & kWideQuat) {
+            const float4 q4 = *reinterpret_cast<const float4*>(quat + 4 * (size_t)i);
+            qv[0] = q4.x;
+            qv[1] = q4.y;
+            qv[2] = q4.z;
+            qv[3] = q4.w;
+        } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) qv[j] = quat[4 * (size_t)i + j];
+            for (int j = 0; j < 4; ++j) qv[j] = quat[4 * (size_t)i + j];
+        }
         op = opacity[i];
     }
     if constexpr (DEG >= 0 && !DIRECT) {
@@ -540,14 +567,15 @@ extern "C" int gsr_preprocess(int32_t n, int32_t sh_degree, const float* mean, c
     cudaStream_t st = (cudaStream_t)stream;
     const int twl = ilog2(tile_w), thl = ilog2(tile_h);
     const bool vec = aligned16(feat);
+    const int wide = (((uintptr_t)feat & 31u) == 0 ? kWideFeat : 0) | (aligned16(quat) ? kWideQuat : 0);
 #define GSR_PRE(D)                                                                                          \
     do {                                                                                                    \
         if (vec) preprocess_kernel<D, true><<<blocks, kChunk, 0, st>>>(n, mean, scale, quat, opacity, feat, k, \
                                                                     gx, gy, twl, thl, splat2d, radius,      \
-                                                                    grad2d_to_zero);                        \
+                                                                    grad2d_to_zero, wide);                  \
         else preprocess_kernel<D, false><<<blocks, kChunk, 0, st>>>(n, mean, scale, quat, opacity, feat, k,   \
                                                                  gx, gy, twl, thl, splat2d, radius,         \
-                                                                 grad2d_to_zero);                           \
+                                                                 grad2d_to_zero, wide);                     \
     } while (0)
     switch (sh_degree) {
         case -1: GSR_PRE(-1); break;

@@ -372,36 +372,40 @@ def test_invalid_arguments_raise(dev):
 
 
 def test_unaligned_features_take_the_scalar_path(dev):
-    """Feature arrays that start off a 16-byte boundary (e.g. a segment of a
+    """Feature and quaternion arrays at any 4-byte offset (e.g. segments of a
     packed parameter buffer) give the same projection and backward
-    projection as aligned ones, bit for bit: aligned SH3 rows take the
-    projection's per-thread register path and the backward projection's
-    16-byte staging, unaligned ones the scalar staging of both (1001
-    Gaussians: the last chunk is ragged)."""
+    projection, bit for bit.  Features 32-byte aligned take the projection's
+    32-byte register loads, 16-byte aligned its 16-byte ones, others the
+    scalar staging; quaternions 16-byte aligned take one 16-byte load, others
+    four scalar ones (1001 Gaussians: the last chunk is ragged)."""
     scene = S.gmm_scene(9, 1001, 8, (-3.3, 0.4), 3)
     cam = S.front_camera(96, 80)
     n = scene.n
     feat = scene.feat.reshape(n, -1)
-    buf = torch.zeros(feat.size + 1, device=dev)
-    buf[1:] = torch.from_numpy(feat.reshape(-1)).to(dev)
-    unaligned = buf[1:]
-    assert unaligned.data_ptr() % 16 != 0
+
+    def at_offset(a, off):  # a copy of a starting `off` floats into a fresh (256-byte aligned) buffer
+        buf = torch.zeros(a.size + off, device=dev)
+        buf[off:] = torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(dev)
+        return buf[off:]
+
     outs = []
-    for f in (T(feat), unaligned):
+    for foff, qoff in ((0, 0), (4, 0), (1, 1), (0, 1)):
+        f = at_offset(feat, foff).view(n, -1)
+        q = at_offset(scene.quat, qoff).view(n, 4)
+        assert (f.data_ptr() % 32 == 0) == (foff == 0) and (f.data_ptr() % 16 == 0) == (foff % 4 == 0)
         splat = torch.zeros((n, 12), device=dev)
         radius = torch.zeros(n, dtype=torch.int32, device=dev)
-        gsr.gsr_preprocess(n, 3, T(scene.mean), T(scene.scale), T(scene.quat), T(scene.opacity), f, cam, 16, 16,
-                           splat, radius)
+        gsr.gsr_preprocess(n, 3, T(scene.mean), T(scene.scale), q, T(scene.opacity), f, cam, 16, 16, splat, radius)
         g12 = torch.ones((n, 12), device=dev)
-        dbuf = torch.zeros(feat.size + 1, device=dev)
-        df = dbuf[1:] if f is unaligned else torch.zeros(feat.size, device=dev)
+        df = at_offset(np.zeros(feat.size, np.float32), foff)
         z = lambda c: torch.zeros((n, c), device=dev)
         dm, ds, dq, do = z(3), z(3), z(4), torch.zeros(n, device=dev)
-        gsr.gsr_backward_project(n, 3, T(scene.mean), T(scene.scale), T(scene.quat), T(scene.opacity), f, cam,
-                                 radius, g12, dm, ds, dq, do, df)
-        outs.append((N(splat), N(radius), N(df), N(dm)))
-    for a, b in zip(outs[0], outs[1]):
-        np.testing.assert_array_equal(a, b)
+        gsr.gsr_backward_project(n, 3, T(scene.mean), T(scene.scale), q, T(scene.opacity), f, cam, radius, g12, dm,
+                                 ds, dq, do, df)
+        outs.append((N(splat), N(radius), N(df), N(dm), N(dq)))
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            np.testing.assert_array_equal(a, b)
 
 
 @pytest.mark.parametrize("ppt,layout", [(1, 0), (1, 1), (2, 0), (2, 1)])
